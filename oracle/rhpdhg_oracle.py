@@ -1,0 +1,439 @@
+"""Plain FP64 CPU oracle for restarted Halpern PDHG (rHPDHG, Algorithm 1) and reflected
+restarted Halpern PDHG (r2HPDHG, Algorithm 2) of Lu & Yang, "Restarted Halpern PDHG for Linear
+Programming" (arXiv 2407.16144).
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package smoke check and the CPU-baseline
+leg of the benchmark may import this module.  It shares no code with the CUDA library: it
+reads the problem from the seeded generators and does every step itself, in numpy/scipy
+float64, one step at a time, in the paper's order and notation.  Library primitives used as
+steps: scipy.sparse matrix-vector products, numpy norms.
+
+Problem form.  The paper treats the standard form (Section 2, eq. lp) min c^T x, Ax = b,
+x >= 0 with saddle form eq. minmax.  This oracle takes the general form
+    min c^T x  s.t.  A x = b,  G x >= h,  l <= x <= u
+with K = [A; G], q = [b; h], X = [l, u], Y = R^{m_eq} x R_+^{m_ineq}, which reduces to eq. lp
+for m_ineq = 0, l = 0, u = +inf.  The dual variable uses the Lagrangian sign
+L(x, y) = c^T x - y^T (K x - q), i.e. the paper's y of eq. pdhg with y -> -y:
+    x~ = proj_X(x - tau (c - K^T y))
+    y~ = proj_Y(y + sigma (q - K (2 x~ - x)))                                   (eq. pdhg)
+With tau = eta/omega and sigma = eta*omega the PDHG norm of Section 1.1 (Notation) becomes
+||z||_P^2 = ||x||^2/tau + ||y||^2/sigma + 2 y^T K x.
+
+Readings of silent or ambiguous passages (each listed with its reason in the design notes):
+  * preprocessing "as cuPDLP" (Section 7, Algorithmic enhancements): Ruiz equilibration
+    (R infinity-norm passes) then Pock-Chambolle scaling with alpha = 1;
+  * constant step eta = safety / sigma_max(K^) with sigma_max from a fixed number of power
+    iterations (Notation; the theory needs eta < 1/||A||);
+  * primal weight omega_0 = ||c^||/||q^|| and, at each restart,
+    omega <- exp(0.5 log(dy/dx) + 0.5 log omega) with dx, dy the anchor movements;
+  * first-epoch length tau^0 of eq. (adaptive-restart) is a parameter, the n = 0 rule is
+    "k > tau^0" as printed;
+  * rel-KKT termination (Section 7, Termination criteria) is the l2 relative primal residual,
+    dual residual and duality gap at the PDHG point (x~, y~), evaluated every C iterations;
+  * the infeasibility candidate is the displacement T(z^{n,0}) - z^{n,0} at each restart
+    point, the quantity Theorem (infeas) proves converges linearly to v.
+Parity pinned by tests/test_oracle_pins.py (vertex enumeration, closed-form box LPs, an
+independent LP solver's optimum, Proposition 1, Lemma (sublinear-feas), Corollary
+(sublinear-feas-reflected), Lemma (iterates-feas)(i), planted optima and planted Farkas
+certificates).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from typing import Callable, Optional
+
+import numpy as np
+import scipy.sparse as sp
+
+# status codes (same meaning as the C library's)
+RUNNING, OPTIMAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, ITERATION_LIMIT, TIME_LIMIT, \
+    NUMERICAL_ERROR, CANCELLED = range(8)
+
+
+@dataclasses.dataclass
+class OracleParams:
+    algorithm: int = 0            # 0 = rHPDHG (Algorithm 1), 1 = r2HPDHG (Algorithm 2)
+    eps_rel_kkt: float = 1e-4
+    eps_infeas: float = 1e-8
+    max_iters: int = 100_000
+    time_limit_s: float = 3600.0
+    ruiz_iters: int = 10
+    pock_chambolle_alpha: float = 1.0
+    step_size: float = 0.0        # 0 = eta from power iteration
+    step_safety: float = 0.9
+    power_iters: int = 100
+    primal_weight: float = 0.0    # 0 = ||c^||/||q^||
+    primal_weight_update: int = 1
+    first_epoch_len: int = 64     # tau^0 of eq. (adaptive-restart)
+    max_epoch_len: int = 1000     # 0 = no cap; restart once k >= max_epoch_len
+    restart_scheme: int = 0       # 0 = adaptive (eq. adaptive-restart), 1 = fixed (eq. fixed-restart)
+    restart_beta: float = math.exp(-1.0)
+    check_every: int = 64
+    x0: Optional[np.ndarray] = None
+    y0: Optional[np.ndarray] = None
+
+
+# ---------------------------------------------------------------------------------------------
+# problem set-up
+# ---------------------------------------------------------------------------------------------
+
+def csr_matrix(lp) -> sp.csr_matrix:
+    return sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+
+
+def scale_problem(K: sp.csr_matrix, ruiz_iters: int, alpha: float):
+    """Diagonal preconditioning K^ = D K E.
+
+    Ruiz equilibration: each pass divides row i by sqrt(max_j |K^_ij|) and column j by
+    sqrt(max_i |K^_ij|) (both norms taken on the same current matrix).  Then one
+    Pock-Chambolle pass with parameter alpha divides row i by sqrt(sum_j |K^_ij|^alpha) and
+    column j by sqrt(sum_i |K^_ij|^(2-alpha)).  A zero row or column keeps factor 1.
+    Returns (K^, D, E) with D, E the accumulated diagonals.
+    """
+    m, n = K.shape
+    Kh = K.copy().tocsr()
+    D = np.ones(m)
+    E = np.ones(n)
+    for _ in range(ruiz_iters):
+        A = abs(Kh)
+        rmax = np.asarray(A.max(axis=1).todense()).ravel() if m else np.zeros(0)
+        cmax = np.asarray(A.max(axis=0).todense()).ravel() if m else np.zeros(n)
+        dr = np.ones(m)
+        dc = np.ones(n)
+        dr[rmax > 0] = 1.0 / np.sqrt(rmax[rmax > 0])
+        dc[cmax > 0] = 1.0 / np.sqrt(cmax[cmax > 0])
+        Kh = (sp.diags(dr) @ Kh @ sp.diags(dc)).tocsr()
+        D *= dr
+        E *= dc
+    if alpha is not None and alpha >= 0:
+        A = abs(Kh)
+        rsum = np.asarray(A.power(alpha).sum(axis=1)).ravel() if m else np.zeros(0)
+        csum = np.asarray(A.power(2.0 - alpha).sum(axis=0)).ravel() if m else np.zeros(n)
+        dr = np.ones(m)
+        dc = np.ones(n)
+        dr[rsum > 0] = 1.0 / np.sqrt(rsum[rsum > 0])
+        dc[csum > 0] = 1.0 / np.sqrt(csum[csum > 0])
+        Kh = (sp.diags(dr) @ Kh @ sp.diags(dc)).tocsr()
+        D *= dr
+        E *= dc
+    return Kh, D, E
+
+
+def power_sigma_max(Kh: sp.csr_matrix, iters: int) -> float:
+    """Largest singular value of K^ by power iteration on K^T K^ from the unit vector
+    1/sqrt(n): v <- K^T K^ v / ||K^T K^ v||, ``iters`` times; returns ||K^ v||."""
+    m, n = Kh.shape
+    if m == 0 or Kh.nnz == 0:
+        return 0.0
+    v = np.full(n, 1.0 / math.sqrt(n))
+    for _ in range(iters):
+        w = Kh.T @ (Kh @ v)
+        s = np.linalg.norm(w)
+        if s == 0.0:
+            return 0.0
+        v = w / s
+    return float(np.linalg.norm(Kh @ v))
+
+
+# ---------------------------------------------------------------------------------------------
+# operator, norms, checks
+# ---------------------------------------------------------------------------------------------
+
+def pdhg_T(Kh, KhT, c, q, l, u, m_eq, tau, sigma, x, y):
+    """One PDHG step T(z) = (x~, y~) (eq. pdhg, Lagrangian sign), the plain definition:
+    both products are formed explicitly."""
+    xt = np.clip(x - tau * (c - KhT @ y), l, u)
+    yt = y + sigma * (q - Kh @ (2.0 * xt - x))
+    yt[m_eq:] = np.maximum(yt[m_eq:], 0.0)
+    return xt, yt
+
+
+def p_norm_sq(Kh, dx, dy, tau, sigma) -> float:
+    """||(dx, dy)||_P^2 = ||dx||^2/tau + ||dy||^2/sigma + 2 dy^T K^ dx (the PDHG norm of
+    Notation, with the square root the text omits restored by squaring)."""
+    return float(dx @ dx / tau + dy @ dy / sigma + 2.0 * (dy @ (Kh @ dx)))
+
+
+def lambda_projection(g, l, u):
+    """Reduced cost lambda = proj_Lambda(g): Lambda_j = {0} (free), [0, inf) (only l finite),
+    (-inf, 0] (only u finite), R (both finite)."""
+    lf = np.isfinite(l)
+    uf = np.isfinite(u)
+    lam = np.zeros_like(g)
+    both = lf & uf
+    lam[both] = g[both]
+    lo = lf & ~uf
+    lam[lo] = np.maximum(g[lo], 0.0)
+    up = uf & ~lf
+    lam[up] = np.minimum(g[up], 0.0)
+    return lam
+
+
+def rel_kkt(lp, K, x, y):
+    """Relative KKT error of an unscaled point (x, y) (Section 7, Termination criteria, read
+    as the l2 form): returns dict(rel_p, rel_d, rel_gap, primal_obj, dual_obj, rel_kkt)."""
+    m_eq = lp.m_eq
+    q, c, l, u = lp.q, lp.c, lp.l, lp.u
+    Kx = K @ x
+    r = q - Kx
+    r[m_eq:] = np.maximum(r[m_eq:], 0.0)
+    rel_p = np.linalg.norm(r) / (1.0 + np.linalg.norm(q))
+    g = c - K.T @ y
+    lam = lambda_projection(g, l, u)
+    rel_d = np.linalg.norm(g - lam) / (1.0 + np.linalg.norm(c))
+    p_obj = float(c @ x) + lp.obj_offset
+    lam_p = np.maximum(lam, 0.0)
+    lam_m = np.maximum(-lam, 0.0)
+    bound_terms = np.where(lam_p > 0, np.where(np.isfinite(l), l, 0.0) * lam_p, 0.0) \
+        - np.where(lam_m > 0, np.where(np.isfinite(u), u, 0.0) * lam_m, 0.0)
+    d_obj = float(q @ y) + float(bound_terms.sum()) + lp.obj_offset
+    rel_gap = abs(p_obj - d_obj) / (1.0 + abs(p_obj) + abs(d_obj))
+    return dict(rel_p=float(rel_p), rel_d=float(rel_d), rel_gap=float(rel_gap),
+                primal_obj=p_obj, dual_obj=d_obj, rel_kkt=float(max(rel_p, rel_d, rel_gap)))
+
+
+def primal_infeasibility_violation(lp, K, y):
+    """Farkas test for primal infeasibility (Proposition full-infeas, dual part of v).
+    A vector y (y_G >= 0) certifies Kx >=/= q has no solution in [l, u] when
+    q^T y - sum_j [ (K^T y)_j^+ u_j - (K^T y)_j^- l_j ] > 0 with (K^T y)_j <= 0 where
+    u_j = inf and (K^T y)_j >= 0 where l_j = -inf.  The candidate is scaled so this ray
+    objective equals 1; the return value is the largest remaining violation (inf when the
+    objective is not positive)."""
+    kty = K.T @ y
+    l, u = lp.l, lp.u
+    pos = np.maximum(kty, 0.0)
+    neg = np.maximum(-kty, 0.0)
+    obj = float(lp.q @ y) - float(np.where(np.isfinite(u), pos * np.where(np.isfinite(u), u, 0.0), 0.0).sum()) \
+        + float(np.where(np.isfinite(l), neg * np.where(np.isfinite(l), l, 0.0), 0.0).sum())
+    if not obj > 0.0:
+        return math.inf, obj
+    s = 1.0 / obj
+    viol = 0.0
+    if (~np.isfinite(u)).any():
+        viol = max(viol, float((pos[~np.isfinite(u)] * s).max(initial=0.0)))
+    if (~np.isfinite(l)).any():
+        viol = max(viol, float((neg[~np.isfinite(l)] * s).max(initial=0.0)))
+    if lp.m_ineq:
+        viol = max(viol, float((np.maximum(-y[lp.m_eq:], 0.0) * s).max(initial=0.0)))
+    return viol, obj
+
+
+def dual_infeasibility_violation(lp, K, d):
+    """Test of an unbounded primal ray d (primal part of v): c^T d < 0, A d = 0, G d >= 0,
+    d_j >= 0 where l_j is finite and d_j <= 0 where u_j is finite.  The ray is scaled so that
+    c^T d = -1; returns the largest remaining violation (inf if c^T d >= 0)."""
+    cd = float(lp.c @ d)
+    if not cd < 0.0:
+        return math.inf, cd
+    s = 1.0 / (-cd)
+    Kd = K @ d
+    viol = 0.0
+    if lp.m_eq:
+        viol = max(viol, float(np.abs(Kd[:lp.m_eq]).max()) * s)
+    if lp.m_ineq:
+        viol = max(viol, float(np.maximum(-Kd[lp.m_eq:], 0.0).max()) * s)
+    lf = np.isfinite(lp.l)
+    uf = np.isfinite(lp.u)
+    if lf.any():
+        viol = max(viol, float(np.maximum(-d[lf], 0.0).max()) * s)
+    if uf.any():
+        viol = max(viol, float(np.maximum(d[uf], 0.0).max()) * s)
+    return viol, cd
+
+
+# ---------------------------------------------------------------------------------------------
+# the solver
+# ---------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class OracleResult:
+    status: int
+    iters: int
+    restarts: int
+    rel_p: float
+    rel_d: float
+    rel_gap: float
+    primal_obj: float
+    dual_obj: float
+    x: np.ndarray
+    y: np.ndarray
+    cert_x: Optional[np.ndarray]
+    cert_y: Optional[np.ndarray]
+    eta: float
+    omega: float
+    sigma_max: float
+    D: np.ndarray
+    E: np.ndarray
+    solve_seconds: float
+    trace: list
+    snapshots: dict
+
+
+def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
+          trace: bool = False, time_limit_s: Optional[float] = None) -> OracleResult:
+    """Run rHPDHG / r2HPDHG on ``lp`` with ``params``.
+
+    The iteration counter t counts PDHG evaluations T(z); iteration t evaluates T at the
+    current iterate z^{n,k}.  ``snapshot_iters`` lists values of t after which the scaled
+    iterate z^{n,k}, the PDHG point T(z^{n,k}) and the anchor z^{n,0} are recorded.
+    ``trace`` records (t, n, k, ||z - T(z)||_P^2, restart, omega) per iteration.
+    """
+    t_start = time.perf_counter()
+    rho = 2.0 if params.algorithm == 1 else 1.0
+    m_eq, m, n = lp.m_eq, lp.m, lp.n
+    K = csr_matrix(lp)
+    Kh, D, E = scale_problem(K, params.ruiz_iters, params.pock_chambolle_alpha)
+    KhT = Kh.T.tocsr()
+    c = E * lp.c
+    q = D * lp.q
+    l = lp.l / E
+    u = lp.u / E
+
+    sigma_max = power_sigma_max(Kh, params.power_iters)
+    if params.step_size > 0:
+        eta = params.step_size
+    elif sigma_max > 1e-12:
+        eta = params.step_safety / sigma_max
+    else:
+        eta = 1.0
+    if params.primal_weight > 0:
+        omega = params.primal_weight
+    else:
+        cn, qn = np.linalg.norm(c), np.linalg.norm(q)
+        omega = cn / qn if (cn > 1e-10 and qn > 1e-10) else 1.0
+    tau, sigma = eta / omega, eta * omega
+
+    # initial point z^{0,0} = (proj_X(0), 0) or the (unscaled) warm start mapped to scaled space
+    x = np.clip(np.zeros(n), l, u) if params.x0 is None else np.asarray(params.x0, float) / E
+    y = np.zeros(m) if params.y0 is None else np.asarray(params.y0, float) / D
+    x0, y0 = x.copy(), y.copy()              # anchor z^{n,0}
+    n_ep, k = 0, 0
+    fpr0 = None
+    tr = []
+    snaps = {}
+    snapshot_iters = set(snapshot_iters)
+    beta2 = params.restart_beta * params.restart_beta
+    limit = params.time_limit_s if time_limit_s is None else time_limit_s
+
+    status = RUNNING
+    xt = yt = None
+    kkt = None
+    cert_x = cert_y = None
+    t = 0
+    while True:
+        xt, yt = pdhg_T(Kh, KhT, c, q, l, u, m_eq, tau, sigma, x, y)
+        dx, dy = x - xt, y - yt
+        fpr2 = p_norm_sq(Kh, dx, dy, tau, sigma)
+        if not np.isfinite(fpr2):
+            status = NUMERICAL_ERROR
+        if k == 0:
+            fpr0 = fpr2
+        if t in snapshot_iters:
+            snaps[t] = dict(x=x.copy(), y=y.copy(), xt=xt.copy(), yt=yt.copy(), x0=x0.copy(),
+                            y0=y0.copy(), n=n_ep, k=k, omega=omega, fpr2=fpr2)
+        last = (t + 1 >= params.max_iters)
+        # infeasibility at restart points: Theorem (infeas) bounds the distance of the
+        # displacement T(z^{n,0}) - z^{n,0} from the infimal displacement vector v, whose
+        # y-part certifies primal and x-part dual infeasibility (Proposition full-infeas)
+        if status == RUNNING and k == 0 and n_ep >= 1:
+            cx, cy = E * (xt - x), D * (yt - y)
+            vy, _ = primal_infeasibility_violation(lp, K, cy)
+            if vy <= params.eps_infeas:
+                status, cert_y = PRIMAL_INFEASIBLE, cy
+            else:
+                vx, _ = dual_infeasibility_violation(lp, K, cx)
+                if vx <= params.eps_infeas:
+                    status, cert_x = DUAL_INFEASIBLE, cx
+        if status == RUNNING and ((t + 1) % params.check_every == 0 or last):
+            kkt = rel_kkt(lp, K, E * xt, D * yt)
+            if kkt["rel_kkt"] <= params.eps_rel_kkt:
+                status = OPTIMAL
+            elif last:
+                status = ITERATION_LIMIT
+            elif time.perf_counter() - t_start > limit:
+                status = TIME_LIMIT
+        # restart test (eq. adaptive-restart / eq. fixed-restart, plus the epoch cap)
+        if params.restart_scheme == 1:
+            restart = params.max_epoch_len > 0 and k >= params.max_epoch_len
+        else:
+            restart = (n_ep == 0 and k > params.first_epoch_len) or \
+                      (n_ep >= 1 and fpr2 <= beta2 * fpr0) or \
+                      (params.max_epoch_len > 0 and k >= params.max_epoch_len)
+        if trace:
+            tr.append((t, n_ep, k, fpr2, bool(restart) and status == RUNNING, omega))
+        t += 1
+        if status != RUNNING:
+            break
+        if restart:
+            # z^{n+1,0} <- T(z^{n,k})
+            if params.primal_weight_update:
+                dxa = np.linalg.norm(xt - x0)
+                dya = np.linalg.norm(yt - y0)
+                ratio = dya / dxa if dxa > 1e-10 else 0.0
+                if dxa > 1e-10 and dya > 1e-10 and 0.0 < ratio < math.inf:
+                    omega = math.exp(0.5 * math.log(ratio) + 0.5 * math.log(omega))
+                    tau, sigma = eta / omega, eta * omega
+            x, y = xt.copy(), yt.copy()
+            x0, y0 = x.copy(), y.copy()
+            n_ep += 1
+            k = 0
+        else:
+            w = (k + 1.0) / (k + 2.0)
+            if rho == 1.0:
+                # eq. hpdhg: (k+1)/(k+2) T(z) + 1/(k+2) z^0
+                x = w * xt + (1.0 - w) * x0
+                y = w * yt + (1.0 - w) * y0
+            else:
+                # eq. hrpdhg: (k+1)/(k+2) (2 T(z) - z) + 1/(k+2) z^0
+                x = w * (2.0 * xt - x) + (1.0 - w) * x0
+                y = w * (2.0 * yt - y) + (1.0 - w) * y0
+            k += 1
+
+    if kkt is None:
+        kkt = rel_kkt(lp, K, E * xt, D * yt)
+    return OracleResult(status=status, iters=t, restarts=n_ep, rel_p=kkt["rel_p"],
+                        rel_d=kkt["rel_d"], rel_gap=kkt["rel_gap"],
+                        primal_obj=kkt["primal_obj"], dual_obj=kkt["dual_obj"], x=E * xt,
+                        y=D * yt, cert_x=cert_x, cert_y=cert_y, eta=eta, omega=omega,
+                        sigma_max=sigma_max, D=D, E=E,
+                        solve_seconds=time.perf_counter() - t_start, trace=tr,
+                        snapshots=snaps)
+
+
+def vanilla_pdhg(lp, eta, omega, iters, x0=None, y0=None):
+    """Plain fixed-point iteration z^{k+1} = T(z^k) on the unscaled problem (no scaling, no
+    restart), used for the trajectory identity of Proposition 1."""
+    K = csr_matrix(lp)
+    KT = K.T.tocsr()
+    tau, sigma = eta / omega, eta * omega
+    x = np.zeros(lp.n) if x0 is None else x0.copy()
+    y = np.zeros(lp.m) if y0 is None else y0.copy()
+    out = [(x.copy(), y.copy())]
+    for _ in range(iters):
+        x, y = pdhg_T(K, KT, lp.c, lp.q, lp.l, lp.u, lp.m_eq, tau, sigma, x, y)
+        out.append((x.copy(), y.copy()))
+    return out
+
+
+def halpern_pdhg(lp, eta, omega, iters, rho=1.0, x0=None, y0=None):
+    """Halpern PDHG without restarts on the unscaled problem (eq. hpdhg, or eq. hrpdhg for
+    rho = 2): returns the iterates z^0..z^iters and the PDHG points T(z^k)."""
+    K = csr_matrix(lp)
+    KT = K.T.tocsr()
+    tau, sigma = eta / omega, eta * omega
+    x = np.zeros(lp.n) if x0 is None else x0.copy()
+    y = np.zeros(lp.m) if y0 is None else y0.copy()
+    xa, ya = x.copy(), y.copy()
+    zs, ts = [], []
+    for k in range(iters + 1):
+        xt, yt = pdhg_T(K, KT, lp.c, lp.q, lp.l, lp.u, lp.m_eq, tau, sigma, x, y)
+        zs.append((x.copy(), y.copy()))
+        ts.append((xt.copy(), yt.copy()))
+        w = (k + 1.0) / (k + 2.0)
+        if rho == 1.0:
+            x, y = w * xt + (1 - w) * xa, w * yt + (1 - w) * ya
+        else:
+            x, y = w * (2 * xt - x) + (1 - w) * xa, w * (2 * yt - y) + (1 - w) * ya
+    return zs, ts
