@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-1e-6 rel-KKT on the 100k x 250k general-form LP (2.5M nonzeros,
+power-law columns, mixed bounds, planted optimum; lpgen.make_c2(seed=1)).
+
+One step = one complete pass of the hot path on that LP through the C ABI: rhpdhg_create from
+device-resident arrays (validation, transpose, Ruiz + Pock-Chambolle scaling, power iteration),
+rhpdhg_solve to rel-KKT <= 1e-6 and rhpdhg_poll into device buffers, then rhpdhg_free.
+``value`` is the whole-job throughput in LPs solved per second (1 / time-to-tolerance at one
+GPU); the e2e figure repeats the step from pinned host buffers, with the host->device copy of
+the problem and the device->host copy of (x, y) inside the timed region.
+
+Multi-GPU: the LPs are independent, so each rank solves its own copy (weak scaling, no data-path
+collective; a barrier and a max-over-ranks of the timings only).
+
+``--impl reference`` times the FP64 CPU oracle (the reference for this build) on the host
+cores instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 rel-KKT, iters/s, HBM GB/s vs peak; batched LPs/s, p50/p99"
+UNIT = "LP/s (100k x 250k LP solved to 1e-6 rel-KKT)"
+WORKLOAD = ("general-form LP 100k rows (70k =, 30k >=) x 250k cols, 2.5M nnz, power-law "
+            "columns (alpha 2.1, max 5000), mixed bounds, planted optimum, seed 1")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algorithm", type=int, default=1)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax = float(parts[1])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def problem_bytes(lp):
+    return (8 * (lp.m + 1) + 12 * lp.nnz + 8 * (3 * lp.n) + 8 * lp.m)
+
+
+def cpu_oracle_sample(lp, algorithm, tol, iters_to_tol, sample_iters=100):
+    """Times the FP64 oracle on the host: set-up (scaling + power iteration) plus
+    ``sample_iters`` iterations; the time to tolerance is extrapolated with ``iters_to_tol``."""
+    from oracle import rhpdhg_oracle as O
+    t0 = time.perf_counter()
+    K = O.csr_matrix(lp)
+    Kh, D, E = O.scale_problem(K, 10, 1.0)
+    O.power_sigma_max(Kh, 100)
+    setup = time.perf_counter() - t0
+    r = O.solve(lp, O.OracleParams(algorithm=algorithm, eps_rel_kkt=tol,
+                                   max_iters=sample_iters))
+    per_iter = (r.solve_seconds - setup) / sample_iters
+    per_iter = max(per_iter, 1e-9)
+    t_tol = setup + iters_to_tol * per_iter
+    return dict(setup_s=setup, s_per_iter=per_iter, time_to_tol_s=t_tol,
+                value=1.0 / t_tol, wall_s=time.perf_counter() - t0)
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from oracle import rhpdhg_oracle as O
+    from paper_2407_16144_gb300 import lpgen
+    lp = lpgen.make_c2(1)
+    # first warm-up step: one full solve, which fixes the oracle's own iteration count
+    t0 = time.perf_counter()
+    full = O.solve(lp, O.OracleParams(algorithm=args.algorithm, eps_rel_kkt=args.tol,
+                                      max_iters=1_000_000))
+    full_s = time.perf_counter() - t0
+    iters = full.iters
+    samples = []
+    for i in range(max(args.warmup - 1, 0) + args.steps):
+        s = cpu_oracle_sample(lp, args.algorithm, args.tol, iters)
+        if i >= max(args.warmup - 1, 0):
+            samples.append(s)
+    t = statistics.mean(s["time_to_tol_s"] for s in samples)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tol": args.tol, "algorithm": args.algorithm,
+                   "precision": "fp64"},
+        "time_to_tol_s": t, "iters": iters, "full_solve_s": full_s,
+        "iters_per_s": 1.0 / statistics.mean(s["s_per_iter"] for s in samples),
+        "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one full oracle solve ({iters} iterations, {full_s:.1f} s) "
+                                   f"fixes the iteration count; each step = set-up + 100 "
+                                   f"iterations, time-to-tol extrapolated"},
+        "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2407_16144_gb300 import _build, lpgen, rhpdhg
+
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    rhpdhg.load()
+    lp = lpgen.make_c2(1)
+    dev = lpgen.LP(**{f: (torch.as_tensor(getattr(lp, f), device="cuda")
+                          if isinstance(getattr(lp, f), np.ndarray) else getattr(lp, f))
+                      for f in ("m_eq", "m_ineq", "n", "row_ptr", "col_idx", "val", "c", "q",
+                                "l", "u")})
+    pinned = lpgen.LP(**{f: (torch.as_tensor(getattr(lp, f)).pin_memory().numpy()
+                             if isinstance(getattr(lp, f), np.ndarray) else getattr(lp, f))
+                         for f in ("m_eq", "m_ineq", "n", "row_ptr", "col_idx", "val", "c", "q",
+                                   "l", "u")})
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    xo = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+    yo = torch.empty(lp.m, dtype=torch.float64, device="cuda")
+    xh = torch.empty(lp.n, dtype=torch.float64).pin_memory().numpy()
+    yh = torch.empty(lp.m, dtype=torch.float64).pin_memory().numpy()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    params = dict(algorithm=args.algorithm, precision=args.precision, eps_rel_kkt=args.tol)
+
+    def step_device():
+        s = rhpdhg.Solver(dev, device=True, stream=sh, **params)
+        s.solve(1)
+        r = s.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
+        nl = s.launch_count()
+        s.close()
+        return r, nl
+
+    def step_host():
+        s = rhpdhg.Solver(pinned, stream=sh, **params)
+        s.solve(1)
+        r = s.poll(x=xh, y=yh)
+        s.close()
+        return r
+
+    def timed(fn, k):
+        out, ms = [], []
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            out.append(o)
+        return out, ms
+
+    for _ in range(args.warmup):
+        step_device()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    outs, ms = timed(step_device, args.steps)
+    if clocks:
+        clk = clocks.stop()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = sum(ms)
+    results = [o[0] for o in outs]
+    launches = sum(o[1] for o in outs)
+    iters = statistics.mean(r.iters for r in results)
+    solve_s = statistics.mean(r.solve_seconds for r in results)
+    ok = all(r.status == rhpdhg.STATUS_OPTIMAL for r in results)
+    # e2e through host buffers
+    e2e_outs, e2e_ms = timed(step_host, max(2, min(args.steps, 3)))
+    # kernel timing (CUDA events around each launch of the two iteration kernels)
+    s = rhpdhg.Solver(dev, device=True, stream=sh, profile=1, **params)
+    s.solve(1)
+    rp = s.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
+    kt = s.kernel_times()
+    s.close()
+    if dist is not None:
+        t = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, e2e_total = float(t[0]), float(t[1])
+    else:
+        e2e_total = sum(e2e_ms)
+    if rank != 0:
+        return 0
+    ms_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+    e2e_value = world * len(e2e_ms) / (e2e_total / 1000.0)
+    peak, peak_kind = load_peaks()
+    # dominant kernel by total time
+    if kt["ms_col"] >= kt["ms_row"]:
+        dom, dom_ms, dom_bytes = "column kernel (K^T y~ + primal step)", kt["ms_col"], kt["bytes_col"]
+    else:
+        dom, dom_ms, dom_bytes = "row kernel (K x~ + dual step)", kt["ms_row"], kt["bytes_row"]
+    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == 0 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tol": args.tol, "algorithm": args.algorithm,
+                   "precision": "fp64" if args.precision == 0 else "fp32 iterates, fp64 restarts",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "256 MB buffer written before every timed step (L2 flush)"},
+        "time_to_tol_s": ms_step / 1000.0, "solve_only_s": solve_s, "iters": iters,
+        "iters_per_s": iters / solve_s, "all_optimal": ok,
+        "rel_kkt": max(results[-1].rel_p, results[-1].rel_d, results[-1].rel_gap),
+        "gpu_launches": int(launches),
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": problem_bytes(lp),
+                "d2h_bytes_per_step": 8 * (lp.n + lp.m)},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "ms_per_launch_row": kt["ms_row"], "ms_per_launch_col": kt["ms_col"],
+                     "bytes_per_launch_row": kt["bytes_row"],
+                     "bytes_per_launch_col": kt["bytes_col"],
+                     "profiled_iters": rp.iters},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_oracle_sample(lp, args.algorithm, args.tol, iters)
+        line["cpu_baseline"] = {
+            "value": cb["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle set-up ({cb['setup_s']:.1f} s) + 100 iterations "
+                      f"({cb['s_per_iter'] * 1e3:.1f} ms each) on this LP; time-to-tol "
+                      f"extrapolated to the {iters:.0f} iterations both paths take "
+                      f"(FP64 iterate parity)"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * rhpdhg.h -- C ABI of a single-GPU (sm_103a) solver for linear programs by restarted Halpern
+ * PDHG (rHPDHG) and reflected restarted Halpern PDHG (r2HPDHG), after H. Lu and J. Yang,
+ * "Restarted Halpern PDHG for Linear Programming" (arXiv 2407.16144).
+ *
+ * Problem (general form; the paper's eq. lp, Section 2, is the case m_ineq = 0, l = 0, u = +inf):
+ *
+ *     minimize    c^T x + obj_offset
+ *     subject to  A x  = b        rows 0 .. m_eq-1 of K
+ *                 G x >= h        rows m_eq .. m_eq+m_ineq-1 of K
+ *                 l <= x <= u     entries of l may be -INFINITY, entries of u +INFINITY
+ *
+ * K = [A; G] is given in CSR; rhs = [b; h].  The method iterates the PDHG operator T of
+ * eq. pdhg (Section 2) inside the Halpern scheme of eq. hpdhg (Algorithm 1) or of its reflected
+ * form eq. hrpdhg (Algorithm 2), restarting by the fixed-point-residual rule of
+ * eq. adaptive-restart (Section 3).  The dual variable y follows the Lagrangian sign
+ * L(x, y) = c^T x - y^T (K x - rhs): y equals the paper's y of eq. pdhg with its sign flipped, so
+ * y >= 0 on the G rows.
+ *
+ * Conventions shared by every function below:
+ *   - Return value: RHPDHG_OK (0) on success, RHPDHG_BUSY (1) from poll while a solve is still
+ *     running, a negative RHPDHG_ERR_* code on failure.  rhpdhg_last_error() gives the message.
+ *     No function aborts, exits or traps; a device-side wait that runs out of its bound reports
+ *     RHPDHG_ERR_DEVICE_TIMEOUT.
+ *   - Problem outcomes (optimal, infeasible, limits) are statuses in rhpdhg_result, not errors.
+ *   - Ownership: create() copies every input, so the caller may free its arrays afterwards.
+ *     Output arrays in rhpdhg_result are owned by the caller and written by poll().
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef RHPDHG_H
+#define RHPDHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------------- */
+#define RHPDHG_OK                  0
+#define RHPDHG_BUSY                1
+#define RHPDHG_ERR_INVALID_ARG    -1   /* malformed CSR, NaN data, l > u, bad parameter        */
+#define RHPDHG_ERR_OOM            -2   /* device or pinned-host allocation failed              */
+#define RHPDHG_ERR_CUDA           -3   /* a CUDA runtime call failed                           */
+#define RHPDHG_ERR_DEVICE_TIMEOUT -4   /* a bounded device-side wait ran out                   */
+#define RHPDHG_ERR_STATE          -5   /* call not valid in the handle's current state         */
+
+/* ---- solve statuses (rhpdhg_result.status) ---------------------------------------------- */
+#define RHPDHG_STATUS_RUNNING            0
+#define RHPDHG_STATUS_OPTIMAL            1   /* rel-KKT <= eps_rel_kkt at the returned point   */
+#define RHPDHG_STATUS_PRIMAL_INFEASIBLE  2   /* cert_y holds a Farkas vector                   */
+#define RHPDHG_STATUS_DUAL_INFEASIBLE    3   /* cert_x holds an unbounded primal ray           */
+#define RHPDHG_STATUS_ITERATION_LIMIT    4
+#define RHPDHG_STATUS_TIME_LIMIT         5
+#define RHPDHG_STATUS_NUMERICAL_ERROR    6   /* a residual norm became NaN or infinite         */
+#define RHPDHG_STATUS_CANCELLED          7
+
+/* ---- memory kinds ---------------------------------------------------------------------- */
+#define RHPDHG_MEM_HOST    0
+#define RHPDHG_MEM_DEVICE  1
+
+typedef struct rhpdhg_handle rhpdhg_handle;
+
+/* The LP.  All arrays are read during rhpdhg_create only.
+ *   memory:  RHPDHG_MEM_HOST (pageable or pinned host memory) or RHPDHG_MEM_DEVICE (device
+ *            memory of the current device).
+ *   row_ptr: m+1 non-decreasing offsets, row_ptr[0] = 0, row_ptr[m] = nnz.
+ *   col_idx: nnz column indices in [0, n), strictly increasing within each row.
+ *   val:     nnz finite values.
+ *   c, l, u: n entries; rhs: m entries (b then h).  l <= u; l may hold -INFINITY and u
+ *            +INFINITY; c and rhs finite.
+ * Validation of the CSR structure and of the data (NaN, l > u) is done on the host for host
+ * memory and on the device for device memory; failures return RHPDHG_ERR_INVALID_ARG.        */
+typedef struct {
+  int32_t m_eq;
+  int32_t m_ineq;
+  int32_t n;
+  int32_t memory;
+  int64_t nnz;
+  const int64_t *row_ptr;
+  const int32_t *col_idx;
+  const double  *val;
+  const double  *c;
+  const double  *rhs;
+  const double  *l;
+  const double  *u;
+  double obj_offset;
+} rhpdhg_problem;
+
+/* Algorithm parameters.  rhpdhg_params_default() fills the documented defaults. */
+typedef struct {
+  int32_t algorithm;            /* 0 = rHPDHG (Algorithm 1, eq. hpdhg); 1 = r2HPDHG
+                                   (Algorithm 2, eq. hrpdhg).                        default 1 */
+  int32_t precision;            /* 0 = FP64 throughout; 1 = FP32 matrix values and iterates with
+                                   FP64 anchors, restart norms, residuals and checks. default 0 */
+  double  eps_rel_kkt;          /* stop when max(rel_p, rel_d, rel_gap) <= eps.   default 1e-4  */
+  double  eps_infeas;           /* certificate tolerance (normalised violation).  default 1e-8  */
+  int64_t max_iters;            /* PDHG evaluations T(z).                         default 1e7   */
+  double  time_limit_s;         /* wall clock, checked between graph launches.    default 3600  */
+  int32_t ruiz_iters;           /* Ruiz infinity-norm equilibration passes.       default 10    */
+  double  pock_chambolle_alpha; /* Pock-Chambolle exponent; < 0 skips the pass.   default 1.0   */
+  double  step_size;            /* eta; 0 = step_safety / sigma_max(K^) from power iteration */
+  double  step_safety;          /*                                                default 0.9   */
+  int32_t power_iters;          /* power-iteration steps for sigma_max.           default 100   */
+  double  primal_weight;        /* omega_0; 0 = ||c^|| / ||rhs^|| (1 if either is ~0)           */
+  int32_t primal_weight_update; /* 1 = omega <- exp(0.5 log(dy/dx) + 0.5 log omega) at restarts */
+  int32_t first_epoch_len;      /* tau^0 of eq. adaptive-restart (restart once k > tau^0 in the
+                                   first epoch).                                  default 64    */
+  int64_t max_epoch_len;        /* restart once k >= this (0 = no cap).           default 1000  */
+  int32_t restart_scheme;       /* 0 = adaptive (eq. adaptive-restart); 1 = fixed frequency
+                                   every max_epoch_len (eq. fixed-restart).       default 0     */
+  double  restart_beta;         /* restart when FPR <= beta * FPR(z^{n,0}).       default e^-1  */
+  int32_t check_every;          /* termination-check cadence C (iterations).      default 64    */
+  int32_t use_graphs;           /* 1 = replay a captured CUDA graph of C iterations. default 1  */
+  int32_t trace;                /* 1 = record one rhpdhg_trace_rec per iteration (device).     */
+  int32_t profile;              /* 1 = time the two per-iteration kernels with CUDA events
+                                   (disables graphs); read with rhpdhg_kernel_times().        */
+  int64_t trace_capacity;       /* records kept when trace = 1.                   default 4096  */
+  const double *x0;             /* optional warm start, host memory, unscaled (n)  (Algorithm 1
+                                   input z^{0,0}); NULL = projection of 0 onto [l, u]          */
+  const double *y0;             /* optional warm start, host memory (m); NULL = 0              */
+} rhpdhg_params;
+
+/* Result of a finished solve, filled by rhpdhg_poll. */
+typedef struct {
+  int32_t status;               /* RHPDHG_STATUS_*                                             */
+  int32_t out_memory;           /* memory kind of x, y, cert_x, cert_y below (input to poll)   */
+  int64_t iters;                /* PDHG evaluations performed                                  */
+  int64_t restarts;             /* outer iterations n (restarts performed)                     */
+  double  rel_p, rel_d, rel_gap;/* relative KKT parts at the returned point (last check)       */
+  double  primal_obj, dual_obj;
+  double  solve_seconds;        /* host wall clock from solve() to the final status           */
+  double  eta, omega, sigma_max;/* step size, final primal weight, power-iteration estimate    */
+  double *x;                    /* caller-owned, n entries, or NULL: primal point (unscaled)   */
+  double *y;                    /* caller-owned, m entries, or NULL: dual point (unscaled)     */
+  double *cert_x;               /* caller-owned, n, or NULL: unbounded ray d (DUAL_INFEASIBLE) */
+  double *cert_y;               /* caller-owned, m, or NULL: Farkas y (PRIMAL_INFEASIBLE)      */
+} rhpdhg_result;
+
+/* One per-iteration record (params.trace = 1). */
+typedef struct {
+  int64_t t;                    /* iteration (PDHG evaluation) index                           */
+  int64_t epoch;                /* outer counter n                                             */
+  int64_t k;                    /* inner counter k of the iterate z^{n,k}                      */
+  double  fpr_sq;               /* ||z^{n,k} - T(z^{n,k})||_P^2                                */
+  double  omega;                /* primal weight in force at iteration t                      */
+  int32_t restart;              /* 1 if z^{n+1,0} = T(z^{n,k}) follows                         */
+  int32_t pad;
+} rhpdhg_trace_rec;
+
+/* Fills *p with the defaults listed above.  Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG if
+ * p is NULL. */
+int rhpdhg_params_default(rhpdhg_params *p);
+
+/* Validates and copies the LP to the current device, builds the transposed matrix, applies
+ * Ruiz and Pock-Chambolle scaling (Section 7, "preprocessing"), estimates sigma_max(K^) by power
+ * iteration and sets the step size and primal weight.  `cuda_stream` is a cudaStream_t of the
+ * current device (NULL = the legacy default stream); all device work of the handle is ordered on
+ * it.  On success *out holds a new handle (free with rhpdhg_free).  On failure *out is NULL and
+ * rhpdhg_last_error(NULL) describes the error. */
+int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *cuda_stream,
+                  rhpdhg_handle **out);
+
+/* Runs Algorithm 1 or 2 (params.algorithm) from the initial point until a status is reached.
+ * blocking = 1 returns when the solve has finished; blocking = 0 returns at once and a host
+ * thread owned by the handle drives the device (poll reports completion).  Calling solve on a
+ * handle whose solve is running returns RHPDHG_ERR_STATE; calling it again after completion
+ * restarts from the initial point. */
+int rhpdhg_solve(rhpdhg_handle *h, int blocking);
+
+/* Non-blocking.  Returns RHPDHG_BUSY while the solve runs.  When done, fills *r (statistics,
+ * and copies of x, y, cert_x, cert_y into the caller's non-NULL arrays of kind r->out_memory)
+ * and returns RHPDHG_OK. */
+int rhpdhg_poll(rhpdhg_handle *h, rhpdhg_result *r);
+
+/* Requests cancellation of a running solve (status CANCELLED once the in-flight graph
+ * launches drain).  No effect on an idle handle. */
+int rhpdhg_cancel(rhpdhg_handle *h);
+
+/* Waits for any running solve, releases all device and host resources.  NULL-safe. */
+void rhpdhg_free(rhpdhg_handle *h);
+
+/* Message of the last error on h (or of the last failed create when h is NULL).  The string is
+ * owned by the library and valid until the next call on the same handle. */
+const char *rhpdhg_last_error(const rhpdhg_handle *h);
+
+/* ---- inspection (tests and tools) -------------------------------------------------------
+ * All copies below go to host memory and synchronise the handle's stream; they return
+ * RHPDHG_ERR_STATE while a solve is running. */
+
+/* Copies the scaled-space state: which = 0 current iterate z^{n,k} (x, y);
+ * 1 = last PDHG point T(z) (x~, y~); 2 = anchor z^{n,0}.  x holds n, y holds m doubles (either
+ * may be NULL).  In FP32 precision the iterate is widened to double. */
+int rhpdhg_get_state(const rhpdhg_handle *h, int which, double *x, double *y);
+
+/* Copies the diagonal scalings D (m) and E (n) with K^ = D K E, and the step data. Any pointer
+ * may be NULL. */
+int rhpdhg_get_scaling(const rhpdhg_handle *h, double *D, double *E, double *eta,
+                       double *omega0, double *sigma_max);
+
+/* Copies up to `capacity` trace records (params.trace = 1) of the last solve; *count receives
+ * the number recorded (min(iterations, trace_capacity)). */
+int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t capacity,
+                     int64_t *count);
+
+/* With params.profile = 1: average device time (ms) per launch of the row-side kernel
+ * (K x~ product + dual step) and of the column-side kernel (K^T y~ product + primal step) over
+ * the last solve, their launch counts, and the algorithmic bytes one launch of each moves. */
+int rhpdhg_kernel_times(const rhpdhg_handle *h, double *ms_row, double *ms_col,
+                        int64_t *launches_row, int64_t *launches_col, double *bytes_row,
+                        double *bytes_col);
+
+/* Number of CUDA kernels of this library the handle has launched so far (create and every
+ * solve; a replay of a captured graph counts each kernel node it runs).  Kernels of the CUB
+ * library used for the transpose during create are not counted.  Returns -1 for NULL. */
+int64_t rhpdhg_launch_count(const rhpdhg_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RHPDHG_H */

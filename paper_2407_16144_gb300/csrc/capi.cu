@@ -1,0 +1,733 @@
+// C ABI (include/rhpdhg.h): problem upload and preprocessing, the host driver of the device
+// iteration (CUDA-graph replays of C iterations, two in flight), polling and inspection.
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rhpdhg.h"
+#include "internal.h"
+
+using namespace rh;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double s() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace
+
+struct rhpdhg_handle {
+  int dev = 0;
+  int sm_count = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int m = 0, m_eq = 0, m_ineq = 0, n = 0;
+  long long nnz = 0;
+  double obj_offset = 0.0;
+  rhpdhg_params p{};
+  std::vector<double> h_x0, h_y0;
+
+  SideStore<double> rows, cols;
+  double *D = nullptr, *E = nullptr, *Dinv = nullptr, *Einv = nullptr;
+  double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr;
+  double *x = nullptr, *xt = nullptr, *x0 = nullptr, *kty = nullptr, *kty0 = nullptr,
+         *xout = nullptr, *certx = nullptr;
+  double *y = nullptr, *yt = nullptr, *y0 = nullptr, *kx = nullptr, *kxt = nullptr,
+         *kx0 = nullptr, *certy = nullptr;
+  double *x_init = nullptr, *y_init = nullptr, *xres = nullptr, *yres = nullptr;
+  Ctl *ctl = nullptr;
+  Ctl *h_mirror = nullptr;   // two pinned host mirrors of the control block
+  double *part_row = nullptr, *part_col = nullptr;
+  TraceRec *trace = nullptr;
+  IterConsts ic{};
+  RowVecs rv{};
+  ColVecs cv{};
+  int grid_row = 1, grid_col = 1, smem_row = 0, smem_col = 0;
+  double eta = 1.0, omega0 = 1.0, sigma_max = 0.0;
+
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::thread th;
+  std::atomic<int> running{0};
+  std::atomic<int> cancel{0};
+  bool solved = false;
+  int final_status = 0;
+  double solve_seconds = 0.0;
+  long long final_iters = 0;
+  Ctl final_ctl{};
+  std::string err;
+  int drive_err = 0;
+
+  double ms_row = 0, ms_col = 0;
+  long long n_row = 0, n_col = 0;
+  long long launches = 0;      // kernels launched by create and solves
+  double bytes_row = 0, bytes_col = 0;
+};
+
+namespace {
+
+int set_err(rhpdhg_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      return set_err(h, e_ == cudaErrorMemoryAllocation ? RHPDHG_ERR_OOM : RHPDHG_ERR_CUDA, \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    }                                                                                     \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, (count > 0 ? count : 1) * sizeof(T));
+}
+
+void destroy(rhpdhg_handle *h) {
+  if (!h) return;
+  if (h->th.joinable()) h->th.join();
+  for (auto &g : h->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  free_side(&h->rows);
+  free_side(&h->cols);
+  double *bufs[] = {h->D, h->E, h->Dinv, h->Einv, h->c, h->q, h->l, h->u, h->x, h->xt, h->x0,
+                    h->kty, h->kty0, h->xout, h->certx, h->y, h->yt, h->y0, h->kx, h->kxt,
+                    h->kx0, h->certy, h->x_init, h->y_init, h->xres, h->yres, h->part_row,
+                    h->part_col};
+  for (double *b : bufs) cudaFree(b);
+  cudaFree(h->ctl);
+  cudaFree(h->trace);
+  if (h->h_mirror) cudaFreeHost(h->h_mirror);
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+  delete h;
+}
+
+// Algorithmic bytes one launch of each iteration kernel moves (FP64, reflected or not): the
+// side's values and indices, row pointers, the gathered vector once, and the streamed vectors.
+void algorithmic_bytes(rhpdhg_handle *h) {
+  const double vb = 8.0, ib = 4.0;
+  const int rho2 = h->ic.rho2;
+  const double nnz = (double)h->nnz;
+  // row kernel: reads y~, y0, Kx~, Kx0, q (+ y, Kx for rho=2), writes y~, Kx~ (+ y, Kx)
+  const double row_vec = (5 + 2 * rho2) + (2 + 2 * rho2);
+  h->bytes_row = nnz * (vb + ib) + (h->m + 1) * ib + h->n * vb + h->m * vb * row_vec;
+  // column kernel: reads x~, x0, K^Ty0, c, l, u (+ x, K^Ty), writes x~ (+ x, K^Ty)
+  const double col_vec = (6 + 2 * rho2) + (1 + 2 * rho2);
+  h->bytes_col = nnz * (vb + ib) + (h->n + 1) * ib + h->m * vb + h->n * vb * col_vec;
+}
+
+void launch_iteration(rhpdhg_handle *h) {
+  launch_row_iter(h->st, h->rows.lay, h->xt, h->rv, h->ctl, h->part_row, h->ic, h->grid_row,
+                  h->smem_row);
+  launch_col_iter(h->st, h->cols.lay, h->yt, h->cv, h->ctl, h->part_col, h->ic, h->grid_col,
+                  h->smem_col, 0);
+}
+
+int capture_graphs(rhpdhg_handle *h) {
+  for (int g = 0; g < 2; ++g) {
+    if (h->gexec[g]) continue;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+    for (int i = 0; i < h->p.check_every; ++i) launch_iteration(h);
+    cudaMemcpyAsync(h->h_mirror + g, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
+    CK(cudaStreamEndCapture(h->st, &graph));
+    cudaError_t e = cudaGraphInstantiate(&h->gexec[g], graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+  }
+  return RHPDHG_OK;
+}
+
+int reset_state(rhpdhg_handle *h) {
+  Ctl c{};
+  c.t = 0; c.k = 0; c.n = 0; c.k_next = 0; c.n_next = 0;
+  c.status = kRunning;
+  c.restart_pending = 1;
+  c.w = 0.0;
+  c.omega = h->omega0;
+  c.tau = h->eta / h->omega0;
+  c.sigma = h->eta * h->omega0;
+  c.eta = h->eta;
+  CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->xt, h->x_init, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  if (h->m > 0)
+    CK(cudaMemcpyAsync(h->yt, h->y_init, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  // K x^{0,0} into the PDHG-point product slot; the first row kernel takes it as K x_0
+  side_spmv(h->st, h->rows.lay, h->x_init, h->kxt, h->grid_row);
+  // the column kernel in set-up phase forms x_0 = x^{0,0}, K^T y_0 and x~_0
+  launch_col_iter(h->st, h->cols.lay, h->yt, h->cv, h->ctl, h->part_col, h->ic, h->grid_col,
+                  h->smem_col, 1);
+  CK(cudaGetLastError());
+  return RHPDHG_OK;
+}
+
+// Runs the solve to completion (in the caller's thread or the handle's thread).
+void drive(rhpdhg_handle *h) {
+  cudaSetDevice(h->dev);
+  Timer timer;
+  int rc = reset_state(h);
+  h->launches += 2;      // K x^{0,0} and the set-up column kernel
+  const bool graphs = h->p.use_graphs && !h->p.profile;
+  if (rc == RHPDHG_OK && graphs) rc = capture_graphs(h);
+  if (rc != RHPDHG_OK) {
+    h->drive_err = rc;
+    h->final_status = kNumericalError;
+    h->running = 0;
+    return;
+  }
+  cudaEvent_t ev[2];
+  cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+  std::vector<cudaEvent_t> pev;
+  if (h->p.profile) {
+    pev.resize(3 * h->p.check_every);
+    for (auto &e : pev) cudaEventCreate(&e);
+  }
+  h->ms_row = h->ms_col = 0.0;
+  h->n_row = h->n_col = 0;
+  // Up to two chunks of C iterations in flight (one while profiling, so the per-launch events
+  // of a chunk can be read back).  Each chunk ends with a copy of the control block into its
+  // own pinned mirror; the host reads mirror g only after chunk g's event, and relaunches g
+  // only after that read.
+  const long long depth = h->p.profile ? 1 : 2;
+  long long launched = 0, done = 0, last_t = 0;
+  int host_status = kRunning;
+  bool stop = false;
+  while (true) {
+    while (!stop && launched - done < depth) {
+      if (h->cancel.load()) { host_status = kCancelled; stop = true; break; }
+      if (timer.s() > h->p.time_limit_s) { host_status = kTimeLimit; stop = true; break; }
+      const int g = (int)(launched & 1);
+      if (graphs) {
+        cudaGraphLaunch(h->gexec[g], h->st);
+      } else {
+        for (int i = 0; i < h->p.check_every; ++i) {
+          if (h->p.profile) cudaEventRecord(pev[3 * i], h->st);
+          launch_row_iter(h->st, h->rows.lay, h->xt, h->rv, h->ctl, h->part_row, h->ic,
+                          h->grid_row, h->smem_row);
+          if (h->p.profile) cudaEventRecord(pev[3 * i + 1], h->st);
+          launch_col_iter(h->st, h->cols.lay, h->yt, h->cv, h->ctl, h->part_col, h->ic,
+                          h->grid_col, h->smem_col, 0);
+          if (h->p.profile) cudaEventRecord(pev[3 * i + 2], h->st);
+        }
+        cudaMemcpyAsync(h->h_mirror + g, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
+      }
+      cudaEventRecord(ev[g], h->st);
+      ++launched;
+      h->launches += 2LL * h->p.check_every;
+    }
+    if (done >= launched) break;
+    const int g = (int)(done & 1);
+    cudaError_t e = cudaEventSynchronize(ev[g]);
+    ++done;
+    if (e != cudaSuccess) {
+      h->drive_err = RHPDHG_ERR_CUDA;
+      h->err = std::string("solve: ") + cudaGetErrorString(e);
+      stop = true;
+      continue;
+    }
+    const Ctl &mc = h->h_mirror[g];
+    if (h->p.profile) {
+      // count only the launches that did work (the rest returned at entry)
+      long long ran = mc.t - last_t;
+      if (mc.status == kNumericalError) ran += 1;
+      last_t = mc.t;
+      for (long long i = 0; i < ran && i < h->p.check_every; ++i) {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, pev[3 * i], pev[3 * i + 1]);
+        cudaEventElapsedTime(&b, pev[3 * i + 1], pev[3 * i + 2]);
+        h->ms_row += a;
+        h->ms_col += b;
+        h->n_row++;
+        h->n_col++;
+      }
+    }
+    if (mc.status != kRunning) stop = true;
+  }
+  cudaStreamSynchronize(h->st);
+  Ctl fin{};
+  cudaMemcpy(&fin, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+  h->final_ctl = fin;
+  h->final_status = fin.status != kRunning ? fin.status : host_status;
+  if (h->final_status == kRunning) h->final_status = kNumericalError;
+  launch_unscale(h->st, h->n, h->m, h->E, h->xout, h->D, h->yt, h->xres, h->yres);
+  h->launches += 1;
+  // time / cancel stops happen at a chunk boundary, right after a check iteration, so xout
+  // and y~ hold the PDHG point of that check
+  cudaStreamSynchronize(h->st);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess && !h->drive_err) {
+    h->drive_err = RHPDHG_ERR_CUDA;
+    h->err = std::string("solve: ") + cudaGetErrorString(le);
+  }
+  h->solve_seconds = timer.s();
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  for (auto &e : pev) cudaEventDestroy(e);
+  h->solved = true;
+  h->running = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rhpdhg_params_default(rhpdhg_params *p) {
+  if (!p) return RHPDHG_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->algorithm = 1;
+  p->precision = 0;
+  p->eps_rel_kkt = 1e-4;
+  p->eps_infeas = 1e-8;
+  p->max_iters = 10000000;
+  p->time_limit_s = 3600.0;
+  p->ruiz_iters = 10;
+  p->pock_chambolle_alpha = 1.0;
+  p->step_size = 0.0;
+  p->step_safety = 0.9;
+  p->power_iters = 100;
+  p->primal_weight = 0.0;
+  p->primal_weight_update = 1;
+  p->first_epoch_len = 64;
+  p->max_epoch_len = 1000;
+  p->restart_scheme = 0;
+  p->restart_beta = std::exp(-1.0);
+  p->check_every = 64;
+  p->use_graphs = 1;
+  p->trace = 0;
+  p->profile = 0;
+  p->trace_capacity = 4096;
+  p->x0 = nullptr;
+  p->y0 = nullptr;
+  return RHPDHG_OK;
+}
+
+const char *rhpdhg_last_error(const rhpdhg_handle *h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *cuda_stream,
+                  rhpdhg_handle **out) {
+  rhpdhg_handle *h = nullptr;
+  if (!out) return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!lp || !params) return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "lp or params is NULL");
+  const rhpdhg_params &P = *params;
+  if (lp->m_eq < 0 || lp->m_ineq < 0 || lp->n < 1 || lp->nnz < 0)
+    return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "negative size or n < 1");
+  if ((long long)lp->m_eq + lp->m_ineq > INT_MAX - 1 || lp->nnz > INT_MAX - 1)
+    return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "m or nnz exceeds the 32-bit index range");
+  if (lp->memory != RHPDHG_MEM_HOST && lp->memory != RHPDHG_MEM_DEVICE)
+    return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "unknown memory kind");
+  const int m = lp->m_eq + lp->m_ineq;
+  if (!lp->row_ptr || !lp->c || !lp->l || !lp->u || (m > 0 && !lp->rhs) ||
+      (lp->nnz > 0 && (!lp->col_idx || !lp->val)))
+    return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "missing problem array");
+  if (P.algorithm < 0 || P.algorithm > 1 || P.precision != 0 || P.check_every < 1 ||
+      P.max_iters < 1 || !(P.eps_rel_kkt > 0) || !(P.eps_infeas > 0) || P.ruiz_iters < 0 ||
+      P.power_iters < 1 || P.step_size < 0 || !(P.step_safety > 0) || P.primal_weight < 0 ||
+      P.first_epoch_len < 0 || P.max_epoch_len < 0 || P.restart_scheme < 0 ||
+      P.restart_scheme > 1 || (P.restart_scheme == 1 && P.max_epoch_len < 1) ||
+      !(P.restart_beta > 0 && P.restart_beta < 1) || P.trace_capacity < 0 ||
+      P.pock_chambolle_alpha > 2.0)
+    return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "invalid parameter");
+
+  h = new rhpdhg_handle();
+  h->p = P;
+  h->m = m;
+  h->m_eq = lp->m_eq;
+  h->m_ineq = lp->m_ineq;
+  h->n = lp->n;
+  h->nnz = lp->nnz;
+  h->obj_offset = lp->obj_offset;
+  h->st = (cudaStream_t)cuda_stream;
+  if (P.x0) h->h_x0.assign(P.x0, P.x0 + h->n);
+  if (P.y0) h->h_y0.assign(P.y0, P.y0 + m);
+  h->p.x0 = nullptr;
+  h->p.y0 = nullptr;
+
+  auto fail = [&](int code) {
+    std::string msg = h->err;
+    destroy(h);
+    g_create_error = msg;
+    return code;
+  };
+#define CKC(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? RHPDHG_ERR_OOM : RHPDHG_ERR_CUDA);          \
+    }                                                                                          \
+  } while (0)
+
+  const long long launches0 = launches_so_far();
+  CKC(cudaGetDevice(&h->dev));
+  if (!h->st) {
+    // stream capture is not allowed on the legacy default stream: use a private stream
+    CKC(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  CKC(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->dev));
+  const int n = h->n;
+  const int nnz = (int)h->nnz;
+  const cudaStream_t st = h->st;
+  const cudaMemcpyKind kind =
+      lp->memory == RHPDHG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+
+  // ---- upload + validate ----
+  long long *rp64 = nullptr;
+  int *rp = nullptr, *col = nullptr, *cp = nullptr, *ridx = nullptr;
+  double *val = nullptr, *cval = nullptr, *c_in = nullptr, *q_in = nullptr, *l_in = nullptr,
+         *u_in = nullptr, *tmp = nullptr;
+  unsigned int *flags = nullptr;
+  auto free_tmp = [&]() {
+    cudaFree(rp64); cudaFree(rp); cudaFree(col); cudaFree(cp); cudaFree(ridx); cudaFree(val);
+    cudaFree(cval); cudaFree(c_in); cudaFree(q_in); cudaFree(l_in); cudaFree(u_in); cudaFree(tmp);
+    cudaFree(flags);
+    rp64 = nullptr; rp = col = cp = ridx = nullptr; val = cval = c_in = q_in = l_in = u_in = tmp = nullptr;
+    flags = nullptr;
+  };
+#define CKT(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      free_tmp();                                                                              \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? RHPDHG_ERR_OOM : RHPDHG_ERR_CUDA);          \
+    }                                                                                          \
+  } while (0)
+
+  CKT(dalloc(&rp64, m + 1));
+  CKT(dalloc(&rp, m + 1));
+  CKT(dalloc(&col, nnz));
+  CKT(dalloc(&val, nnz));
+  CKT(dalloc(&c_in, n));
+  CKT(dalloc(&q_in, m));
+  CKT(dalloc(&l_in, n));
+  CKT(dalloc(&u_in, n));
+  CKT(dalloc(&flags, 1));
+  CKT(dalloc(&tmp, 1024));
+  CKT(cudaMemcpyAsync(rp64, lp->row_ptr, (m + 1) * sizeof(long long), kind, st));
+  if (nnz > 0) {
+    CKT(cudaMemcpyAsync(col, lp->col_idx, (size_t)nnz * sizeof(int), kind, st));
+    CKT(cudaMemcpyAsync(val, lp->val, (size_t)nnz * sizeof(double), kind, st));
+  }
+  CKT(cudaMemcpyAsync(c_in, lp->c, n * sizeof(double), kind, st));
+  if (m > 0) CKT(cudaMemcpyAsync(q_in, lp->rhs, m * sizeof(double), kind, st));
+  CKT(cudaMemcpyAsync(l_in, lp->l, n * sizeof(double), kind, st));
+  CKT(cudaMemcpyAsync(u_in, lp->u, n * sizeof(double), kind, st));
+  unsigned int vf = validate_problem(st, m, n, h->nnz, rp64, col, val, c_in, q_in, l_in, u_in,
+                                     flags);
+  CKT(cudaGetLastError());
+  if (vf) {
+    std::string msg = "invalid problem:";
+    if (vf & 1u) msg += " malformed row_ptr;";
+    if (vf & 2u) msg += " column index out of range or not strictly increasing in a row;";
+    if (vf & 4u) msg += " non-finite matrix value;";
+    if (vf & 8u) msg += " non-finite c or rhs;";
+    if (vf & 16u) msg += " NaN bound or l > u;";
+    if (vf & 32u) msg += " l = +inf or u = -inf;";
+    free_tmp();
+    h->err = msg;
+    return fail(RHPDHG_ERR_INVALID_ARG);
+  }
+  convert_row_ptr(st, m, rp64, rp);
+
+  // ---- transpose + scaling ----
+  CKT(dalloc(&cp, n + 1));
+  CKT(dalloc(&ridx, nnz));
+  CKT(dalloc(&cval, nnz));
+  CKT(build_transpose(st, m, n, nnz, rp, col, val, cp, ridx, cval));
+  CKT(dalloc(&h->D, m));
+  CKT(dalloc(&h->E, n));
+  CKT(dalloc(&h->Dinv, m));
+  CKT(dalloc(&h->Einv, n));
+  {
+    double *tm = nullptr, *tn = nullptr;
+    CKT(dalloc(&tm, m));
+    CKT(dalloc(&tn, n));
+    compute_scaling(st, m, n, rp, col, val, cp, ridx, cval, P.ruiz_iters, P.pock_chambolle_alpha,
+                    h->D, h->E, tm, tn);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(tm);
+    cudaFree(tn);
+    CKT(e);
+    CKT(cudaGetLastError());
+  }
+  // ---- layouts ----
+  {
+    std::vector<int> hrp(m + 1), hcp(n + 1);
+    CKT(cudaMemcpy(hrp.data(), rp, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    CKT(cudaMemcpy(hcp.data(), cp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    const int Lr = choose_short_threshold(hrp.data(), m);
+    const int Lc = choose_short_threshold(hcp.data(), n);
+    CKT(build_side<double>(st, m, nnz, rp, col, val, h->D, h->E, Lr, &h->rows));
+    CKT(build_side<double>(st, n, nnz, cp, ridx, cval, h->E, h->D, Lc, &h->cols));
+  }
+  // ---- scaled vectors ----
+  CKT(dalloc(&h->c, n));
+  CKT(dalloc(&h->q, m));
+  CKT(dalloc(&h->l, n));
+  CKT(dalloc(&h->u, n));
+  vmul(st, n, h->E, c_in, h->c, 0);
+  vmul(st, m, h->D, q_in, h->q, 0);
+  vmul(st, n, h->E, l_in, h->l, 1);
+  vmul(st, n, h->E, u_in, h->u, 1);
+  fill(st, m, 1.0, h->Dinv);
+  fill(st, n, 1.0, h->Einv);
+  vmul(st, m, h->D, h->Dinv, h->Dinv, 1);
+  vmul(st, n, h->E, h->Einv, h->Einv, 1);
+  // norms: ||c||, ||rhs|| (unscaled) and ||c^||, ||q^|| (scaled)
+  double *dn = nullptr;
+  CKT(dalloc(&dn, 8));
+  sumsq(st, n, c_in, dn + 0, tmp);
+  sumsq(st, m, q_in, dn + 1, tmp);
+  sumsq(st, n, h->c, dn + 2, tmp);
+  sumsq(st, m, h->q, dn + 3, tmp);
+  double hn[8] = {0};
+  CKT(cudaMemcpyAsync(hn, dn, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKT(cudaStreamSynchronize(st));
+  const double cn = std::sqrt(hn[0]), qn = std::sqrt(hn[1]);
+  const double chn = std::sqrt(hn[2]), qhn = std::sqrt(hn[3]);
+  free_tmp();
+
+  // ---- launch geometry ----
+  h->smem_row = kBlockWarps * kTileRows * h->rows.lay.L * (int)sizeof(double);
+  h->smem_col = kBlockWarps * kTileRows * h->cols.lay.L * (int)sizeof(double);
+  allow_large_smem(kMaxTileSmem);
+  allow_large_smem_setup(kMaxTileSmem);
+  h->grid_row = tile_grid(h->rows.lay, h->smem_row, h->sm_count, row_iter_blocks_per_sm(h->smem_row));
+  h->grid_col = tile_grid(h->cols.lay, h->smem_col, h->sm_count, col_iter_blocks_per_sm(h->smem_col));
+
+  // ---- power iteration for sigma_max(K^) ----
+  {
+    double *v = nullptr, *w = nullptr, *um = nullptr;
+    CKT(dalloc(&v, n));
+    CKT(dalloc(&w, n));
+    CKT(dalloc(&um, m));
+    CKT(dalloc(&tmp, 1024));
+    fill(st, n, 1.0 / std::sqrt((double)n), v);
+    for (int it = 0; it < P.power_iters; ++it) {
+      side_spmv(st, h->rows.lay, v, um, h->grid_row);
+      side_spmv(st, h->cols.lay, um, w, h->grid_col);
+      sumsq(st, n, w, dn + 4, tmp);
+      normalize(st, n, w, dn + 4, v);
+    }
+    side_spmv(st, h->rows.lay, v, um, h->grid_row);
+    sumsq(st, m, um, dn + 5, tmp);
+    double s2 = 0;
+    CKT(cudaMemcpyAsync(&s2, dn + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKT(cudaStreamSynchronize(st));
+    cudaFree(v);
+    cudaFree(w);
+    cudaFree(um);
+    cudaFree(tmp);
+    tmp = nullptr;
+    h->sigma_max = (m > 0 && h->nnz > 0) ? std::sqrt(s2) : 0.0;
+  }
+  cudaFree(dn);
+  if (P.step_size > 0) h->eta = P.step_size;
+  else if (h->sigma_max > 1e-12) h->eta = P.step_safety / h->sigma_max;
+  else h->eta = 1.0;
+  if (P.primal_weight > 0) h->omega0 = P.primal_weight;
+  else h->omega0 = (chn > 1e-10 && qhn > 1e-10) ? chn / qhn : 1.0;
+
+  // ---- iteration state ----
+  double **nv[] = {&h->x, &h->xt, &h->x0, &h->kty, &h->kty0, &h->xout, &h->certx, &h->x_init,
+                   &h->xres};
+  for (double **b : nv) CKC(dalloc(b, n));
+  double **mv[] = {&h->y, &h->yt, &h->y0, &h->kx, &h->kxt, &h->kx0, &h->certy, &h->y_init,
+                   &h->yres};
+  for (double **b : mv) CKC(dalloc(b, m));
+  CKC(cudaMemsetAsync(h->certx, 0, n * sizeof(double), st));
+  if (m) CKC(cudaMemsetAsync(h->certy, 0, m * sizeof(double), st));
+  CKC(dalloc(&h->ctl, 1));
+  CKC(cudaHostAlloc((void **)&h->h_mirror, 2 * sizeof(Ctl), cudaHostAllocDefault));
+  std::memset(h->h_mirror, 0, 2 * sizeof(Ctl));
+  CKC(dalloc(&h->part_row, (size_t)h->grid_row * kMaxPartials));
+  CKC(dalloc(&h->part_col, (size_t)h->grid_col * kMaxPartials));
+  if (P.trace && P.trace_capacity > 0) CKC(dalloc(&h->trace, (size_t)P.trace_capacity));
+  CKC(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), st));
+
+  // initial point z^{0,0}: the projection of 0 onto [l, u], or the warm start (scaled)
+  if (!h->h_x0.empty()) {
+    CKC(cudaMemcpyAsync(h->x_init, h->h_x0.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    vmul(st, n, h->E, h->x_init, h->x_init, 1);
+  } else {
+    fill(st, n, 0.0, h->x_init);
+    vclamp(st, n, h->x_init, h->l, h->u);
+  }
+  if (m) {
+    if (!h->h_y0.empty()) {
+      CKC(cudaMemcpyAsync(h->y_init, h->h_y0.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+      vmul(st, m, h->D, h->y_init, h->y_init, 1);
+    } else {
+      fill(st, m, 0.0, h->y_init);
+    }
+  }
+
+  IterConsts &ic = h->ic;
+  ic.m = m; ic.m_eq = h->m_eq; ic.n = n;
+  ic.rho2 = P.algorithm == 1 ? 1 : 0;
+  ic.max_iters = P.max_iters;
+  ic.check_every = P.check_every;
+  ic.first_epoch_len = P.first_epoch_len;
+  ic.max_epoch_len = P.max_epoch_len;
+  ic.restart_scheme = P.restart_scheme;
+  ic.pw_update = P.primal_weight_update;
+  ic.beta2 = P.restart_beta * P.restart_beta;
+  ic.eta = h->eta;
+  ic.eps_kkt = P.eps_rel_kkt;
+  ic.eps_infeas = P.eps_infeas;
+  ic.qn1 = 1.0 + qn;
+  ic.cn1 = 1.0 + cn;
+  ic.obj_offset = h->obj_offset;
+  ic.trace_cap = h->trace ? P.trace_capacity : 0;
+  ic.trace = h->trace;
+  h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv};
+  h->cv = ColVecs{h->x, h->xt, h->x0, h->kty, h->kty0, h->xout, h->certx, h->c, h->l, h->u,
+                  h->E, h->Einv};
+  algorithmic_bytes(h);
+  h->launches = launches_so_far() - launches0;
+  CKC(cudaStreamSynchronize(st));
+  CKC(cudaGetLastError());
+  *out = h;
+  return RHPDHG_OK;
+#undef CKC
+#undef CKT
+}
+
+int rhpdhg_solve(rhpdhg_handle *h, int blocking) {
+  if (!h) return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "handle is NULL");
+  if (h->running.load()) return set_err(h, RHPDHG_ERR_STATE, "a solve is already running");
+  if (h->th.joinable()) h->th.join();
+  h->cancel = 0;
+  h->drive_err = 0;
+  h->solved = false;
+  h->running = 1;
+  if (blocking) {
+    drive(h);
+    return h->drive_err ? h->drive_err : RHPDHG_OK;
+  }
+  h->th = std::thread(drive, h);
+  return RHPDHG_OK;
+}
+
+int rhpdhg_poll(rhpdhg_handle *h, rhpdhg_result *r) {
+  if (!h || !r) return set_err(h, RHPDHG_ERR_INVALID_ARG, "handle or result is NULL");
+  if (h->running.load()) return RHPDHG_BUSY;
+  if (h->th.joinable()) h->th.join();
+  if (!h->solved) return set_err(h, RHPDHG_ERR_STATE, "no solve has run");
+  if (h->drive_err) return h->drive_err;
+  const Ctl &c = h->final_ctl;
+  r->status = h->final_status;
+  r->iters = c.t;
+  r->restarts = c.n;
+  r->rel_p = c.rel_p;
+  r->rel_d = c.rel_d;
+  r->rel_gap = c.rel_gap;
+  r->primal_obj = c.pobj;
+  r->dual_obj = c.dobj;
+  r->solve_seconds = h->solve_seconds;
+  r->eta = h->eta;
+  r->omega = c.omega;
+  r->sigma_max = h->sigma_max;
+  const cudaMemcpyKind kind =
+      r->out_memory == RHPDHG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (r->x) CK(cudaMemcpyAsync(r->x, h->xres, h->n * sizeof(double), kind, h->st));
+  if (r->y && h->m) CK(cudaMemcpyAsync(r->y, h->yres, h->m * sizeof(double), kind, h->st));
+  if (r->cert_x) CK(cudaMemcpyAsync(r->cert_x, h->certx, h->n * sizeof(double), kind, h->st));
+  if (r->cert_y && h->m)
+    CK(cudaMemcpyAsync(r->cert_y, h->certy, h->m * sizeof(double), kind, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RHPDHG_OK;
+}
+
+int rhpdhg_cancel(rhpdhg_handle *h) {
+  if (!h) return RHPDHG_ERR_INVALID_ARG;
+  h->cancel = 1;
+  return RHPDHG_OK;
+}
+
+void rhpdhg_free(rhpdhg_handle *h) {
+  if (!h) return;
+  h->cancel = 1;
+  if (h->th.joinable()) h->th.join();
+  destroy(h);
+}
+
+int rhpdhg_get_state(const rhpdhg_handle *hc, int which, double *x, double *y) {
+  rhpdhg_handle *h = const_cast<rhpdhg_handle *>(hc);
+  if (!h) return RHPDHG_ERR_INVALID_ARG;
+  if (h->running.load()) return set_err(h, RHPDHG_ERR_STATE, "solve running");
+  const double *xs = nullptr, *ys = nullptr;
+  if (which == 1) { xs = h->xout; ys = h->yt; }
+  else if (which == 2) { xs = h->x0; ys = h->y0; }
+  else return set_err(h, RHPDHG_ERR_INVALID_ARG, "which must be 1 (PDHG point) or 2 (anchor)");
+  if (x) CK(cudaMemcpyAsync(x, xs, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (y && h->m) CK(cudaMemcpyAsync(y, ys, h->m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return RHPDHG_OK;
+}
+
+int rhpdhg_get_scaling(const rhpdhg_handle *hc, double *D, double *E, double *eta,
+                       double *omega0, double *sigma_max) {
+  rhpdhg_handle *h = const_cast<rhpdhg_handle *>(hc);
+  if (!h) return RHPDHG_ERR_INVALID_ARG;
+  if (h->running.load()) return set_err(h, RHPDHG_ERR_STATE, "solve running");
+  if (D && h->m) CK(cudaMemcpyAsync(D, h->D, h->m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (E) CK(cudaMemcpyAsync(E, h->E, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (eta) *eta = h->eta;
+  if (omega0) *omega0 = h->omega0;
+  if (sigma_max) *sigma_max = h->sigma_max;
+  return RHPDHG_OK;
+}
+
+int rhpdhg_get_trace(const rhpdhg_handle *hc, rhpdhg_trace_rec *recs, int64_t capacity,
+                     int64_t *count) {
+  rhpdhg_handle *h = const_cast<rhpdhg_handle *>(hc);
+  if (!h || !count) return RHPDHG_ERR_INVALID_ARG;
+  if (h->running.load()) return set_err(h, RHPDHG_ERR_STATE, "solve running");
+  if (!h->trace) { *count = 0; return RHPDHG_OK; }
+  long long iters = h->final_ctl.t;
+  long long cnt = std::min<long long>(iters, h->ic.trace_cap);
+  *count = cnt;
+  long long ncopy = std::min<long long>(cnt, capacity);
+  static_assert(sizeof(TraceRec) == sizeof(rhpdhg_trace_rec), "trace record layout");
+  if (recs && ncopy > 0)
+    CK(cudaMemcpy(recs, h->trace, ncopy * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+  return RHPDHG_OK;
+}
+
+int rhpdhg_kernel_times(const rhpdhg_handle *hc, double *ms_row, double *ms_col,
+                        int64_t *launches_row, int64_t *launches_col, double *bytes_row,
+                        double *bytes_col) {
+  const rhpdhg_handle *h = hc;
+  if (!h) return RHPDHG_ERR_INVALID_ARG;
+  if (ms_row) *ms_row = h->n_row ? h->ms_row / h->n_row : 0.0;
+  if (ms_col) *ms_col = h->n_col ? h->ms_col / h->n_col : 0.0;
+  if (launches_row) *launches_row = h->n_row;
+  if (launches_col) *launches_col = h->n_col;
+  if (bytes_row) *bytes_row = h->bytes_row;
+  if (bytes_col) *bytes_col = h->bytes_col;
+  return RHPDHG_OK;
+}
+
+int64_t rhpdhg_launch_count(const rhpdhg_handle *h) { return h ? h->launches : -1; }
+
+}  // extern "C"

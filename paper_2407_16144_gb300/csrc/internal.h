@@ -1,0 +1,94 @@
+// Launch wrappers shared between the translation units of the library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rh {
+
+// Owning device buffers of one side layout (see SideLayout).
+template <typename VT>
+struct SideStore {
+  SideLayout<VT> lay;
+  int *ptr_s = nullptr, *idx_s = nullptr, *long_rows = nullptr, *ptr_l = nullptr,
+      *idx_l = nullptr;
+  VT *val_s = nullptr, *val_l = nullptr;
+  uint32_t *long_mask = nullptr;
+  long long nnz_short = 0, nnz_long = 0;
+};
+
+struct RowVecs {      // m-vectors used by the row kernel (K^ x~ and the dual step)
+  double *y, *yt, *y0, *kx, *kxt, *kx0, *certy;
+  const double *q, *d, *dinv;
+};
+
+struct ColVecs {      // n-vectors used by the column kernel (K^T y~ and the primal step)
+  double *x, *xt, *x0, *kty, *kty0, *xout, *certx;
+  const double *c, *l, *u, *e, *einv;
+};
+
+// Process-wide count of kernels launched by this library's wrappers (for launch accounting).
+void count_launches(long long n);
+long long launches_so_far();
+
+// ---- setup (setup.cu) ------------------------------------------------------------------------
+// Validation of a device-resident problem: returns a bit mask of problems found (0 = valid).
+unsigned int validate_problem(cudaStream_t st, int m, int n, long long nnz, const long long *row_ptr,
+                              const int *col, const double *val, const double *c, const double *q,
+                              const double *l, const double *u, unsigned int *d_flags);
+// int64 -> int32 row pointers
+void convert_row_ptr(cudaStream_t st, int m, const long long *rp64, int *rp32);
+// CSR (m x n) -> CSC (column pointers, row indices, values), stable (rows ascending).
+// Returns cudaSuccess or an error.
+cudaError_t build_transpose(cudaStream_t st, int m, int n, int nnz, const int *rp, const int *col,
+                            const double *val, int *cp, int *ridx, double *cval);
+// Ruiz (ruiz_iters passes) then Pock-Chambolle (alpha; skipped when alpha < 0): fills D (m),
+// E (n) so that D K E is the scaled matrix.
+void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *col,
+                     const double *val, const int *cp, const int *ridx, const double *cval,
+                     int ruiz_iters, double alpha, double *D, double *E, double *tmp_m,
+                     double *tmp_n);
+// Build a split-CSR side layout from a CSR (nrows rows) with values scaled as
+// val * rscale[row] * cscale[col].  Allocates device buffers (cudaMalloc).
+template <typename VT>
+cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
+                       const double *val, const double *rscale, const double *cscale, int L,
+                       SideStore<VT> *out);
+template <typename VT>
+void free_side(SideStore<VT> *s);
+// Choose the short-row threshold L from the row-length distribution (host copy of ptr).
+int choose_short_threshold(const int *h_ptr, int nrows);
+// Launch geometry of the tile kernels for a side with L.
+int tile_grid(const SideLayout<double> &lay, int smem_bytes, int sm_count, int blocks_per_sm);
+// out = side * src   (plain product, FP64)
+void side_spmv(cudaStream_t st, const SideLayout<double> &lay, const double *src, double *out,
+               int grid);
+// deterministic sum of squares -> *out (device scalar); tmp holds >= 1024 doubles
+void sumsq(cudaStream_t st, int n, const double *x, double *out, double *tmp);
+// v = w / sqrt(*ss)
+void normalize(cudaStream_t st, int n, const double *w, const double *ss, double *v);
+void fill(cudaStream_t st, int n, double v, double *x);
+// y = a .* x (elementwise), optionally y = x ./ a when div = 1
+void vmul(cudaStream_t st, int n, const double *a, const double *x, double *y, int div);
+// x = clamp(x, l, u)
+void vclamp(cudaStream_t st, int n, double *x, const double *l, const double *u);
+
+// ---- iteration (iterate.cu) -----------------------------------------------------------------
+void launch_row_iter(cudaStream_t st, const SideLayout<double> &lay, const double *xt,
+                     const RowVecs &v, Ctl *ctl, double *part, const IterConsts &ic, int grid,
+                     int smem);
+void launch_col_iter(cudaStream_t st, const SideLayout<double> &lay, const double *yt,
+                     const ColVecs &v, Ctl *ctl, double *part, const IterConsts &ic, int grid,
+                     int smem, int phase);
+// x_out = E .* xout ; y_out = D .* yt
+void launch_unscale(cudaStream_t st, int n, int m, const double *e, const double *xs,
+                    const double *d, const double *ys, double *xo, double *yo);
+int row_iter_blocks_per_sm(int smem);
+// opt in to dynamic shared memory above 48 KB for the tile kernels
+void allow_large_smem(int bytes);
+void allow_large_smem_setup(int bytes);
+int col_iter_blocks_per_sm(int smem);
+
+}  // namespace rh

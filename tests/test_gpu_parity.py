@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.
+
+Tolerances (FP64 mode):
+  * scaling vectors D, E: 1e-12 relative (same operations, different rounding order);
+  * PDHG points (x~_t, y~_t) for t < 200: 1e-10 relative in the max norm, and the per-iteration
+    fixed-point residual ||z - T(z)||_P^2: 1e-10 relative; restart iterations identical (a
+    restart test within 1e-9 of its threshold is a tie and ends the comparison);
+  * solutions to tolerance: same status; objective within 1e-8 relative of the oracle's and of
+    the planted optimum at eps = 1e-8; the returned point's rel-KKT, recomputed on the host by
+    the oracle's checker, within the tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import rhpdhg_oracle as O
+from paper_2407_16144_gb300 import lpgen
+
+pytestmark = pytest.mark.gpu
+
+TIE = 1e-9
+
+
+@pytest.fixture(scope="module")
+def rh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_16144_gb300 import _build, rhpdhg
+    _build.build()
+    rhpdhg.load()
+    return rhpdhg
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    if a.size == 0:
+        return 0.0
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+def first_tie(trace, beta=math.exp(-1.0)):
+    """Index of the first iteration whose restart test is within TIE of its threshold."""
+    fpr0 = None
+    for idx, (t, n, k, f, rs, om) in enumerate(trace):
+        if k == 0:
+            fpr0 = f
+        if n >= 1 and fpr0 and abs(f / fpr0 - beta * beta) < TIE:
+            return idx
+    return len(trace)
+
+
+CASES = {
+    "c1": lambda: lpgen.make_c1(0),
+    "c2_small": lambda: lpgen.make_c2(1, scale=0.01),
+    "tiny_general": lambda: lpgen.make_tiny_general(2, 3, 4, 9),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_scaling_and_step_match_oracle(rh, case):
+    lp = CASES[case]()
+    with rh.Solver(lp) as s:
+        D, E, eta, om0, smax = s.scaling()
+    Kh, Do, Eo = O.scale_problem(O.csr_matrix(lp), 10, 1.0)
+    assert rel(D, Do) < 1e-12 and rel(E, Eo) < 1e-12
+    so = O.power_sigma_max(Kh, 100)
+    assert abs(smax - so) <= 1e-10 * so
+    assert abs(eta - 0.9 / so) <= 1e-10 * eta
+    c, q = Eo * lp.c, Do * lp.q
+    assert abs(om0 - np.linalg.norm(c) / np.linalg.norm(q)) <= 1e-12 * om0
+
+
+SNAP = [0, 1, 2, 3, 5, 10, 31, 62, 63, 64, 65, 100, 127, 128, 150, 199]
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("pw", [0, 1])
+@pytest.mark.parametrize("case", list(CASES))
+def test_iterates_match_oracle_first_200(rh, case, alg, pw):
+    lp = CASES[case]()
+    common = dict(algorithm=alg, eps_rel_kkt=1e-14, primal_weight_update=pw, first_epoch_len=20,
+                  check_every=16)
+    o = O.solve(lp, O.OracleParams(max_iters=200, **common), snapshot_iters=SNAP, trace=True)
+    with rh.Solver(lp, max_iters=200, trace=1, trace_capacity=256, **common) as s:
+        r = s.run()
+        tr = s.trace()
+        assert r.status == rh.STATUS_ITERATION_LIMIT and r.iters == 200
+        stop = min(first_tie(o.trace), first_tie(tr))
+        assert len(tr) == 200
+        for (a, b) in zip(tr[:stop], o.trace[:stop]):
+            assert a[:3] == b[:3]                                   # t, n, k
+            assert a[4] == b[4], f"restart flag differs at t={a[0]}"
+            assert abs(a[3] - b[3]) <= 1e-10 * max(abs(b[3]), 1e-300)
+            assert abs(a[5] - b[5]) <= 1e-10 * b[5]                  # omega
+    # PDHG points at the snapshot iterations: rerun with max_iters = t + 1
+    for t in SNAP:
+        if t >= stop:
+            break
+        with rh.Solver(lp, max_iters=t + 1, **common) as s:
+            r = s.run()
+            xt, yt = s.state(1)
+        assert r.iters == t + 1
+        sn = o.snapshots[t]
+        assert rel(xt, sn["xt"]) < 1e-10, (t, rel(xt, sn["xt"]))
+        assert rel(yt, sn["yt"]) < 1e-10, (t, rel(yt, sn["yt"]))
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("case", ["c1", "c2_small"])
+def test_solve_to_1e8_matches_oracle(rh, case, alg):
+    lp = CASES[case]()
+    o = O.solve(lp, O.OracleParams(algorithm=alg, eps_rel_kkt=1e-8, max_iters=200_000))
+    with rh.Solver(lp, algorithm=alg, eps_rel_kkt=1e-8) as s:
+        r = s.run()
+    assert r.status == rh.STATUS_OPTIMAL == o.status
+    assert abs(r.primal_obj - o.primal_obj) <= 1e-8 * (1 + abs(o.primal_obj))
+    ref = lp.planted_objective()
+    assert abs(r.primal_obj - ref) <= 1e-7 * (1 + abs(ref))
+    k = O.rel_kkt(lp, O.csr_matrix(lp), r.x, r.y)
+    assert k["rel_kkt"] <= 1e-8 * 1.0001
+    assert abs(k["rel_p"] - r.rel_p) <= 1e-6 * max(k["rel_p"], 1e-16) + 1e-15
+    # error of the GPU solution against the oracle's solution (reported, loose bound)
+    print(f"{case} alg={alg}: iters gpu {r.iters} oracle {o.iters}; |x-x_o|/|x_o| = "
+          f"{np.linalg.norm(r.x - o.x) / max(1, np.linalg.norm(o.x)):.2e}")
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_full_size_c2_first_iterations(rh, alg):
+    """The 100k x 250k (2.5M nnz) workload at full size, in the benchmark's launch
+    configuration: PDHG points of the first iterations against the oracle."""
+    lp = lpgen.make_c2(1)
+    T = 12
+    common = dict(algorithm=alg, eps_rel_kkt=1e-14, first_epoch_len=5, check_every=64)
+    o = O.solve(lp, O.OracleParams(max_iters=T, **common), snapshot_iters=[T - 1])
+    with rh.Solver(lp, max_iters=T, **common) as s:
+        r = s.run()
+        xt, yt = s.state(1)
+    assert r.iters == T
+    sn = o.snapshots[T - 1]
+    assert rel(xt, sn["xt"]) < 1e-10 and rel(yt, sn["yt"]) < 1e-10
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_infeasibility_certificates(rh, alg):
+    for kind in ("primal", "dual"):
+        lp = (lpgen.make_primal_infeasible(3, 500, 1000) if kind == "primal"
+              else lpgen.make_dual_infeasible(3, 500, 1000))
+        o = O.solve(lp, O.OracleParams(algorithm=alg, max_iters=50_000, max_epoch_len=200))
+        with rh.Solver(lp, algorithm=alg, max_iters=50_000, max_epoch_len=200) as s:
+            r = s.run()
+        K = O.csr_matrix(lp)
+        if kind == "primal":
+            assert r.status == rh.STATUS_PRIMAL_INFEASIBLE == o.status
+            by = lp.q @ r.cert_y
+            assert by > 0 and (K.T @ r.cert_y).max() / by <= 1e-8
+        else:
+            assert r.status == rh.STATUS_DUAL_INFEASIBLE == o.status
+            cd = lp.c @ r.cert_x
+            assert cd < 0 and np.abs(K @ r.cert_x).max() / -cd <= 1e-8
+            assert (-r.cert_x).max() / -cd <= 1e-8
+        print(f"{kind} alg={alg}: detected at {r.iters} (oracle {o.iters})")
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_box_lp_and_fig1(rh, alg):
+    lp = lpgen.make_box_lp(1, n=77)
+    with rh.Solver(lp, algorithm=alg, eps_rel_kkt=1e-12, check_every=8) as s:
+        r = s.run()
+    assert r.status == rh.STATUS_OPTIMAL
+    assert np.abs(r.x - np.where(lp.c > 0, lp.l, lp.u)).max() <= 1e-9
+    lp = lpgen.make_fig1_lp()
+    with rh.Solver(lp, algorithm=alg, eps_rel_kkt=1e-12, check_every=4) as s:
+        r = s.run()
+    assert r.status == rh.STATUS_OPTIMAL
+    assert abs(r.x[0] - 1.0) < 1e-10 and abs(r.y[0]) < 1e-10
+
+
+def test_empty_row_and_column(rh):
+    """A row with no entries and a column that appears in no row (degenerate structure)."""
+    base = lpgen.make_tiny_general(4, 2, 2, 6)
+    m, n = base.m + 1, base.n + 1
+    row_ptr = np.concatenate([base.row_ptr, [base.row_ptr[-1]]])      # empty last (>=) row
+    lp = lpgen.LP(m_eq=base.m_eq, m_ineq=base.m_ineq + 1, n=n, row_ptr=row_ptr,
+                  col_idx=base.col_idx, val=base.val, c=np.concatenate([base.c, [1.0]]),
+                  q=np.concatenate([base.q, [-1.0]]), l=np.concatenate([base.l, [0.0]]),
+                  u=np.concatenate([base.u, [2.0]]))
+    o = O.solve(lp, O.OracleParams(algorithm=1, eps_rel_kkt=1e-10, max_iters=100_000))
+    with rh.Solver(lp, algorithm=1, eps_rel_kkt=1e-10) as s:
+        r = s.run()
+    assert r.status == o.status == rh.STATUS_OPTIMAL
+    assert abs(r.primal_obj - o.primal_obj) <= 1e-8 * (1 + abs(o.primal_obj))
+    assert abs(r.x[-1]) < 1e-8                                        # c_j = 1 > 0, l_j = 0
+
+
+def test_invalid_problems_rejected(rh):
+    lp = lpgen.make_c1(0)
+    bad = lpgen.make_c1(0)
+    bad.col_idx = bad.col_idx.copy()
+    s0, s1 = bad.row_ptr[3], bad.row_ptr[4]
+    bad.col_idx[s0:s1] = bad.col_idx[s0:s1][::-1]                      # unsorted row
+    with pytest.raises(rh.RHPDHGError, match="strictly increasing"):
+        rh.Solver(bad)
+    bad = lpgen.make_c1(0)
+    bad.val = bad.val.copy()
+    bad.val[7] = np.nan
+    with pytest.raises(rh.RHPDHGError, match="non-finite"):
+        rh.Solver(bad)
+    bad = lpgen.make_c1(0)
+    bad.l = bad.l.copy()
+    bad.l[3] = 5.0
+    bad.u = bad.u.copy()
+    bad.u[3] = 1.0
+    with pytest.raises(rh.RHPDHGError, match="l > u"):
+        rh.Solver(bad)
+    bad = lpgen.make_c1(0)
+    bad.col_idx = bad.col_idx.copy()
+    bad.col_idx[0] = lp.n + 4
+    with pytest.raises(rh.RHPDHGError, match="out of range"):
+        rh.Solver(bad)
+
+
+def test_warm_start_at_planted_optimum(rh):
+    lp = lpgen.make_c1(0)
+    with rh.Solver(lp, eps_rel_kkt=1e-9, x0=lp.x_star, y0=lp.y_star) as s:
+        r = s.run()
+    assert r.status == rh.STATUS_OPTIMAL and r.iters == 64
+
+
+def test_device_input_equals_host_input(rh):
+    import torch
+    lp = lpgen.make_c2(2, scale=0.01)
+    dev = lpgen.LP(**{f: (torch.as_tensor(getattr(lp, f), device="cuda")
+                          if isinstance(getattr(lp, f), np.ndarray) else getattr(lp, f))
+                      for f in ("m_eq", "m_ineq", "n", "row_ptr", "col_idx", "val", "c", "q",
+                                "l", "u")})
+    with rh.Solver(lp, eps_rel_kkt=1e-7) as s:
+        a = s.run()
+    with rh.Solver(dev, device=True, stream=torch.cuda.current_stream().cuda_stream,
+                   eps_rel_kkt=1e-7) as s:
+        s.solve(1)
+        xo = torch.empty(lp.n, dtype=torch.float64, device="cuda")
+        yo = torch.empty(lp.m, dtype=torch.float64, device="cuda")
+        b = s.poll(x=xo, y=yo, out_memory=rh.MEM_DEVICE)
+    assert a.iters == b.iters and a.primal_obj == b.primal_obj
+    assert np.array_equal(a.x, xo.cpu().numpy()) and np.array_equal(a.y, yo.cpu().numpy())
+
+
+def test_deterministic_and_profile_mode_identical(rh):
+    lp = lpgen.make_c2(3, scale=0.01)
+    outs = []
+    for prof in (0, 0, 1):
+        with rh.Solver(lp, eps_rel_kkt=1e-7, profile=prof) as s:
+            r = s.run()
+            kt = s.kernel_times()
+        outs.append(r)
+        if prof:
+            assert kt["launches_row"] == r.iters and kt["ms_row"] > 0 and kt["ms_col"] > 0
+    for r in outs[1:]:
+        assert r.iters == outs[0].iters and np.array_equal(r.x, outs[0].x)
+        assert np.array_equal(r.y, outs[0].y)
+
+
+def test_nonblocking_poll_cancel_and_limits(rh):
+    lp = lpgen.make_c2(1, scale=0.05)
+    with rh.Solver(lp, eps_rel_kkt=1e-15, max_iters=10_000_000) as s:
+        for _ in range(2):                              # a handle can solve again
+            s.solve(0)
+            assert s.poll() is None                     # BUSY while running
+            s.cancel()
+            r = None
+            while r is None:
+                r = s.poll()
+            assert r.status == rh.STATUS_CANCELLED
+    with rh.Solver(lp, eps_rel_kkt=1e-15, time_limit_s=0.05) as s:
+        r = s.run()
+        assert r.status == rh.STATUS_TIME_LIMIT
+    with rh.Solver(lp, eps_rel_kkt=1e-15, max_iters=1000) as s:
+        r = s.run()
+        assert r.status == rh.STATUS_ITERATION_LIMIT and r.iters == 1000
