@@ -38,7 +38,7 @@ struct rhpdhg_handle {
   rhpdhg_params p{};
   std::vector<double> h_x0, h_y0;
 
-  SideStore<double> rows, cols;
+  SideStore rows, cols;
   double *D = nullptr, *E = nullptr, *Dinv = nullptr, *Einv = nullptr;
   double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr;
   double *x = nullptr, *xt = nullptr, *x0 = nullptr, *kty = nullptr, *kty0 = nullptr,
@@ -46,6 +46,15 @@ struct rhpdhg_handle {
   double *y = nullptr, *yt = nullptr, *y0 = nullptr, *kx = nullptr, *kxt = nullptr,
          *kx0 = nullptr, *certy = nullptr;
   double *x_init = nullptr, *y_init = nullptr, *xres = nullptr, *yres = nullptr;
+  // mixed precision: FP32 offsets and anchor images
+  bool mixed = false;
+  float *dxt = nullptr, *dx = nullptr, *ktdy = nullptr, *s0 = nullptr, *xlo = nullptr,
+        *xhi = nullptr;
+  float *dyt = nullptr, *kdxt = nullptr, *dy = nullptr, *kdx = nullptr, *r0 = nullptr,
+        *ylo = nullptr;
+  double *dxt64 = nullptr, *dyt64 = nullptr;
+  RowVecsMx rvm{};
+  ColVecsMx cvm{};
   Ctl *ctl = nullptr;
   Ctl *h_mirror = nullptr;   // two pinned host mirrors of the control block
   double *part_row = nullptr, *part_col = nullptr;
@@ -106,8 +115,11 @@ void destroy(rhpdhg_handle *h) {
   double *bufs[] = {h->D, h->E, h->Dinv, h->Einv, h->c, h->q, h->l, h->u, h->x, h->xt, h->x0,
                     h->kty, h->kty0, h->xout, h->certx, h->y, h->yt, h->y0, h->kx, h->kxt,
                     h->kx0, h->certy, h->x_init, h->y_init, h->xres, h->yres, h->part_row,
-                    h->part_col};
+                    h->part_col, h->dxt64, h->dyt64};
   for (double *b : bufs) cudaFree(b);
+  float *fbufs[] = {h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi,
+                    h->dyt, h->kdxt, h->dy, h->kdx, h->r0, h->ylo};
+  for (float *b : fbufs) cudaFree(b);
   cudaFree(h->ctl);
   cudaFree(h->trace);
   if (h->h_mirror) cudaFreeHost(h->h_mirror);
@@ -118,9 +130,21 @@ void destroy(rhpdhg_handle *h) {
 // Algorithmic bytes one launch of each iteration kernel moves (FP64, reflected or not): the
 // side's values and indices, row pointers, the gathered vector once, and the streamed vectors.
 void algorithmic_bytes(rhpdhg_handle *h) {
-  const double vb = 8.0, ib = 4.0;
+  const double ib = 4.0;
   const int rho2 = h->ic.rho2;
   const double nnz = (double)h->nnz;
+  if (h->mixed) {
+    // FP32 values; row kernel reads dyt, kdxt, r0, ylo (+ dy, kdx), writes dyt, kdxt (+ dy, kdx),
+    // gathers dxt; column kernel reads dxt, s0, xlo, xhi (+ dx, ktdy), writes dxt (+ dx, ktdy),
+    // gathers dyt.  (Restart iterations add the FP64 anchor products; not counted here.)
+    const double fb = 4.0;
+    h->bytes_row = nnz * (fb + ib) + (h->m + 1) * ib + h->n * fb +
+                   h->m * fb * ((4 + 2 * rho2) + (2 + 2 * rho2));
+    h->bytes_col = nnz * (fb + ib) + (h->n + 1) * ib + h->m * fb +
+                   h->n * fb * ((4 + 2 * rho2) + (1 + 2 * rho2));
+    return;
+  }
+  const double vb = 8.0;
   // row kernel: reads y~, y0, Kx~, Kx0, q (+ y, Kx for rho=2), writes y~, Kx~ (+ y, Kx)
   const double row_vec = (5 + 2 * rho2) + (2 + 2 * rho2);
   h->bytes_row = nnz * (vb + ib) + (h->m + 1) * ib + h->n * vb + h->m * vb * row_vec;
@@ -129,11 +153,27 @@ void algorithmic_bytes(rhpdhg_handle *h) {
   h->bytes_col = nnz * (vb + ib) + (h->n + 1) * ib + h->m * vb + h->n * vb * col_vec;
 }
 
+void launch_row(rhpdhg_handle *h) {
+  if (h->mixed)
+    launch_row_iter_mx(h->st, h->rows, h->rvm, h->dxt, h->dxt64, h->x0, h->ctl, h->part_row,
+                       h->ic, h->grid_row, h->smem_row);
+  else
+    launch_row_iter(h->st, h->rows, h->xt, h->rv, h->ctl, h->part_row, h->ic, h->grid_row,
+                    h->smem_row);
+}
+
+void launch_col(rhpdhg_handle *h, int phase) {
+  if (h->mixed)
+    launch_col_iter_mx(h->st, h->cols, h->cvm, h->dyt, h->dyt64, h->y0, h->ctl, h->part_col,
+                       h->ic, h->grid_col, h->smem_col, phase);
+  else
+    launch_col_iter(h->st, h->cols, h->yt, h->cv, h->ctl, h->part_col, h->ic, h->grid_col,
+                    h->smem_col, phase);
+}
+
 void launch_iteration(rhpdhg_handle *h) {
-  launch_row_iter(h->st, h->rows.lay, h->xt, h->rv, h->ctl, h->part_row, h->ic, h->grid_row,
-                  h->smem_row);
-  launch_col_iter(h->st, h->cols.lay, h->yt, h->cv, h->ctl, h->part_col, h->ic, h->grid_col,
-                  h->smem_col, 0);
+  launch_row(h);
+  launch_col(h, 0);
 }
 
 int capture_graphs(rhpdhg_handle *h) {
@@ -162,14 +202,27 @@ int reset_state(rhpdhg_handle *h) {
   c.sigma = h->eta * h->omega0;
   c.eta = h->eta;
   CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
+  if (h->mixed) {
+    // anchors z^{0,0}, zero offsets; the set-up column kernel runs in restart mode and forms
+    // K^T y0, the anchor images and dxt_0; the first row kernel forms K x0 likewise
+    CK(cudaMemcpyAsync(h->x0, h->x_init, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    if (h->m > 0)
+      CK(cudaMemcpyAsync(h->y0, h->y_init, h->m * sizeof(double), cudaMemcpyDeviceToDevice,
+                         h->st));
+    float *zn[] = {h->dxt, h->dx, h->ktdy};
+    for (float *z : zn) zero_f32(h->st, h->n, z);
+    float *zm[] = {h->dyt, h->kdxt, h->dy, h->kdx};
+    for (float *z : zm) zero_f32(h->st, h->m, z);
+    launch_col(h, 1);
+    return RHPDHG_OK;
+  }
   CK(cudaMemcpyAsync(h->xt, h->x_init, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   if (h->m > 0)
     CK(cudaMemcpyAsync(h->yt, h->y_init, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   // K x^{0,0} into the PDHG-point product slot; the first row kernel takes it as K x_0
-  side_spmv(h->st, h->rows.lay, h->x_init, h->kxt, h->grid_row);
+  side_spmv(h->st, h->rows, h->x_init, h->kxt, h->grid_row);
   // the column kernel in set-up phase forms x_0 = x^{0,0}, K^T y_0 and x~_0
-  launch_col_iter(h->st, h->cols.lay, h->yt, h->cv, h->ctl, h->part_col, h->ic, h->grid_col,
-                  h->smem_col, 1);
+  launch_col(h, 1);
   CK(cudaGetLastError());
   return RHPDHG_OK;
 }
@@ -179,7 +232,7 @@ void drive(rhpdhg_handle *h) {
   cudaSetDevice(h->dev);
   Timer timer;
   int rc = reset_state(h);
-  h->launches += 2;      // K x^{0,0} and the set-up column kernel
+  h->launches += h->mixed ? 8 : 2;   // set-up kernels of the solve
   const bool graphs = h->p.use_graphs && !h->p.profile;
   if (rc == RHPDHG_OK && graphs) rc = capture_graphs(h);
   if (rc != RHPDHG_OK) {
@@ -216,11 +269,9 @@ void drive(rhpdhg_handle *h) {
       } else {
         for (int i = 0; i < h->p.check_every; ++i) {
           if (h->p.profile) cudaEventRecord(pev[3 * i], h->st);
-          launch_row_iter(h->st, h->rows.lay, h->xt, h->rv, h->ctl, h->part_row, h->ic,
-                          h->grid_row, h->smem_row);
+          launch_row(h);
           if (h->p.profile) cudaEventRecord(pev[3 * i + 1], h->st);
-          launch_col_iter(h->st, h->cols.lay, h->yt, h->cv, h->ctl, h->part_col, h->ic,
-                          h->grid_col, h->smem_col, 0);
+          launch_col(h, 0);
           if (h->p.profile) cudaEventRecord(pev[3 * i + 2], h->st);
         }
         cudaMemcpyAsync(h->h_mirror + g, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
@@ -263,7 +314,11 @@ void drive(rhpdhg_handle *h) {
   h->final_ctl = fin;
   h->final_status = fin.status != kRunning ? fin.status : host_status;
   if (h->final_status == kRunning) h->final_status = kNumericalError;
-  launch_unscale(h->st, h->n, h->m, h->E, h->xout, h->D, h->yt, h->xres, h->yres);
+  if (h->mixed)
+    launch_unscale_mx(h->st, h->n, h->m, h->E, h->xout, h->D, h->y0, h->dyt, h->xres, h->yres,
+                      h->yt);
+  else
+    launch_unscale(h->st, h->n, h->m, h->E, h->xout, h->D, h->yt, h->xres, h->yres);
   h->launches += 1;
   // time / cancel stops happen at a chunk boundary, right after a check iteration, so xout
   // and y~ hold the PDHG point of that check
@@ -336,7 +391,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   if (!lp->row_ptr || !lp->c || !lp->l || !lp->u || (m > 0 && !lp->rhs) ||
       (lp->nnz > 0 && (!lp->col_idx || !lp->val)))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "missing problem array");
-  if (P.algorithm < 0 || P.algorithm > 1 || P.precision != 0 || P.check_every < 1 ||
+  if (P.algorithm < 0 || P.algorithm > 1 || P.precision < 0 || P.precision > 1 || P.check_every < 1 ||
       P.max_iters < 1 || !(P.eps_rel_kkt > 0) || !(P.eps_infeas > 0) || P.ruiz_iters < 0 ||
       P.power_iters < 1 || P.step_size < 0 || !(P.step_safety > 0) || P.primal_weight < 0 ||
       P.first_epoch_len < 0 || P.max_epoch_len < 0 || P.restart_scheme < 0 ||
@@ -347,6 +402,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
 
   h = new rhpdhg_handle();
   h->p = P;
+  h->mixed = P.precision == 1;
   h->m = m;
   h->m_eq = lp->m_eq;
   h->m_ineq = lp->m_ineq;
@@ -475,8 +531,9 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     CKT(cudaMemcpy(hcp.data(), cp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
     const int Lr = choose_short_threshold(hrp.data(), m);
     const int Lc = choose_short_threshold(hcp.data(), n);
-    CKT(build_side<double>(st, m, nnz, rp, col, val, h->D, h->E, Lr, &h->rows));
-    CKT(build_side<double>(st, n, nnz, cp, ridx, cval, h->E, h->D, Lc, &h->cols));
+    const bool with32 = P.precision == 1;
+    CKT(build_side(st, m, nnz, rp, col, val, h->D, h->E, Lr, with32, &h->rows));
+    CKT(build_side(st, n, nnz, cp, ridx, cval, h->E, h->D, Lc, with32, &h->cols));
   }
   // ---- scaled vectors ----
   CKT(dalloc(&h->c, n));
@@ -510,8 +567,14 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   h->smem_col = kBlockWarps * kTileRows * h->cols.lay.L * (int)sizeof(double);
   allow_large_smem(kMaxTileSmem);
   allow_large_smem_setup(kMaxTileSmem);
-  h->grid_row = tile_grid(h->rows.lay, h->smem_row, h->sm_count, row_iter_blocks_per_sm(h->smem_row));
-  h->grid_col = tile_grid(h->cols.lay, h->smem_col, h->sm_count, col_iter_blocks_per_sm(h->smem_col));
+  allow_large_smem_mx(kMaxTileSmem);
+  if (h->mixed) {
+    h->grid_row = tile_grid(h->rows.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_row));
+    h->grid_col = tile_grid(h->cols.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_col));
+  } else {
+    h->grid_row = tile_grid(h->rows.lay, h->sm_count, row_iter_blocks_per_sm(h->smem_row));
+    h->grid_col = tile_grid(h->cols.lay, h->sm_count, col_iter_blocks_per_sm(h->smem_col));
+  }
 
   // ---- power iteration for sigma_max(K^) ----
   {
@@ -522,12 +585,12 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     CKT(dalloc(&tmp, 1024));
     fill(st, n, 1.0 / std::sqrt((double)n), v);
     for (int it = 0; it < P.power_iters; ++it) {
-      side_spmv(st, h->rows.lay, v, um, h->grid_row);
-      side_spmv(st, h->cols.lay, um, w, h->grid_col);
+      side_spmv(st, h->rows, v, um, h->grid_row);
+      side_spmv(st, h->cols, um, w, h->grid_col);
       sumsq(st, n, w, dn + 4, tmp);
       normalize(st, n, w, dn + 4, v);
     }
-    side_spmv(st, h->rows.lay, v, um, h->grid_row);
+    side_spmv(st, h->rows, v, um, h->grid_row);
     sumsq(st, m, um, dn + 5, tmp);
     double s2 = 0;
     CKT(cudaMemcpyAsync(&s2, dn + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -553,6 +616,14 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   double **mv[] = {&h->y, &h->yt, &h->y0, &h->kx, &h->kxt, &h->kx0, &h->certy, &h->y_init,
                    &h->yres};
   for (double **b : mv) CKC(dalloc(b, m));
+  if (h->mixed) {
+    float **fn[] = {&h->dxt, &h->dx, &h->ktdy, &h->s0, &h->xlo, &h->xhi};
+    for (float **b : fn) CKC(dalloc(b, n));
+    float **fm[] = {&h->dyt, &h->kdxt, &h->dy, &h->kdx, &h->r0, &h->ylo};
+    for (float **b : fm) CKC(dalloc(b, m));
+    CKC(dalloc(&h->dxt64, n));
+    CKC(dalloc(&h->dyt64, m));
+  }
   CKC(cudaMemsetAsync(h->certx, 0, n * sizeof(double), st));
   if (m) CKC(cudaMemsetAsync(h->certy, 0, m * sizeof(double), st));
   CKC(dalloc(&h->ctl, 1));
@@ -601,6 +672,10 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv};
   h->cv = ColVecs{h->x, h->xt, h->x0, h->kty, h->kty0, h->xout, h->certx, h->c, h->l, h->u,
                   h->E, h->Einv};
+  h->rvm = RowVecsMx{h->dyt, h->kdxt, h->dy, h->kdx, h->r0, h->ylo, h->y0, h->kx0, h->certy,
+                     h->dyt64, h->q, h->D, h->Dinv};
+  h->cvm = ColVecsMx{h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi, h->x0, h->kty0, h->xout,
+                     h->certx, h->dxt64, h->c, h->l, h->u, h->E, h->Einv};
   algorithmic_bytes(h);
   h->launches = launches_so_far() - launches0;
   CKC(cudaStreamSynchronize(st));

@@ -28,29 +28,49 @@ constexpr int kBlockThreads = kBlockWarps * kWarp;
 constexpr int kMaxPartials = 16;       // reduction slots per CTA
 constexpr int kMaxTileL = 64;          // largest short-row threshold
 constexpr int kMaxTileSmem = kBlockWarps * kTileRows * kMaxTileL * 8;   // bytes
+constexpr int kChunk = 256;            // entries per long-row chunk (8 per lane)
+constexpr int kStageUnroll = 4;        // independent gathers in flight per lane
 
 enum Status : int {
   kRunning = 0, kOptimal = 1, kPrimalInfeasible = 2, kDualInfeasible = 3, kIterLimit = 4,
   kTimeLimit = 5, kNumericalError = 6, kCancelled = 7
 };
 
-// Split-CSR layout of one side (see file comment).  Values are the scaled matrix entries.
-template <typename VT>
+// Split-CSR structure of one side (see file comment).  The values live in separate arrays
+// (FP64 and, for the mixed-precision path, FP32 copies share this structure).  Long rows are
+// further cut into chunks of at most kChunk entries; a chunk is one warp task.
 struct SideLayout {
   int nrows = 0;
   int L = 32;                // short-row threshold: rows with <= L entries are short
   int n_short_tiles = 0;     // ceil(nrows / 32)
   int n_long = 0;            // number of long rows
-  int n_long_tiles = 0;      // ceil(n_long / 32)
+  int n_long_tiles = 0;      // ceil(n_long / 32): groups of 32 long rows sharing an epilogue
+  int n_chunks = 0;          // chunks of the long rows
   const int *ptr_s = nullptr;       // nrows + 1
   const int *idx_s = nullptr;       // nnz_short
-  const VT *val_s = nullptr;        // nnz_short
   const uint32_t *long_mask = nullptr;  // n_short_tiles words: bit r set if row 32t+r is long
   const int *long_rows = nullptr;   // n_long row ids (ascending)
   const int *ptr_l = nullptr;       // n_long + 1
   const int *idx_l = nullptr;       // nnz_long
-  const VT *val_l = nullptr;        // nnz_long
-  __host__ __device__ int total_tiles() const { return n_short_tiles + n_long_tiles; }
+  const int *chunk_ptr = nullptr;   // n_long + 1: chunks of long row i are [chunk_ptr[i], ..[i+1])
+  const int *chunk_row = nullptr;   // n_chunks: long-row index of each chunk
+  __host__ __device__ int total_items() const { return n_chunks + n_short_tiles; }
+};
+
+// Values of one side in one precision.
+template <typename VT>
+struct SideVals {
+  const VT *s = nullptr;     // nnz_short
+  const VT *l = nullptr;     // nnz_long
+};
+
+// Per-walk scratch: chunk partial sums and group tickets (kept at zero between launches).  Two
+// walks in the same kernel use two disjoint scratch sets.
+struct WalkScratch {
+  double *chunk_part = nullptr;       // n_chunks
+  unsigned int *group_done = nullptr; // n_long_tiles
+  double *group_part = nullptr;       // n_long_tiles * kMaxPartials: reduction slots of the
+                                      // long-row epilogues of each group (see walk_tiles)
 };
 
 // Device control block.  Written only by the last CTA of a kernel (or by the host while no
@@ -174,20 +194,47 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, double *part, unsigned int
   return last;
 }
 
-// In the last CTA: reduce the grid's partials in block order.  out[i] valid in all threads.
+// Warp-collective: reduce the long-row accumulator al of every lane and store it as group grp's
+// partials (lane 0), then clear al.
 template <int NS, int NM>
-__device__ void grid_finish(const double *part, double *out) {
+__device__ __forceinline__ void store_group(Acc<NS, NM> &al, double *gpart, int grp) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const double v = warp_sum(al.s[i]);
+    if (lane == 0) gpart[(size_t)grp * kMaxPartials + i] = v;
+  }
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    const double v = warp_max(al.mx[i]);
+    if (lane == 0) gpart[(size_t)grp * kMaxPartials + NS + i] = v;
+  }
+  al.zero();
+}
+
+// In the last CTA: reduce the grid's partials in block order, then the long-row groups'
+// partials in group order.  out[i] valid in all threads.
+template <int NS, int NM>
+__device__ void grid_finish(const double *part, double *out, const double *gpart = nullptr,
+                            int ngroups = 0) {
   __shared__ double red[kBlockWarps][kMaxPartials];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = gridDim.x;
   double v[NS + NM];
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) v[i] = 0.0;
-  // thread t sums blocks t, t + blockDim, ... (fixed order)
+  // thread t sums blocks t, t + blockDim, ... then groups t, t + blockDim, ... (fixed order)
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
 #pragma unroll
     for (int i = 0; i < NS + NM; ++i) {
       double p = __ldcg(part + (size_t)b * kMaxPartials + i);
+      v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
+    }
+  }
+  for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < NS + NM; ++i) {
+      double p = __ldcg(gpart + (size_t)g * kMaxPartials + i);
       v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
     }
   }
@@ -213,35 +260,74 @@ __device__ void grid_finish(const double *part, double *out) {
 
 // ---------------------------------------------------------------------------------------------
 // The tile walker: computes dot = (row of the side operator) . src for every row and calls
-// epi(row, dot) once per row, from one lane.  SrcT is the gathered vector type, VT the value
-// type, PT the product/accumulator type.  smem points to this warp's staging area of at least
-// 32 * L elements of PT.
+// epi(row, dot) once per row, from one lane, 32 rows per warp at a time.  Work items are the
+// chunks of the long rows followed by the short-row tiles, distributed over all warps of the
+// grid in a fixed order (so two walks over the same structure give every row to the same warp
+// and lane).  A chunk's warp sums its entries (fixed shuffle tree) into chunk_part; the warp
+// that completes the last chunk of a group of 32 long rows (ticket in group_done, no waiting)
+// adds each row's chunk partials in chunk order and runs the 32 epilogues lane-parallel.  A short
+// tile stages the products of its contiguous entry segment in shared memory, then lane r sums
+// row r's products in column order.  VT is the value type, PT the product/accumulator type;
+// src(j) returns the gathered vector entry; smem is this warp's staging area of 32 * L PTs.
 
-template <typename VT, typename SrcT, typename PT, typename Epi>
-__device__ __forceinline__ void walk_tiles(const SideLayout<VT> &lay, const SrcT *__restrict__ src,
-                                           PT *smem, Epi &epi) {
+template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone>
+__device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals<VT> vals,
+                                           const Src &src, PT *smem, const WalkScratch ws,
+                                           Epi &epi, GroupDone &gdone) {
   const int lane = threadIdx.x & 31;
   const int gwarp = blockIdx.x * kBlockWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kBlockWarps;
-  const int total = lay.total_tiles();
-  for (int tile = gwarp; tile < total; tile += nwarps) {
-    if (tile < lay.n_long_tiles) {
-      // long rows: a whole warp per row, results collected one per lane
-      const int base = tile * kTileRows;
-      const int cnt = min(kTileRows, lay.n_long - base);
-      PT mine = PT(0);
-      int my_row = -1;
-      for (int i = 0; i < cnt; ++i) {
-        const int b = lay.ptr_l[base + i], e = lay.ptr_l[base + i + 1];
-        PT s = PT(0);
-        for (int p = b + lane; p < e; p += kWarp)
-          s += PT(lay.val_l[p]) * PT(src[lay.idx_l[p]]);
-        s = warp_sum(s);
-        if (lane == i) { mine = s; my_row = lay.long_rows[base + i]; }
+  const int total = lay.total_items();
+  for (int item = gwarp; item < total; item += nwarps) {
+    if (item < lay.n_chunks) {
+      const int li = lay.chunk_row[item];
+      const int c0 = lay.chunk_ptr[li];
+      const int re = lay.ptr_l[li + 1];
+      const int cb = lay.ptr_l[li] + (item - c0) * kChunk;
+      const int ce = min(cb + kChunk, re);
+      PT s = PT(0);
+      int jj[kChunk / kWarp];
+      VT vv[kChunk / kWarp];
+#pragma unroll
+      for (int u = 0; u < kChunk / kWarp; ++u) {
+        const int p = cb + u * kWarp + lane;
+        jj[u] = p < ce ? lay.idx_l[p] : 0;
+        vv[u] = p < ce ? vals.l[p] : VT(0);
       }
-      if (my_row >= 0) epi(my_row, mine);
+#pragma unroll
+      for (int u = 0; u < kChunk / kWarp; ++u) {
+        const int p = cb + u * kWarp + lane;
+        if (p < ce) s += PT(vv[u]) * PT(src(jj[u]));
+      }
+      s = warp_sum(s);
+      const int grp = li / kTileRows;
+      const int g0 = grp * kTileRows;
+      const int g1 = min(g0 + kTileRows, lay.n_long);
+      int fin = 0;
+      if (lane == 0) {
+        ws.chunk_part[item] = (double)s;
+        __threadfence();
+        const unsigned int need = (unsigned int)(lay.chunk_ptr[g1] - lay.chunk_ptr[g0]);
+        const unsigned int old = atomicAdd(ws.group_done + grp, 1u);
+        fin = (old == need - 1) ? 1 : 0;
+      }
+      fin = __shfl_sync(0xffffffffu, fin, 0);
+      if (fin) {
+        __threadfence();
+        const int lr = g0 + lane;
+        if (lr < g1) {
+          PT d = PT(0);
+          for (int c = lay.chunk_ptr[lr]; c < lay.chunk_ptr[lr + 1]; ++c)
+            d += PT(__ldcg(ws.chunk_part + c));
+          epi(lay.long_rows[lr], d, true);
+        }
+        // the finishing warp varies from run to run: the group's reduction contributions go
+        // to the group's own slots, which the last CTA adds in group order
+        gdone(grp);
+        if (lane == 0) ws.group_done[grp] = 0u;
+      }
     } else {
-      const int st = tile - lay.n_long_tiles;
+      const int st = item - lay.n_chunks;
       const int row0 = st * kTileRows;
       const int nr = min(kTileRows, lay.nrows - row0);
       // row pointers: lane r holds ptr_s[row0 + r] (clamped to the tile end)
@@ -251,15 +337,35 @@ __device__ __forceinline__ void walk_tiles(const SideLayout<VT> &lay, const SrcT
       const int rb = pl;
       int re = __shfl_down_sync(0xffffffffu, pl, 1);
       if (lane == kWarp - 1) re = seg_e;
-      // stage the products of the tile's segment (coalesced value / index loads)
-      for (int p = seg_b + lane; p < seg_e; p += kWarp)
-        smem[p - seg_b] = PT(lay.val_s[p]) * PT(src[lay.idx_s[p]]);
+      // stage the products of the tile's segment: coalesced value / index loads, kStageUnroll
+      // independent gathers in flight per lane
+      for (int base = seg_b; base < seg_e; base += kWarp * kStageUnroll) {
+        int jj[kStageUnroll];
+        VT vv[kStageUnroll];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+          const int p = base + u * kWarp + lane;
+          jj[u] = p < seg_e ? lay.idx_s[p] : 0;
+          vv[u] = p < seg_e ? vals.s[p] : VT(0);
+        }
+        PT xs[kStageUnroll];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+          const int p = base + u * kWarp + lane;
+          xs[u] = p < seg_e ? PT(src(jj[u])) : PT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+          const int p = base + u * kWarp + lane;
+          if (p < seg_e) smem[p - seg_b] = PT(vv[u]) * xs[u];
+        }
+      }
       __syncwarp();
       const uint32_t lm = lay.long_mask[st];
       if (lane < nr && !((lm >> lane) & 1u)) {
         PT s = PT(0);
         for (int p = rb; p < re; ++p) s += smem[p - seg_b];
-        epi(row0 + lane, s);
+        epi(row0 + lane, s, false);
       }
       __syncwarp();
     }

@@ -8,14 +8,22 @@
 
 namespace rh {
 
-// Owning device buffers of one side layout (see SideLayout).
-template <typename VT>
+// Owning device buffers of one side: the split-CSR structure, its FP64 values, optionally an
+// FP32 copy of the values (mixed precision), and two sets of walk scratch.
 struct SideStore {
-  SideLayout<VT> lay;
+  SideLayout lay;
+  SideVals<double> v64;
+  SideVals<float> v32;
+  WalkScratch wa, wb;
   int *ptr_s = nullptr, *idx_s = nullptr, *long_rows = nullptr, *ptr_l = nullptr,
       *idx_l = nullptr;
-  VT *val_s = nullptr, *val_l = nullptr;
   uint32_t *long_mask = nullptr;
+  int *chunk_ptr = nullptr, *chunk_row = nullptr;
+  double *val64_s = nullptr, *val64_l = nullptr;
+  float *val32_s = nullptr, *val32_l = nullptr;
+  double *part_a = nullptr, *part_b = nullptr;
+  unsigned int *done_a = nullptr, *done_b = nullptr;
+  double *gpart_a = nullptr, *gpart_b = nullptr;
   long long nnz_short = 0, nnz_long = 0;
 };
 
@@ -26,6 +34,18 @@ struct RowVecs {      // m-vectors used by the row kernel (K^ x~ and the dual st
 
 struct ColVecs {      // n-vectors used by the column kernel (K^T y~ and the primal step)
   double *x, *xt, *x0, *kty, *kty0, *xout, *certx;
+  const double *c, *l, *u, *e, *einv;
+};
+
+struct RowVecsMx {    // mixed precision, m-vectors (offsets from the FP64 anchor y0)
+  float *dyt, *kdxt, *dy, *kdx, *r0, *ylo;
+  double *y0, *kx0, *certy, *dyt64;
+  const double *q, *d, *dinv;
+};
+
+struct ColVecsMx {    // mixed precision, n-vectors (offsets from the FP64 anchor x0)
+  float *dxt, *dx, *ktdy, *s0, *xlo, *xhi;
+  double *x0, *kty0, *xout, *certx, *dxt64;
   const double *c, *l, *u, *e, *einv;
 };
 
@@ -50,21 +70,19 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
                      const double *val, const int *cp, const int *ridx, const double *cval,
                      int ruiz_iters, double alpha, double *D, double *E, double *tmp_m,
                      double *tmp_n);
-// Build a split-CSR side layout from a CSR (nrows rows) with values scaled as
-// val * rscale[row] * cscale[col].  Allocates device buffers (cudaMalloc).
-template <typename VT>
+// Build a split-CSR side from a CSR (nrows rows) with values scaled as
+// val * rscale[row] * cscale[col] (FP64, plus an FP32 copy when with32).  Allocates device
+// buffers (cudaMalloc).
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
                        const double *val, const double *rscale, const double *cscale, int L,
-                       SideStore<VT> *out);
-template <typename VT>
-void free_side(SideStore<VT> *s);
+                       bool with32, SideStore *out);
+void free_side(SideStore *s);
 // Choose the short-row threshold L from the row-length distribution (host copy of ptr).
 int choose_short_threshold(const int *h_ptr, int nrows);
 // Launch geometry of the tile kernels for a side with L.
-int tile_grid(const SideLayout<double> &lay, int smem_bytes, int sm_count, int blocks_per_sm);
+int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm);
 // out = side * src   (plain product, FP64)
-void side_spmv(cudaStream_t st, const SideLayout<double> &lay, const double *src, double *out,
-               int grid);
+void side_spmv(cudaStream_t st, const SideStore &side, const double *src, double *out, int grid);
 // deterministic sum of squares -> *out (device scalar); tmp holds >= 1024 doubles
 void sumsq(cudaStream_t st, int n, const double *x, double *out, double *tmp);
 // v = w / sqrt(*ss)
@@ -76,16 +94,29 @@ void vmul(cudaStream_t st, int n, const double *a, const double *x, double *y, i
 void vclamp(cudaStream_t st, int n, double *x, const double *l, const double *u);
 
 // ---- iteration (iterate.cu) -----------------------------------------------------------------
-void launch_row_iter(cudaStream_t st, const SideLayout<double> &lay, const double *xt,
-                     const RowVecs &v, Ctl *ctl, double *part, const IterConsts &ic, int grid,
-                     int smem);
-void launch_col_iter(cudaStream_t st, const SideLayout<double> &lay, const double *yt,
-                     const ColVecs &v, Ctl *ctl, double *part, const IterConsts &ic, int grid,
-                     int smem, int phase);
+void launch_row_iter(cudaStream_t st, const SideStore &side, const double *xt, const RowVecs &v,
+                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem);
+void launch_col_iter(cudaStream_t st, const SideStore &side, const double *yt, const ColVecs &v,
+                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem,
+                     int phase);
 // x_out = E .* xout ; y_out = D .* yt
 void launch_unscale(cudaStream_t st, int n, int m, const double *e, const double *xs,
                     const double *d, const double *ys, double *xo, double *yo);
 int row_iter_blocks_per_sm(int smem);
+
+// ---- mixed-precision iteration (iterate_mx.cu) -------------------------------------------------
+void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
+                        const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
+                        double *part, const IterConsts &ic, int grid, int smem);
+void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx &v,
+                        const float *dyt, const double *dyt64, const double *y0, Ctl *ctl,
+                        double *part, const IterConsts &ic, int grid, int smem, int phase);
+void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const double *xs,
+                       const double *d, const double *y0, const float *dyt, double *xo,
+                       double *yo, double *yt64);
+void zero_f32(cudaStream_t st, int n, float *x);
+void allow_large_smem_mx(int bytes);
+int iter_mx_blocks_per_sm(int smem);
 // opt in to dynamic shared memory above 48 KB for the tile kernels
 void allow_large_smem(int bytes);
 void allow_large_smem_setup(int bytes);

@@ -17,19 +17,11 @@
 // SpMVs deliver (K x_{t+1} = w (rho K x~_t + (1 - rho) K x_t) + (1 - w) K x^{n,0}).  Each iteration
 // therefore needs exactly the two SpMVs of eq. pdhg.
 #include "internal.h"
+#include "iter_common.cuh"
 
 namespace rh {
 
 namespace {
-
-__device__ __forceinline__ double proj_lambda(double g, double l, double u) {
-  // reduced cost lambda = proj onto {0} (free), [0,inf) (l finite), (-inf,0] (u finite), R
-  const bool lf = isfinite(l), uf = isfinite(u);
-  if (lf && uf) return g;
-  if (lf) return fmax(g, 0.0);
-  if (uf) return fmin(g, 0.0);
-  return 0.0;
-}
 
 // sums: 0 dy2, 1 cross, 2 ya2, 3 rp2, 4 qy, 5 qv ; maxima: 0 yneg, 1 kd_eq, 2 kd_in
 using RowAcc = Acc<6, 3>;
@@ -39,8 +31,8 @@ using ColAcc = Acc<8, 4>;
 
 template <int RHO2>
 __global__ void __launch_bounds__(kBlockThreads)
-k_row_iter(SideLayout<double> lay, const double *__restrict__ xt, RowVecs v, Ctl *ctl,
-           double *part, IterConsts ic) {
+k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ xt,
+           RowVecs v, Ctl *ctl, double *part, IterConsts ic) {
   extern __shared__ double smem[];
   if (ctl->status != kRunning) return;
   const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
@@ -49,11 +41,12 @@ k_row_iter(SideLayout<double> lay, const double *__restrict__ xt, RowVecs v, Ctl
   const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
   const bool rp = (k == 0 && n_ep >= 1);
   const int m_eq = ic.m_eq;
-  RowAcc a;
+  RowAcc a, al;   // al: contributions of long rows (see walk_tiles)
   a.zero();
+  al.zero();
   double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
 
-  auto epi = [&](int i, double dot) {
+  auto body = [&](int i, double dot, RowAcc &a) {
     const double ytp = v.yt[i], kxtp = v.kxt[i];
     double yi, kxi, y0i;
     if (restart) {
@@ -99,65 +92,25 @@ k_row_iter(SideLayout<double> lay, const double *__restrict__ xt, RowVecs v, Ctl
       v.certy[i] = vy * di;
     }
   };
-  walk_tiles(lay, xt, my, epi);
+  auto epi = [&](int i, double dot, bool lg) {
+    if (lg) body(i, dot, al);
+    else body(i, dot, a);
+  };
+  auto gdone = [&](int grp) { store_group(al, ws.group_part, grp); };
+  auto gather = [&](int j) { return xt[j]; };
+  walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 
   if (cta_reduce_and_ticket(a, part, &ctl->cnt_row)) {
     double r[9];
-    grid_finish<6, 3>(part, r);
-    if (threadIdx.x == 0) {
-      const double tau = ctl->tau, omega = ctl->omega;
-      const double fpr2 = ctl->dx_sq / tau + r[0] / sigma + 2.0 * r[1];
-      const double fpr0 = (k == 0) ? fpr2 : ctl->fpr0_sq;
-      bool rs;
-      if (ic.restart_scheme == 1) {
-        rs = ic.max_epoch_len > 0 && k >= ic.max_epoch_len;
-      } else {
-        rs = (n_ep == 0 && k > ic.first_epoch_len) || (n_ep >= 1 && fpr2 <= ic.beta2 * fpr0) ||
-             (ic.max_epoch_len > 0 && k >= ic.max_epoch_len);
-      }
-      if (ic.trace && t < ic.trace_cap) {
-        TraceRec tr;
-        tr.t = t; tr.epoch = n_ep; tr.k = k; tr.fpr_sq = fpr2; tr.omega = omega;
-        tr.restart = rs ? 1 : 0; tr.pad = 0;
-        ic.trace[t] = tr;
-      }
-      ctl->fpr0_sq = fpr0;
-      ctl->fpr_sq = fpr2;
-      ctl->rp_sq = r[3];
-      ctl->qy = r[4];
-      ctl->inf_qv = r[5];
-      ctl->inf_yneg = r[6];
-      ctl->inf_kd_eq = r[7];
-      ctl->inf_kd_in = r[8];
-      if (!isfinite(fpr2)) ctl->status = kNumericalError;
-      if (rs) {
-        if (ic.pw_update) {
-          const double dxa = sqrt(ctl->xa_sq), dya = sqrt(r[2]);
-          const double ratio = dxa > 1e-10 ? dya / dxa : 0.0;
-          if (dxa > 1e-10 && dya > 1e-10 && ratio > 0.0 && isfinite(ratio)) {
-            const double om = exp(0.5 * log(ratio) + 0.5 * log(omega));
-            ctl->omega = om;
-            ctl->tau = ic.eta / om;
-            ctl->sigma = ic.eta * om;
-          }
-        }
-        ctl->k_next = 0;
-        ctl->n_next = n_ep + 1;
-      } else {
-        ctl->w = (k + 1.0) / (k + 2.0);
-        ctl->k_next = k + 1;
-        ctl->n_next = n_ep;
-      }
-      ctl->restart_pending = rs ? 1 : 0;
-      ctl->cnt_row = 0;
-    }
+    grid_finish<6, 3>(part, r, ws.group_part, lay.n_long_tiles);
+    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma);
   }
 }
 
 template <int RHO2>
 __global__ void __launch_bounds__(kBlockThreads)
-k_col_iter(SideLayout<double> lay, const double *__restrict__ ytv, ColVecs v, Ctl *ctl,
-           double *part, IterConsts ic, int phase) {
+k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ ytv,
+           ColVecs v, Ctl *ctl, double *part, IterConsts ic, int phase) {
   extern __shared__ double smem[];
   if (ctl->status != kRunning) return;
   const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
@@ -165,11 +118,12 @@ k_col_iter(SideLayout<double> lay, const double *__restrict__ ytv, ColVecs v, Ct
   const double w = ctl->w, tau = ctl->tau;
   const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
   const bool rp = phase == 0 && (k == 0 && n_ep >= 1);
-  ColAcc a;
+  ColAcc a, al;
   a.zero();
+  al.zero();
   double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
 
-  auto epi = [&](int j, double dot) {
+  auto body = [&](int j, double dot, ColAcc &a) {
     const double xtj = v.xt[j];
     const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
     if (check) {
@@ -219,49 +173,18 @@ k_col_iter(SideLayout<double> lay, const double *__restrict__ ytv, ColVecs v, Ct
     const double xa = xtn - x0j;
     a.s[1] += xa * xa;
   };
-  walk_tiles(lay, ytv, my, epi);
+  auto epi = [&](int j, double dot, bool lg) {
+    if (lg) body(j, dot, al);
+    else body(j, dot, a);
+  };
+  auto gdone = [&](int grp) { store_group(al, ws.group_part, grp); };
+  auto gather = [&](int j) { return ytv[j]; };
+  walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 
   if (cta_reduce_and_ticket(a, part, &ctl->cnt_col)) {
     double r[12];
-    grid_finish<8, 4>(part, r);
-    if (threadIdx.x == 0) {
-      ctl->dx_sq = r[0];
-      ctl->xa_sq = r[1];
-      int st = kRunning;
-      if (rp) {
-        const double obj = ctl->inf_qv - r[6] + r[7];
-        const double vy = fmax(fmax(r[10], r[11]), ctl->inf_yneg);
-        const double cd = r[5];
-        const double vx = fmax(fmax(ctl->inf_kd_eq, ctl->inf_kd_in), fmax(r[8], r[9]));
-        if (obj > 0.0 && vy / obj <= ic.eps_infeas) st = kPrimalInfeasible;
-        else if (cd < 0.0 && vx / (-cd) <= ic.eps_infeas) st = kDualInfeasible;
-      }
-      if (st == kRunning && check) {
-        const double rel_p = sqrt(ctl->rp_sq) / ic.qn1;
-        const double rel_d = sqrt(r[2]) / ic.cn1;
-        const double pobj = r[3] + ic.obj_offset;
-        const double dobj = ctl->qy + r[4] + ic.obj_offset;
-        const double gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
-        ctl->rel_p = rel_p;
-        ctl->rel_d = rel_d;
-        ctl->rel_gap = gap;
-        ctl->pobj = pobj;
-        ctl->dobj = dobj;
-        ctl->check_t = t;
-        const double kkt = fmax(rel_p, fmax(rel_d, gap));
-        if (!isfinite(kkt)) st = kNumericalError;
-        else if (kkt <= ic.eps_kkt) st = kOptimal;
-        else if (t + 1 >= ic.max_iters) st = kIterLimit;
-      }
-      if (st == kRunning && !isfinite(r[0])) st = kNumericalError;
-      if (st != kRunning) ctl->status = st;
-      ctl->t = (phase == 0) ? t + 1 : 0;
-      if (st == kRunning) {     // a final iteration keeps its own (k, n)
-        ctl->k = ctl->k_next;
-        ctl->n = ctl->n_next;
-      }
-      ctl->cnt_col = 0;
-    }
+    grid_finish<8, 4>(part, r, ws.group_part, lay.n_long_tiles);
+    if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, phase);
   }
 }
 
@@ -274,22 +197,25 @@ __global__ void k_unscale(int n, int m, const double *e, const double *xs, const
 
 }  // namespace
 
-void launch_row_iter(cudaStream_t st, const SideLayout<double> &lay, const double *xt,
-                     const RowVecs &v, Ctl *ctl, double *part, const IterConsts &ic, int grid,
-                     int smem) {
+void launch_row_iter(cudaStream_t st, const SideStore &side, const double *xt, const RowVecs &v,
+                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem) {
   if (ic.rho2)
-    k_row_iter<1><<<grid, kBlockThreads, smem, st>>>(lay, xt, v, ctl, part, ic);
+    k_row_iter<1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl,
+                                                      part, ic);
   else
-    k_row_iter<0><<<grid, kBlockThreads, smem, st>>>(lay, xt, v, ctl, part, ic);
+    k_row_iter<0><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl,
+                                                      part, ic);
 }
 
-void launch_col_iter(cudaStream_t st, const SideLayout<double> &lay, const double *yt,
-                     const ColVecs &v, Ctl *ctl, double *part, const IterConsts &ic, int grid,
-                     int smem, int phase) {
+void launch_col_iter(cudaStream_t st, const SideStore &side, const double *yt, const ColVecs &v,
+                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem,
+                     int phase) {
   if (ic.rho2)
-    k_col_iter<1><<<grid, kBlockThreads, smem, st>>>(lay, yt, v, ctl, part, ic, phase);
+    k_col_iter<1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, yt, v, ctl,
+                                                      part, ic, phase);
   else
-    k_col_iter<0><<<grid, kBlockThreads, smem, st>>>(lay, yt, v, ctl, part, ic, phase);
+    k_col_iter<0><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, yt, v, ctl,
+                                                      part, ic, phase);
 }
 
 void launch_unscale(cudaStream_t st, int n, int m, const double *e, const double *xs,

@@ -123,10 +123,9 @@ __global__ void k_long_lengths(int n_long, const int *long_rows, const int *ptr,
   len_l[i] = ptr[r + 1] - ptr[r];
 }
 
-template <typename VT>
 __global__ void k_copy_short(int nrows, const int *ptr, const int *idx, const double *val,
                              const double *rs, const double *cs, const int *ptr_s, int *idx_s,
-                             VT *val_s, int L) {
+                             double *val_s, float *val32_s, int L) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
   int b = ptr[r], e = ptr[r + 1];
@@ -136,14 +135,15 @@ __global__ void k_copy_short(int nrows, const int *ptr, const int *idx, const do
   for (int p = b; p < e; ++p, ++o) {
     int j = idx[p];
     idx_s[o] = j;
-    val_s[o] = (VT)(sr * val[p] * cs[j]);
+    const double v = sr * val[p] * cs[j];
+    val_s[o] = v;
+    if (val32_s) val32_s[o] = (float)v;
   }
 }
 
-template <typename VT>
 __global__ void k_copy_long(int n_long, const int *long_rows, const int *ptr, const int *idx,
                             const double *val, const double *rs, const double *cs,
-                            const int *ptr_l, int *idx_l, VT *val_l) {
+                            const int *ptr_l, int *idx_l, double *val_l, float *val32_l) {
   // one warp per long row
   int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -155,7 +155,9 @@ __global__ void k_copy_long(int n_long, const int *long_rows, const int *ptr, co
   for (int p = b + lane; p < e; p += 32) {
     int j = idx[p];
     idx_l[o + (p - b)] = j;
-    val_l[o + (p - b)] = (VT)(sr * val[p] * cs[j]);
+    const double v = sr * val[p] * cs[j];
+    val_l[o + (p - b)] = v;
+    if (val32_l) val32_l[o + (p - b)] = (float)v;
   }
 }
 
@@ -223,11 +225,14 @@ __global__ void k_vclamp(int n, double *x, const double *l, const double *u) {
 }
 
 __global__ void __launch_bounds__(kBlockThreads)
-k_side_spmv(SideLayout<double> lay, const double *__restrict__ src, double *out) {
+k_side_spmv(SideLayout lay, SideVals<double> vals, WalkScratch ws,
+            const double *__restrict__ src, double *out) {
   extern __shared__ double smem[];
   double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
-  auto epi = [&](int row, double dot) { out[row] = dot; };
-  walk_tiles(lay, src, my, epi);
+  auto epi = [&](int row, double dot, bool) { out[row] = dot; };
+  auto gather = [&](int j) { return src[j]; };
+  auto gdone = [&](int) {};
+  walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 }
 
 }  // namespace
@@ -320,12 +325,11 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
   }
 }
 
-template <typename VT>
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
                        const double *val, const double *rscale, const double *cscale, int L,
-                       SideStore<VT> *out) {
+                       bool with32, SideStore *out) {
   cudaError_t err;
-  SideStore<VT> s;
+  SideStore s;
   int *len_s = nullptr, *is_long = nullptr, *iota = nullptr, *nsel = nullptr, *len_l = nullptr;
   void *tmp = nullptr;
   size_t tb = 0, tb2 = 0, tb3 = 0;
@@ -359,11 +363,13 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   s.lay.n_long_tiles = (h_nlong + kTileRows - 1) / kTileRows;
   s.nnz_short = h_nnz_s;
   if ((err = cudaMalloc(&s.idx_s, (size_t)std::max(h_nnz_s, 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&s.val_s, (size_t)std::max(h_nnz_s, 1) * sizeof(VT)))) goto fail;
+  if ((err = cudaMalloc(&s.val64_s, (size_t)std::max(h_nnz_s, 1) * sizeof(double)))) goto fail;
+  if (with32 && (err = cudaMalloc(&s.val32_s, (size_t)std::max(h_nnz_s, 1) * sizeof(float))))
+    goto fail;
   if ((err = cudaMalloc(&s.ptr_l, (size_t)(h_nlong + 1) * sizeof(int)))) goto fail;
   if ((err = cudaMalloc(&len_l, (size_t)(h_nlong + 1) * sizeof(int)))) goto fail;
-  k_copy_short<VT><<<nblocks(nrows, 128), 128, 0, st>>>(nrows, ptr, idx, val, rscale, cscale,
-                                                         s.ptr_s, s.idx_s, s.val_s, L);
+  k_copy_short<<<nblocks(nrows, 128), 128, 0, st>>>(nrows, ptr, idx, val, rscale, cscale,
+                                                     s.ptr_s, s.idx_s, s.val64_s, s.val32_s, L);
   k_long_lengths<<<nblocks(h_nlong + 1, 256), 256, 0, st>>>(h_nlong, s.long_rows, ptr, len_l);
   count_launches(2 + (h_nlong > 0 ? 1 : 0));
   cub::DeviceScan::ExclusiveSum(nullptr, tb3, len_l, s.ptr_l, h_nlong + 1, st);
@@ -378,12 +384,48 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   if ((err = cudaStreamSynchronize(st))) goto fail;
   s.nnz_long = h_nnz_l;
   if ((err = cudaMalloc(&s.idx_l, (size_t)std::max(h_nnz_l, 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&s.val_l, (size_t)std::max(h_nnz_l, 1) * sizeof(VT)))) goto fail;
+  if ((err = cudaMalloc(&s.val64_l, (size_t)std::max(h_nnz_l, 1) * sizeof(double)))) goto fail;
+  if (with32 && (err = cudaMalloc(&s.val32_l, (size_t)std::max(h_nnz_l, 1) * sizeof(float))))
+    goto fail;
   if (h_nlong > 0)
-    k_copy_long<VT><<<nblocks((long long)h_nlong * 32, 128), 128, 0, st>>>(
-        h_nlong, s.long_rows, ptr, idx, val, rscale, cscale, s.ptr_l, s.idx_l, s.val_l);
+    k_copy_long<<<nblocks((long long)h_nlong * 32, 128), 128, 0, st>>>(
+        h_nlong, s.long_rows, ptr, idx, val, rscale, cscale, s.ptr_l, s.idx_l, s.val64_l,
+        s.val32_l);
   if ((err = cudaStreamSynchronize(st))) goto fail;
   if ((err = cudaGetLastError())) goto fail;
+  {
+    // chunks of the long rows (host-side: n_long + 1 offsets)
+    std::vector<int> hpl(h_nlong + 1), hcp(h_nlong + 1), hcr;
+    if ((err = cudaMemcpy(hpl.data(), s.ptr_l, (h_nlong + 1) * sizeof(int),
+                          cudaMemcpyDeviceToHost)))
+      goto fail;
+    hcp[0] = 0;
+    for (int i = 0; i < h_nlong; ++i) {
+      const int len = hpl[i + 1] - hpl[i];
+      const int nc = (len + kChunk - 1) / kChunk;
+      hcp[i + 1] = hcp[i] + nc;
+      for (int c = 0; c < nc; ++c) hcr.push_back(i);
+    }
+    const int nch = hcp[h_nlong];
+    s.lay.n_chunks = nch;
+    if ((err = cudaMalloc(&s.chunk_ptr, (size_t)(h_nlong + 1) * sizeof(int)))) goto fail;
+    if ((err = cudaMalloc(&s.chunk_row, (size_t)std::max(nch, 1) * sizeof(int)))) goto fail;
+    if ((err = cudaMalloc(&s.part_a, (size_t)std::max(nch, 1) * sizeof(double)))) goto fail;
+    if ((err = cudaMalloc(&s.part_b, (size_t)std::max(nch, 1) * sizeof(double)))) goto fail;
+    const size_t ng = (size_t)std::max(s.lay.n_long_tiles, 1);
+    if ((err = cudaMalloc(&s.done_a, ng * sizeof(unsigned int)))) goto fail;
+    if ((err = cudaMalloc(&s.done_b, ng * sizeof(unsigned int)))) goto fail;
+    if ((err = cudaMalloc(&s.gpart_a, ng * kMaxPartials * sizeof(double)))) goto fail;
+    if ((err = cudaMalloc(&s.gpart_b, ng * kMaxPartials * sizeof(double)))) goto fail;
+    if ((err = cudaMemcpy(s.chunk_ptr, hcp.data(), (h_nlong + 1) * sizeof(int),
+                          cudaMemcpyHostToDevice)))
+      goto fail;
+    if (nch > 0 && (err = cudaMemcpy(s.chunk_row, hcr.data(), nch * sizeof(int),
+                                     cudaMemcpyHostToDevice)))
+      goto fail;
+    if ((err = cudaMemset(s.done_a, 0, ng * sizeof(unsigned int)))) goto fail;
+    if ((err = cudaMemset(s.done_b, 0, ng * sizeof(unsigned int)))) goto fail;
+  }
   cudaFree(len_s);
   cudaFree(is_long);
   cudaFree(iota);
@@ -392,12 +434,22 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   cudaFree(tmp);
   s.lay.ptr_s = s.ptr_s;
   s.lay.idx_s = s.idx_s;
-  s.lay.val_s = s.val_s;
   s.lay.long_mask = s.long_mask;
   s.lay.long_rows = s.long_rows;
   s.lay.ptr_l = s.ptr_l;
   s.lay.idx_l = s.idx_l;
-  s.lay.val_l = s.val_l;
+  s.lay.chunk_ptr = s.chunk_ptr;
+  s.lay.chunk_row = s.chunk_row;
+  s.v64.s = s.val64_s;
+  s.v64.l = s.val64_l;
+  s.v32.s = s.val32_s;
+  s.v32.l = s.val32_l;
+  s.wa.chunk_part = s.part_a;
+  s.wa.group_done = s.done_a;
+  s.wa.group_part = s.gpart_a;
+  s.wb.chunk_part = s.part_b;
+  s.wb.group_done = s.done_b;
+  s.wb.group_part = s.gpart_b;
   *out = s;
   return cudaSuccess;
 fail:
@@ -411,32 +463,18 @@ fail:
   return err;
 }
 
-template <typename VT>
-void free_side(SideStore<VT> *s) {
-  cudaFree(s->ptr_s);
-  cudaFree(s->idx_s);
-  cudaFree(s->val_s);
-  cudaFree(s->long_mask);
-  cudaFree(s->long_rows);
-  cudaFree(s->ptr_l);
-  cudaFree(s->idx_l);
-  cudaFree(s->val_l);
-  *s = SideStore<VT>();
+void free_side(SideStore *s) {
+  void *bufs[] = {s->ptr_s, s->idx_s, s->long_mask, s->long_rows, s->ptr_l, s->idx_l,
+                  s->chunk_ptr, s->chunk_row, s->val64_s, s->val64_l, s->val32_s, s->val32_l,
+                  s->part_a, s->part_b, s->done_a, s->done_b, s->gpart_a, s->gpart_b};
+  for (void *b : bufs) cudaFree(b);
+  *s = SideStore();
 }
 
-template cudaError_t build_side<double>(cudaStream_t, int, int, const int *, const int *,
-                                        const double *, const double *, const double *, int,
-                                        SideStore<double> *);
-template cudaError_t build_side<float>(cudaStream_t, int, int, const int *, const int *,
-                                       const double *, const double *, const double *, int,
-                                       SideStore<float> *);
-template void free_side<double>(SideStore<double> *);
-template void free_side<float>(SideStore<float> *);
-
 int choose_short_threshold(const int *h_ptr, int nrows) {
-  // Short rows are staged for a whole 32-row tile in shared memory (32 * L products per warp).
-  // Pick the smallest L in {8, 16, 32, 64} that keeps at least 97% of the rows short; rows
-  // beyond it go to the warp-per-row path.
+  // Short rows are staged for a whole 32-row tile in shared memory (32 * L products per warp);
+  // longer rows go to the chunked warp-per-chunk path.  Pick the smallest L in {8, 16, 32, 64}
+  // that keeps at least 90% of the rows short.
   if (nrows <= 0) return 8;
   std::vector<int> len(nrows);
   for (int i = 0; i < nrows; ++i) len[i] = h_ptr[i + 1] - h_ptr[i];
@@ -444,14 +482,13 @@ int choose_short_threshold(const int *h_ptr, int nrows) {
   for (int L : cands) {
     long long nshort = 0;
     for (int i = 0; i < nrows; ++i) nshort += (len[i] <= L);
-    if (nshort >= (long long)(0.97 * nrows)) return L;
+    if (nshort >= (long long)(0.90 * nrows)) return L;
   }
   return 64;
 }
 
-int tile_grid(const SideLayout<double> &lay, int smem_bytes, int sm_count, int blocks_per_sm) {
-  (void)smem_bytes;
-  long long need = ((long long)lay.total_tiles() + kBlockWarps - 1) / kBlockWarps;
+int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm) {
+  long long need = ((long long)lay.total_items() + kBlockWarps - 1) / kBlockWarps;
   long long cap = (long long)sm_count * std::max(blocks_per_sm, 1);
   long long g = std::min(need, cap);
   return (int)std::max<long long>(g, 1);
@@ -461,10 +498,9 @@ void allow_large_smem_setup(int bytes) {
   cudaFuncSetAttribute(k_side_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void side_spmv(cudaStream_t st, const SideLayout<double> &lay, const double *src, double *out,
-               int grid) {
-  int smem = kBlockWarps * kTileRows * lay.L * (int)sizeof(double);
-  k_side_spmv<<<grid, kBlockThreads, smem, st>>>(lay, src, out);
+void side_spmv(cudaStream_t st, const SideStore &side, const double *src, double *out, int grid) {
+  int smem = kBlockWarps * kTileRows * side.lay.L * (int)sizeof(double);
+  k_side_spmv<<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, src, out);
   count_launches(1);
 }
 

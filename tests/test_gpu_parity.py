@@ -280,3 +280,72 @@ def test_nonblocking_poll_cancel_and_limits(rh):
     with rh.Solver(lp, eps_rel_kkt=1e-15, max_iters=1000) as s:
         r = s.run()
         assert r.status == rh.STATUS_ITERATION_LIMIT and r.iters == 1000
+
+
+# ---------------------------------------------------------------------------------------------
+# mixed precision (FP32 matrix values and iterate offsets, FP64 anchors and checks): no iterate
+# parity is claimed; the solution must reach the tolerance as measured by the FP64 checker on the
+# host, and its objective must agree with the FP64 oracle's to the accuracy the tolerance allows.
+
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("tol", [1e-6, 1e-8])
+@pytest.mark.parametrize("case", ["c1", "c2_small"])
+def test_mixed_precision_reaches_tolerance(rh, case, tol, alg):
+    lp = CASES[case]()
+    o = O.solve(lp, O.OracleParams(algorithm=alg, eps_rel_kkt=tol, max_iters=400_000))
+    with rh.Solver(lp, algorithm=alg, precision=1, eps_rel_kkt=tol, max_iters=400_000) as s:
+        r = s.run()
+    assert r.status == rh.STATUS_OPTIMAL, r.status_name
+    k = O.rel_kkt(lp, O.csr_matrix(lp), r.x, r.y)
+    assert k["rel_kkt"] <= tol * 1.05, k
+    assert abs(r.primal_obj - o.primal_obj) <= 20 * tol * (1 + abs(o.primal_obj))
+    print(f"mixed {case} tol={tol} alg={alg}: iters {r.iters} (fp64 oracle {o.iters}); "
+          f"host rel-KKT {k['rel_kkt']:.2e}; |obj - obj_oracle|/(1+|obj|) = "
+          f"{abs(r.primal_obj - o.primal_obj) / (1 + abs(o.primal_obj)):.2e}")
+
+
+def test_mixed_precision_full_size_c2(rh):
+    lp = lpgen.make_c2(1)
+    with rh.Solver(lp, algorithm=1, precision=1, eps_rel_kkt=1e-6) as s:
+        r = s.run()
+    assert r.status == rh.STATUS_OPTIMAL
+    k = O.rel_kkt(lp, O.csr_matrix(lp), r.x, r.y)
+    assert k["rel_kkt"] <= 1.05e-6
+    ref = lp.planted_objective()
+    assert abs(r.primal_obj - ref) <= 1e-5 * (1 + abs(ref))
+
+
+@pytest.mark.xfail(reason="FP32 offsets of diverging iterates limit the mixed-precision "
+                          "certificate to ~1e-5; detection needs the planned FP64 escalation",
+                   strict=False)
+@pytest.mark.parametrize("alg", [0, 1])
+def test_mixed_precision_certificates(rh, alg):
+    for kind in ("primal", "dual"):
+        lp = (lpgen.make_primal_infeasible(3, 500, 1000) if kind == "primal"
+              else lpgen.make_dual_infeasible(3, 500, 1000))
+        with rh.Solver(lp, algorithm=alg, precision=1, max_iters=100_000,
+                       max_epoch_len=200) as s:
+            r = s.run()
+        K = O.csr_matrix(lp)
+        if kind == "primal":
+            assert r.status == rh.STATUS_PRIMAL_INFEASIBLE, r.status_name
+            by = lp.q @ r.cert_y
+            assert by > 0 and (K.T @ r.cert_y).max() / by <= 1e-8
+        else:
+            assert r.status == rh.STATUS_DUAL_INFEASIBLE, r.status_name
+            cd = lp.c @ r.cert_x
+            assert cd < 0 and np.abs(K @ r.cert_x).max() / -cd <= 1e-8
+
+
+def test_mixed_first_iterations_close_to_fp64(rh):
+    """Before any restart the mixed path follows the FP64 trajectory to FP32 accuracy."""
+    lp = CASES["c2_small"]()
+    T = 40
+    common = dict(algorithm=1, eps_rel_kkt=1e-14, first_epoch_len=100, max_iters=T)
+    with rh.Solver(lp, **common) as s:
+        s.run()
+        x64, y64 = s.state(1)
+    with rh.Solver(lp, precision=1, **common) as s:
+        s.run()
+        x32, y32 = s.state(1)
+    assert rel(x32, x64) < 1e-5 and rel(y32, y64) < 1e-5
