@@ -210,6 +210,19 @@ int rhpdhg_kernel_times(const rhpdhg_handle *h, double *ms_row, double *ms_col,
                         int64_t *launches_row, int64_t *launches_col, double *bytes_row,
                         double *bytes_col);
 
+/* Relative KKT error of an arbitrary point, the solver's termination measure (Section 7,
+ * "Termination criteria"; l2 form, see rhpdhg_params.eps_rel_kkt): for the LP `lp`, whose arrays
+ * must be in device memory (lp->memory = RHPDHG_MEM_DEVICE), and the unscaled point x (n
+ * doubles) and y (m doubles) in device memory, writes to the host array out:
+ *     out[0] = rel_p, out[1] = rel_d, out[2] = rel_gap, out[3] = primal_obj, out[4] = dual_obj.
+ * Only the CSR of K is needed: K^T y is accumulated with atomic FP64 adds, so the last digits
+ * may differ from run to run.  Work is ordered on `cuda_stream` (NULL = legacy default stream)
+ * and the call synchronises it.  Scratch (n + 8200 doubles) is allocated with cudaMalloc and
+ * freed before returning.  Returns RHPDHG_ERR_INVALID_ARG for host-memory or incomplete input,
+ * RHPDHG_ERR_OOM / RHPDHG_ERR_CUDA on CUDA failures. */
+int rhpdhg_kkt_eval(const rhpdhg_problem *lp, const double *x, const double *y,
+                    void *cuda_stream, double *out);
+
 /* Number of CUDA kernels of this library the handle has launched so far (create and every
  * solve; a replay of a captured graph counts each kernel node it runs).  Kernels of the CUB
  * library used for the transpose during create are not counted.  Returns -1 for NULL. */

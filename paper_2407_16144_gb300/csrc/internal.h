@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "../../include/rhpdhg.h"
 
 namespace rh {
 
@@ -103,6 +104,15 @@ void launch_col_iter(cudaStream_t st, const SideStore &side, const double *yt, c
 void launch_unscale(cudaStream_t st, int n, int m, const double *e, const double *xs,
                     const double *d, const double *ys, double *xo, double *yo);
 int row_iter_blocks_per_sm(int smem);
+
+// ---- standalone KKT evaluation (kkt.cu) --------------------------------------------------------
+constexpr int kKktMaxBlocks = 1024;   // block partials of the evaluation kernels
+constexpr int kKktSlotCount = 8;
+int kkt_blocks(int m, int n);
+// scratch: kty (n doubles), part (kKktMaxBlocks * kKktSlotCount doubles), dout (8 doubles)
+cudaError_t kkt_eval_with_scratch(const rhpdhg_problem *lp, const double *x, const double *y,
+                                  cudaStream_t st, double *kty, double *part, double *dout,
+                                  double *out);
 
 // ---- mixed-precision iteration (iterate_mx.cu) -------------------------------------------------
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,

@@ -70,7 +70,7 @@ class rhpdhg_trace_rec(C.Structure):
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
             "rhpdhg_cancel", "rhpdhg_free", "rhpdhg_last_error", "rhpdhg_get_state",
             "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_kernel_times",
-            "rhpdhg_launch_count"]
+            "rhpdhg_launch_count", "rhpdhg_kkt_eval"]
 
 _lib = None
 
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
         "rhpdhg_kernel_times": (C.c_int, [H, _dp, _dp, C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int64), _dp, _dp]),
         "rhpdhg_launch_count": (C.c_int64, [H]),
+        "rhpdhg_kkt_eval": (C.c_int, [C.POINTER(rhpdhg_problem), C.c_void_p, C.c_void_p,
+                                      C.c_void_p, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -172,6 +174,29 @@ def rhpdhg_kernel_times(h):
 
 def rhpdhg_launch_count(h) -> int:
     return load().rhpdhg_launch_count(h)
+
+
+def rhpdhg_kkt_eval(lp: rhpdhg_problem, x, y, stream: int = 0):
+    """x, y: device pointers (int).  Returns (rc, [rel_p, rel_d, rel_gap, primal_obj,
+    dual_obj])."""
+    out = (C.c_double * 5)()
+    rc = load().rhpdhg_kkt_eval(C.byref(lp), C.c_void_p(x), C.c_void_p(y or None),
+                                C.c_void_p(stream or None), out)
+    return rc, list(out)
+
+
+def device_problem(lp) -> rhpdhg_problem:
+    """rhpdhg_problem describing an LP whose arrays are torch CUDA tensors (the caller keeps
+    them alive)."""
+    prob = rhpdhg_problem()
+    prob.m_eq, prob.m_ineq, prob.n = int(lp.m_eq), int(lp.m_ineq), int(lp.n)
+    prob.memory = MEM_DEVICE
+    prob.nnz = int(lp.row_ptr[-1].item())
+    for f in ("row_ptr", "col_idx", "val", "c", "l", "u"):
+        setattr(prob, f, int(getattr(lp, f).data_ptr()))
+    prob.rhs = int(lp.q.data_ptr()) if prob.m_eq + prob.m_ineq else None
+    prob.obj_offset = float(getattr(lp, "obj_offset", 0.0))
+    return prob
 
 
 def _ptr(a):

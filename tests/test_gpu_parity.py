@@ -349,3 +349,40 @@ def test_mixed_first_iterations_close_to_fp64(rh):
         s.run()
         x32, y32 = s.state(1)
     assert rel(x32, x64) < 1e-5 and rel(y32, y64) < 1e-5
+
+
+def _device_lp(lp):
+    import torch
+    return lpgen.LP(**{f: (torch.as_tensor(getattr(lp, f), device="cuda")
+                           if isinstance(getattr(lp, f), np.ndarray) else getattr(lp, f))
+                       for f in ("m_eq", "m_ineq", "n", "row_ptr", "col_idx", "val", "c", "q",
+                                 "l", "u", "obj_offset")})
+
+
+@pytest.mark.parametrize("case", ["c1", "c2_small", "tiny_general"])
+def test_kkt_eval_matches_oracle_checker(rh, case):
+    """rhpdhg_kkt_eval (the termination measure for any point) against the oracle's checker."""
+    import torch
+    lp = CASES[case]()
+    dlp = _device_lp(lp)
+    prob = rh.device_problem(dlp)
+    rng = np.random.default_rng(5)
+    points = []
+    if lp.x_star is not None:
+        points.append((lp.x_star, lp.y_star))
+    points.append((rng.uniform(0, 2, lp.n) * np.isfinite(lp.l) + np.where(np.isfinite(lp.l), 0, 0.3),
+                   rng.standard_normal(lp.m)))
+    with rh.Solver(lp, eps_rel_kkt=1e-6) as s:
+        r = s.run()
+    points.append((r.x, r.y))
+    K = O.csr_matrix(lp)
+    for x, y in points:
+        xd = torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+        yd = torch.as_tensor(np.ascontiguousarray(y), device="cuda")
+        rc, out = rh.rhpdhg_kkt_eval(prob, xd.data_ptr(), yd.data_ptr())
+        assert rc == rh.OK
+        ref = O.rel_kkt(lp, K, x, y)
+        for got, key in zip(out, ["rel_p", "rel_d", "rel_gap", "primal_obj", "dual_obj"]):
+            assert abs(got - ref[key]) <= 1e-12 * max(1.0, abs(ref[key])), (key, got, ref[key])
+    # solver's own report agrees with the independent evaluation of its returned point
+    assert abs(out[0] - r.rel_p) <= 1e-9 * max(r.rel_p, 1e-12) + 1e-15
