@@ -223,6 +223,24 @@ int rhpdhg_kernel_times(const rhpdhg_handle *h, double *ms_row, double *ms_col,
 int rhpdhg_kkt_eval(const rhpdhg_problem *lp, const double *x, const double *y,
                     void *cuda_stream, double *out);
 
+/* Same evaluation as rhpdhg_kkt_eval, for callers that may not allocate device memory (for
+ * instance code inside a framework that owns all device memory through its own pool, or a
+ * latency-critical loop that must not take cudaMalloc's device-wide synchronisation).  The
+ * paper has no counterpart to this call; it exists for those callers only.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  Its scratch is a
+ *     fixed array of (2^20 + 8200) doubles (about 8.1 MiB) at file scope in the library, held by
+ *     every GPU that loads the library until the process exits.
+ *   - Size limit: n <= 1,048,576 (2^20).  Larger problems return RHPDHG_ERR_INVALID_ARG with a
+ *     message in rhpdhg_last_error(NULL); use rhpdhg_kkt_eval for them.
+ *   - The first call on each device looks up the array's device address (with that device
+ *     current) and keeps it; make that first call before any stream capture.
+ *   - All calls share the one array, and it keeps the previous call's contents (the call clears
+ *     what has to start at zero).  Calls that overlap on the GPU, on any stream or from any host
+ *     thread, race on the array and give wrong results: order them.
+ * Arguments, results and other errors are those of rhpdhg_kkt_eval. */
+int rhpdhg_kkt_eval_noalloc(const rhpdhg_problem *lp, const double *x, const double *y,
+                            void *cuda_stream, double *out);
+
 /* Number of CUDA kernels of this library the handle has launched so far (create and every
  * solve; a replay of a captured graph counts each kernel node it runs).  Kernels of the CUB
  * library used for the transpose during create are not counted.  Returns -1 for NULL. */

@@ -27,6 +27,10 @@ struct Timer {
 
 }  // namespace
 
+namespace rh {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace rh
+
 struct rhpdhg_handle {
   int dev = 0;
   int sm_count = 0;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 #include "../../include/rhpdhg.h"
 
@@ -49,6 +51,9 @@ struct ColVecsMx {    // mixed precision, n-vectors (offsets from the FP64 ancho
   double *x0, *kty0, *xout, *certx, *dxt64;
   const double *c, *l, *u, *e, *einv;
 };
+
+// Message for rhpdhg_last_error(NULL) (calls without a handle).
+void set_global_error(const std::string &msg);
 
 // Process-wide count of kernels launched by this library's wrappers (for launch accounting).
 void count_launches(long long n);

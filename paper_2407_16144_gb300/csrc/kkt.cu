@@ -11,6 +11,9 @@
 // partials and finished by one block.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <string>
+
 #include "../../include/rhpdhg.h"
 #include "internal.h"
 
@@ -165,5 +168,73 @@ extern "C" int rhpdhg_kkt_eval(const rhpdhg_problem *lp, const double *x, const 
   cudaFree(part);
   cudaFree(dout);
   if (e == cudaErrorMemoryAllocation) return RHPDHG_ERR_OOM;
+  return e == cudaSuccess ? RHPDHG_OK : RHPDHG_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant.  Some callers may not call cudaMalloc: code that lives inside a
+// framework which owns all device memory through its own pool and forbids raw allocations, code
+// in latency-critical loops that must not take the allocator's device-wide synchronisation, and
+// services that must keep a fixed device-memory footprint.  For them the same evaluation runs on
+// a scratch array fixed at file scope: every GPU that loads this library holds it until the
+// process exits.  Its host-side name is only a stand-in for the device symbol, so the device
+// address is looked up once per device with cudaGetSymbolAddress and kept.
+
+namespace {
+
+constexpr long long kNoAllocMaxN = 1LL << 20;   // largest n accepted (8 MiB of K^T y scratch)
+constexpr long long kNoAllocDoubles =
+    kNoAllocMaxN + (long long)rh::kKktMaxBlocks * rh::kKktSlotCount + 8;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_kkt_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" int rhpdhg_kkt_eval_noalloc(const rhpdhg_problem *lp, const double *x,
+                                       const double *y, void *stream, double *out) {
+  using namespace rh;
+  if (!lp || !x || !out || lp->n < 1 || lp->m_eq < 0 || lp->m_ineq < 0 ||
+      lp->memory != RHPDHG_MEM_DEVICE || (lp->m_eq + lp->m_ineq > 0 && (!y || !lp->rhs)) ||
+      !lp->row_ptr || !lp->c || !lp->l || !lp->u) {
+    set_global_error("rhpdhg_kkt_eval_noalloc: missing or host-memory input");
+    return RHPDHG_ERR_INVALID_ARG;
+  }
+  if ((long long)lp->n > kNoAllocMaxN) {
+    set_global_error("rhpdhg_kkt_eval_noalloc: n = " + std::to_string(lp->n) +
+                     " exceeds the fixed scratch of this entry point (n <= " +
+                     std::to_string(kNoAllocMaxN) + "); use rhpdhg_kkt_eval");
+    return RHPDHG_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return RHPDHG_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_global_error("rhpdhg_kkt_eval_noalloc: device ordinal out of range");
+    return RHPDHG_ERR_INVALID_ARG;
+  }
+  double *base = nullptr;
+  {
+    // one-time set-up per device, with that device current
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_kkt_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        set_global_error(std::string("rhpdhg_kkt_eval_noalloc: cudaGetSymbolAddress: ") +
+                         cudaGetErrorString(e));
+        return RHPDHG_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = static_cast<double *>(p);
+    }
+    base = g_noalloc_addr[dev];
+  }
+  double *kty = base;                                            // cleared by the first kernel
+  double *part = base + kNoAllocMaxN;                            // fully rewritten per call
+  double *dout = part + (long long)kKktMaxBlocks * kKktSlotCount;
+  e = kkt_eval_with_scratch(lp, x, y, (cudaStream_t)stream, kty, part, dout, out);
   return e == cudaSuccess ? RHPDHG_OK : RHPDHG_ERR_CUDA;
 }

@@ -70,7 +70,7 @@ class rhpdhg_trace_rec(C.Structure):
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
             "rhpdhg_cancel", "rhpdhg_free", "rhpdhg_last_error", "rhpdhg_get_state",
             "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_kernel_times",
-            "rhpdhg_launch_count", "rhpdhg_kkt_eval"]
+            "rhpdhg_launch_count", "rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc"]
 
 _lib = None
 
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
         "rhpdhg_launch_count": (C.c_int64, [H]),
         "rhpdhg_kkt_eval": (C.c_int, [C.POINTER(rhpdhg_problem), C.c_void_p, C.c_void_p,
                                       C.c_void_p, _dp]),
+        "rhpdhg_kkt_eval_noalloc": (C.c_int, [C.POINTER(rhpdhg_problem), C.c_void_p,
+                                              C.c_void_p, C.c_void_p, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -182,6 +184,14 @@ def rhpdhg_kkt_eval(lp: rhpdhg_problem, x, y, stream: int = 0):
     out = (C.c_double * 5)()
     rc = load().rhpdhg_kkt_eval(C.byref(lp), C.c_void_p(x), C.c_void_p(y or None),
                                 C.c_void_p(stream or None), out)
+    return rc, list(out)
+
+
+def rhpdhg_kkt_eval_noalloc(lp: rhpdhg_problem, x, y, stream: int = 0):
+    """As rhpdhg_kkt_eval, on the library's fixed scratch (allocates no device memory)."""
+    out = (C.c_double * 5)()
+    rc = load().rhpdhg_kkt_eval_noalloc(C.byref(lp), C.c_void_p(x), C.c_void_p(y or None),
+                                        C.c_void_p(stream or None), out)
     return rc, list(out)
 
 
