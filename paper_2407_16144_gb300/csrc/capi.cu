@@ -200,6 +200,7 @@ int reset_state(rhpdhg_handle *h) {
   c.t = 0; c.k = 0; c.n = 0; c.k_next = 0; c.n_next = 0;
   c.status = kRunning;
   c.restart_pending = 1;
+  c.stage = 1;           // the set-up column kernel runs first
   c.w = 0.0;
   c.omega = h->omega0;
   c.tau = h->eta / h->omega0;
@@ -282,7 +283,7 @@ void drive(rhpdhg_handle *h) {
       }
       cudaEventRecord(ev[g], h->st);
       ++launched;
-      h->launches += 2LL * h->p.check_every;
+      h->launches += (h->mixed ? 4LL : 2LL) * h->p.check_every;
     }
     if (done >= launched) break;
     const int g = (int)(done & 1);
@@ -567,8 +568,8 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   free_tmp();
 
   // ---- launch geometry ----
-  h->smem_row = kBlockWarps * kTileRows * h->rows.lay.L * (int)sizeof(double);
-  h->smem_col = kBlockWarps * kTileRows * h->cols.lay.L * (int)sizeof(double);
+  h->smem_row = kBlockWarps * (kTileRows * h->rows.lay.L + 4) * (int)sizeof(double);
+  h->smem_col = kBlockWarps * (kTileRows * h->cols.lay.L + 4) * (int)sizeof(double);
   allow_large_smem(kMaxTileSmem);
   allow_large_smem_setup(kMaxTileSmem);
   allow_large_smem_mx(kMaxTileSmem);

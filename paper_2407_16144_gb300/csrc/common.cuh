@@ -27,9 +27,9 @@ constexpr int kBlockWarps = 4;         // warps per CTA of the tile kernels
 constexpr int kBlockThreads = kBlockWarps * kWarp;
 constexpr int kMaxPartials = 16;       // reduction slots per CTA
 constexpr int kMaxTileL = 64;          // largest short-row threshold
-constexpr int kMaxTileSmem = kBlockWarps * kTileRows * kMaxTileL * 8;   // bytes
+constexpr int kMaxTileSmem = kBlockWarps * (kTileRows * kMaxTileL + 4) * 8;   // bytes
 constexpr int kChunk = 256;            // entries per long-row chunk (8 per lane)
-constexpr int kStageUnroll = 4;        // independent gathers in flight per lane
+constexpr int kStageUnroll = 2;        // 4-entry groups staged per lane per round
 
 enum Status : int {
   kRunning = 0, kOptimal = 1, kPrimalInfeasible = 2, kDualInfeasible = 3, kIterLimit = 4,
@@ -37,8 +37,10 @@ enum Status : int {
 };
 
 // Split-CSR structure of one side (see file comment).  The values live in separate arrays
-// (FP64 and, for the mixed-precision path, FP32 copies share this structure).  Long rows are
-// further cut into chunks of at most kChunk entries; a chunk is one warp task.
+// (FP64 and, for the mixed-precision path, FP32 copies share this structure).  Every short-row
+// tile and every long row starts on a 4-entry (16-byte) boundary; the gaps are zero-filled
+// padding that no row's range covers, so tiles and chunks can be read with 128-bit loads.  Long
+// rows are further cut into chunks of at most kChunk entries; a chunk is one warp task.
 struct SideLayout {
   int nrows = 0;
   int L = 32;                // short-row threshold: rows with <= L entries are short
@@ -46,12 +48,14 @@ struct SideLayout {
   int n_long = 0;            // number of long rows
   int n_long_tiles = 0;      // ceil(n_long / 32): groups of 32 long rows sharing an epilogue
   int n_chunks = 0;          // chunks of the long rows
-  const int *ptr_s = nullptr;       // nrows + 1
-  const int *idx_s = nullptr;       // nnz_short
+  const int *ptr_s = nullptr;       // nrows: start of each row in the short arrays (long: empty)
+  const int *tile_end = nullptr;    // n_short_tiles: end of the last row of each tile (unpadded)
+  const int *idx_s = nullptr;       // short entries (padded)
   const uint32_t *long_mask = nullptr;  // n_short_tiles words: bit r set if row 32t+r is long
   const int *long_rows = nullptr;   // n_long row ids (ascending)
-  const int *ptr_l = nullptr;       // n_long + 1
-  const int *idx_l = nullptr;       // nnz_long
+  const int *beg_l = nullptr;       // n_long: start of each long row (4-aligned)
+  const int *end_l = nullptr;       // n_long: end of each long row
+  const int *idx_l = nullptr;       // long entries (padded, plus kChunk slack at the end)
   const int *chunk_ptr = nullptr;   // n_long + 1: chunks of long row i are [chunk_ptr[i], ..[i+1])
   const int *chunk_row = nullptr;   // n_chunks: long-row index of each chunk
   __host__ __device__ int total_items() const { return n_chunks + n_short_tiles; }
@@ -95,7 +99,9 @@ struct Ctl {
   long long check_t;
   long long restarts;
   unsigned int cnt_row, cnt_col;   // last-CTA tickets
-  int pad;
+  int stage;             // 0: the row stage of iteration t is next; 1: the column stage is next
+                         // (each finalisation advances it, so of two kernels launched for the
+                         // same stage only the first one whose mode matches does the work)
 };
 
 struct TraceRec {      // mirrors rhpdhg_trace_rec
@@ -158,35 +164,48 @@ struct Acc {
 };
 
 // Reduce Acc over the CTA (deterministic: fixed shuffle tree, warps summed in index order) and
-// write the CTA's partials to part[blockIdx.x * kMaxPartials + slot].  Returns true in every
-// thread of the last CTA to finish (after a fence), which then owns the grid-level reduction.
+// write the CTA's partials to part[blockIdx.x * kMaxPartials + slot].  Only the slots set in
+// smask (sums) and mmask (maxima) are reduced and written; slots set in prewarp hold, in lane 0,
+// a value already summed over the warp.  Returns true in every thread of the last CTA to finish
+// (after a fence), which then owns the grid-level reduction.
 template <int NS, int NM>
-__device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, double *part, unsigned int *ticket) {
+__device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, unsigned smask, unsigned mmask,
+                                      unsigned prewarp, double *part, unsigned int *ticket) {
   __shared__ double red[kBlockWarps][kMaxPartials];
   __shared__ bool last;
   static_assert(NS + NM <= kMaxPartials, "too many partial slots");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
-    double v = warp_sum(a.s[i]);
+    if (!((smask >> i) & 1u)) continue;
+    const double v = ((prewarp >> i) & 1u) ? a.s[i] : warp_sum(a.s[i]);
     if (lane == 0) red[warp][i] = v;
   }
 #pragma unroll
   for (int i = 0; i < NM; ++i) {
-    double v = warp_max(a.mx[i]);
+    if (!((mmask >> i) & 1u)) continue;
+    const double v = warp_max(a.mx[i]);
     if (lane == 0) red[warp][NS + i] = v;
   }
   __syncthreads();
-  if (threadIdx.x < NS + NM) {
-    const int i = threadIdx.x;
-    double v = red[0][i];
-    for (int w = 1; w < kBlockWarps; ++w) v = (i < NS) ? v + red[w][i] : fmax(v, red[w][i]);
-    part[(size_t)blockIdx.x * kMaxPartials + i] = v;
-  }
-  __threadfence();
-  __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int tk = atomicAdd(ticket, 1u);
+    double *dst = part + (size_t)blockIdx.x * kMaxPartials;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      if (!((smask >> i) & 1u)) continue;
+      double v = red[0][i];
+      for (int w = 1; w < kBlockWarps; ++w) v += red[w][i];
+      dst[i] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+      if (!((mmask >> i) & 1u)) continue;
+      double v = red[0][NS + i];
+      for (int w = 1; w < kBlockWarps; ++w) v = fmax(v, red[w][NS + i]);
+      dst[NS + i] = v;
+    }
+    __threadfence();
+    const unsigned int tk = atomicAdd(ticket, 1u);
     last = (tk == gridDim.x - 1);
   }
   __syncthreads();
@@ -195,17 +214,20 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, double *part, unsigned int
 }
 
 // Warp-collective: reduce the long-row accumulator al of every lane and store it as group grp's
-// partials (lane 0), then clear al.
+// partials (lane 0), then clear al.  Same slot masks as cta_reduce_and_ticket.
 template <int NS, int NM>
-__device__ __forceinline__ void store_group(Acc<NS, NM> &al, double *gpart, int grp) {
+__device__ __forceinline__ void store_group(Acc<NS, NM> &al, unsigned smask, unsigned mmask,
+                                            double *gpart, int grp) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
+    if (!((smask >> i) & 1u)) continue;
     const double v = warp_sum(al.s[i]);
     if (lane == 0) gpart[(size_t)grp * kMaxPartials + i] = v;
   }
 #pragma unroll
   for (int i = 0; i < NM; ++i) {
+    if (!((mmask >> i) & 1u)) continue;
     const double v = warp_max(al.mx[i]);
     if (lane == 0) gpart[(size_t)grp * kMaxPartials + NS + i] = v;
   }
@@ -213,44 +235,47 @@ __device__ __forceinline__ void store_group(Acc<NS, NM> &al, double *gpart, int 
 }
 
 // In the last CTA: reduce the grid's partials in block order, then the long-row groups'
-// partials in group order.  out[i] valid in all threads.
+// partials in group order, for the slots in the masks (others return 0).  out[i] valid in all
+// threads.
 template <int NS, int NM>
-__device__ void grid_finish(const double *part, double *out, const double *gpart = nullptr,
-                            int ngroups = 0) {
+__device__ void grid_finish(const double *part, double *out, unsigned smask, unsigned mmask,
+                            const double *gpart = nullptr, int ngroups = 0) {
   __shared__ double red[kBlockWarps][kMaxPartials];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nb = gridDim.x;
   double v[NS + NM];
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) v[i] = 0.0;
+  const unsigned all = smask | (mmask << NS);
   // thread t sums blocks t, t + blockDim, ... then groups t, t + blockDim, ... (fixed order)
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const double *src = part + (size_t)b * kMaxPartials;
 #pragma unroll
     for (int i = 0; i < NS + NM; ++i) {
-      double p = __ldcg(part + (size_t)b * kMaxPartials + i);
+      if (!((all >> i) & 1u)) continue;
+      const double p = __ldcg(src + i);
       v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
     }
   }
   for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const double *src = gpart + (size_t)g * kMaxPartials;
 #pragma unroll
     for (int i = 0; i < NS + NM; ++i) {
-      double p = __ldcg(gpart + (size_t)g * kMaxPartials + i);
+      if (!((all >> i) & 1u)) continue;
+      const double p = __ldcg(src + i);
       v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
     }
   }
 #pragma unroll
-  for (int i = 0; i < NS; ++i) {
-    double r = warp_sum(v[i]);
-    if (lane == 0) red[warp][i] = r;
-  }
-#pragma unroll
-  for (int i = NS; i < NS + NM; ++i) {
-    double r = warp_max(v[i]);
+  for (int i = 0; i < NS + NM; ++i) {
+    if (!((all >> i) & 1u)) continue;
+    const double r = (i < NS) ? warp_sum(v[i]) : warp_max(v[i]);
     if (lane == 0) red[warp][i] = r;
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) {
+    if (!((all >> i) & 1u)) { out[i] = 0.0; continue; }
     double r = red[0][i];
     for (int w = 1; w < kBlockWarps; ++w) r = (i < NS) ? r + red[w][i] : fmax(r, red[w][i]);
     out[i] = r;
@@ -260,15 +285,44 @@ __device__ void grid_finish(const double *part, double *out, const double *gpart
 
 // ---------------------------------------------------------------------------------------------
 // The tile walker: computes dot = (row of the side operator) . src for every row and calls
-// epi(row, dot) once per row, from one lane, 32 rows per warp at a time.  Work items are the
-// chunks of the long rows followed by the short-row tiles, distributed over all warps of the
+// epi(row, dot, is_long) once per row, from one lane, 32 rows per warp at a time.  Work items are
+// the chunks of the long rows followed by the short-row tiles, distributed over all warps of the
 // grid in a fixed order (so two walks over the same structure give every row to the same warp
-// and lane).  A chunk's warp sums its entries (fixed shuffle tree) into chunk_part; the warp
-// that completes the last chunk of a group of 32 long rows (ticket in group_done, no waiting)
-// adds each row's chunk partials in chunk order and runs the 32 epilogues lane-parallel.  A short
-// tile stages the products of its contiguous entry segment in shared memory, then lane r sums
-// row r's products in column order.  VT is the value type, PT the product/accumulator type;
-// src(j) returns the gathered vector entry; smem is this warp's staging area of 32 * L PTs.
+// and lane).
+//   * A chunk's warp reads its (<= 256) entries as 32 contiguous bytes of indices and values per
+//     lane, sums them (fixed shuffle tree) into chunk_part and takes a ticket; the warp that
+//     completes the last chunk of a group of 32 long rows (no waiting) adds each row's chunk
+//     partials in chunk order, runs the 32 epilogues lane-parallel and calls gdone(group).
+//   * A short tile stages the products of its 16-byte-aligned entry segment in shared memory
+//     (128-bit index / value loads, kStageUnroll gathers per lane in flight), then lane r sums
+//     row r's products with four interleaved accumulators.
+// VT is the value type, PT the product/accumulator type; src(j) returns the gathered vector
+// entry; smem is this warp's staging area of 32 * L + 4 PTs.
+
+template <typename VT>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  float v[4];
+  __device__ __forceinline__ void load(const float *p) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  double v[4];
+  __device__ __forceinline__ void load(const double *p) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+
+__device__ __forceinline__ void load_idx4(const int *p, int *j) {
+  const int4 t = __ldg(reinterpret_cast<const int4 *>(p));
+  j[0] = t.x; j[1] = t.y; j[2] = t.z; j[3] = t.w;
+}
 
 template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone>
 __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals<VT> vals,
@@ -282,22 +336,26 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
     if (item < lay.n_chunks) {
       const int li = lay.chunk_row[item];
       const int c0 = lay.chunk_ptr[li];
-      const int re = lay.ptr_l[li + 1];
-      const int cb = lay.ptr_l[li] + (item - c0) * kChunk;
+      const int re = lay.end_l[li];
+      const int cb = lay.beg_l[li] + (item - c0) * kChunk;   // 4-aligned
       const int ce = min(cb + kChunk, re);
+      // lane reads entries [p0, p0 + 8): two 16-byte index loads, 16 or 32 bytes of values
+      const int p0 = cb + 8 * lane;
       PT s = PT(0);
-      int jj[kChunk / kWarp];
-      VT vv[kChunk / kWarp];
+      if (p0 < ce) {
+        int j[8];
+        Vec4<VT> va, vb;
+        load_idx4(lay.idx_l + p0, j);
+        load_idx4(lay.idx_l + p0 + 4, j + 4);
+        va.load(vals.l + p0);
+        vb.load(vals.l + p0 + 4);
+        PT x[8];
 #pragma unroll
-      for (int u = 0; u < kChunk / kWarp; ++u) {
-        const int p = cb + u * kWarp + lane;
-        jj[u] = p < ce ? lay.idx_l[p] : 0;
-        vv[u] = p < ce ? vals.l[p] : VT(0);
-      }
+        for (int u = 0; u < 8; ++u) x[u] = (p0 + u < ce) ? PT(src(j[u])) : PT(0);
 #pragma unroll
-      for (int u = 0; u < kChunk / kWarp; ++u) {
-        const int p = cb + u * kWarp + lane;
-        if (p < ce) s += PT(vv[u]) * PT(src(jj[u]));
+        for (int u = 0; u < 4; ++u) s += PT(va.v[u]) * x[u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s += PT(vb.v[u]) * x[4 + u];
       }
       s = warp_sum(s);
       const int grp = li / kTileRows;
@@ -330,42 +388,57 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
       const int st = item - lay.n_chunks;
       const int row0 = st * kTileRows;
       const int nr = min(kTileRows, lay.nrows - row0);
-      // row pointers: lane r holds ptr_s[row0 + r] (clamped to the tile end)
-      const int pl = lay.ptr_s[row0 + min(lane, nr)];
-      const int seg_e = lay.ptr_s[row0 + nr];
-      const int seg_b = __shfl_sync(0xffffffffu, pl, 0);
-      const int rb = pl;
-      int re = __shfl_down_sync(0xffffffffu, pl, 1);
-      if (lane == kWarp - 1) re = seg_e;
-      // stage the products of the tile's segment: coalesced value / index loads, kStageUnroll
-      // independent gathers in flight per lane
-      for (int base = seg_b; base < seg_e; base += kWarp * kStageUnroll) {
-        int jj[kStageUnroll];
-        VT vv[kStageUnroll];
+      const int rb = lay.ptr_s[row0 + min(lane, nr - 1)];
+      const int seg_e = lay.tile_end[st];
+      const int seg_b = __shfl_sync(0xffffffffu, rb, 0);     // 4-aligned
+      int re = __shfl_down_sync(0xffffffffu, rb, 1);
+      if (lane >= nr - 1) re = seg_e;
+      const int nvec = (seg_e - seg_b + 3) >> 2;             // groups of 4 entries
+      // stage: lane handles groups g = lane, lane + 32, ... (kStageUnroll at a time)
+      for (int g0 = 0; g0 < nvec; g0 += kWarp * kStageUnroll) {
+        int j[kStageUnroll][4];
+        Vec4<VT> vv[kStageUnroll];
 #pragma unroll
         for (int u = 0; u < kStageUnroll; ++u) {
-          const int p = base + u * kWarp + lane;
-          jj[u] = p < seg_e ? lay.idx_s[p] : 0;
-          vv[u] = p < seg_e ? vals.s[p] : VT(0);
+          const int g = g0 + u * kWarp + lane;
+          if (g < nvec) {
+            load_idx4(lay.idx_s + seg_b + 4 * g, j[u]);
+            vv[u].load(vals.s + seg_b + 4 * g);
+          }
         }
-        PT xs[kStageUnroll];
+        PT x[kStageUnroll][4];
 #pragma unroll
         for (int u = 0; u < kStageUnroll; ++u) {
-          const int p = base + u * kWarp + lane;
-          xs[u] = p < seg_e ? PT(src(jj[u])) : PT(0);
+          const int g = g0 + u * kWarp + lane;
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            x[u][e] = (g < nvec && seg_b + 4 * g + e < seg_e) ? PT(src(j[u][e])) : PT(0);
         }
 #pragma unroll
         for (int u = 0; u < kStageUnroll; ++u) {
-          const int p = base + u * kWarp + lane;
-          if (p < seg_e) smem[p - seg_b] = PT(vv[u]) * xs[u];
+          const int g = g0 + u * kWarp + lane;
+          if (g < nvec) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) smem[4 * g + e] = PT(vv[u].v[e]) * x[u][e];
+          }
         }
       }
       __syncwarp();
       const uint32_t lm = lay.long_mask[st];
       if (lane < nr && !((lm >> lane) & 1u)) {
-        PT s = PT(0);
-        for (int p = rb; p < re; ++p) s += smem[p - seg_b];
-        epi(row0 + lane, s, false);
+        PT s0 = PT(0), s1 = PT(0), s2 = PT(0), s3 = PT(0);
+        int p = rb - seg_b;
+        const int pe = re - seg_b;
+        for (; p + 4 <= pe; p += 4) {
+          s0 += smem[p];
+          s1 += smem[p + 1];
+          s2 += smem[p + 2];
+          s3 += smem[p + 3];
+        }
+        if (p < pe) s0 += smem[p];
+        if (p + 1 < pe) s1 += smem[p + 1];
+        if (p + 2 < pe) s2 += smem[p + 2];
+        epi(row0 + lane, (s0 + s1) + (s2 + s3), false);
       }
       __syncwarp();
     }

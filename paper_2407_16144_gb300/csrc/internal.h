@@ -18,8 +18,8 @@ struct SideStore {
   SideVals<double> v64;
   SideVals<float> v32;
   WalkScratch wa, wb;
-  int *ptr_s = nullptr, *idx_s = nullptr, *long_rows = nullptr, *ptr_l = nullptr,
-      *idx_l = nullptr;
+  int *ptr_s = nullptr, *tile_end = nullptr, *idx_s = nullptr, *long_rows = nullptr,
+      *beg_l = nullptr, *end_l = nullptr, *idx_l = nullptr;
   uint32_t *long_mask = nullptr;
   int *chunk_ptr = nullptr, *chunk_row = nullptr;
   double *val64_s = nullptr, *val64_l = nullptr;

@@ -68,6 +68,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
   }
   ctl->restart_pending = rs ? 1 : 0;
   ctl->cnt_row = 0;
+  ctl->stage = 1;
 }
 
 // Column-kernel slots: sums 0 dx2, 1 xa2, 2 rd2, 3 cx, 4 bnd, 5 cd, 6 uterm, 7 lterm ;
@@ -112,6 +113,7 @@ __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, con
     ctl->n = ctl->n_next;
   }
   ctl->cnt_col = 0;
+  ctl->stage = 0;
 }
 
 }  // namespace rh

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ xt,
            RowVecs v, Ctl *ctl, double *part, IterConsts ic) {
   extern __shared__ double smem[];
-  if (ctl->status != kRunning) return;
+  if (ctl->status != kRunning || ctl->stage != 0) return;
   const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
   const int restart = ctl->restart_pending;
   const double w = ctl->w, sigma = ctl->sigma;
@@ -44,7 +44,7 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   RowAcc a, al;   // al: contributions of long rows (see walk_tiles)
   a.zero();
   al.zero();
-  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
+  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
 
   auto body = [&](int i, double dot, RowAcc &a) {
     const double ytp = v.yt[i], kxtp = v.kxt[i];
@@ -96,13 +96,15 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
     if (lg) body(i, dot, al);
     else body(i, dot, a);
   };
-  auto gdone = [&](int grp) { store_group(al, ws.group_part, grp); };
+  const unsigned smask = 0x7u | (check ? 0x18u : 0u) | (rp ? 0x20u : 0u);
+  const unsigned mmask = rp ? 0x7u : 0u;
+  auto gdone = [&](int grp) { store_group(al, smask, mmask, ws.group_part, grp); };
   auto gather = [&](int j) { return xt[j]; };
   walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 
-  if (cta_reduce_and_ticket(a, part, &ctl->cnt_row)) {
+  if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
     double r[9];
-    grid_finish<6, 3>(part, r, ws.group_part, lay.n_long_tiles);
+    grid_finish<6, 3>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma);
   }
 }
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ ytv,
            ColVecs v, Ctl *ctl, double *part, IterConsts ic, int phase) {
   extern __shared__ double smem[];
-  if (ctl->status != kRunning) return;
+  if (ctl->status != kRunning || ctl->stage != 1) return;
   const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
   const int restart = ctl->restart_pending;
   const double w = ctl->w, tau = ctl->tau;
@@ -121,7 +123,7 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   ColAcc a, al;
   a.zero();
   al.zero();
-  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
+  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
 
   auto body = [&](int j, double dot, ColAcc &a) {
     const double xtj = v.xt[j];
@@ -177,13 +179,15 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
     if (lg) body(j, dot, al);
     else body(j, dot, a);
   };
-  auto gdone = [&](int grp) { store_group(al, ws.group_part, grp); };
+  const unsigned smask = 0x3u | (check ? 0x1Cu : 0u) | (rp ? 0xE0u : 0u);
+  const unsigned mmask = rp ? 0xFu : 0u;
+  auto gdone = [&](int grp) { store_group(al, smask, mmask, ws.group_part, grp); };
   auto gather = [&](int j) { return ytv[j]; };
   walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 
-  if (cta_reduce_and_ticket(a, part, &ctl->cnt_col)) {
+  if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[12];
-    grid_finish<8, 4>(part, r, ws.group_part, lay.n_long_tiles);
+    grid_finish<8, 4>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, phase);
   }
 }

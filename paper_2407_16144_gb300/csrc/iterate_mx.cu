@@ -39,29 +39,37 @@ struct F3 {
   float a = 0.f, b = 0.f, c = 0.f;
 };
 
-template <int RHO2>
+// MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
+// MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
+// launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
+template <int RHO2, int MODE>
 __global__ void __launch_bounds__(kBlockThreads)
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
               const double *__restrict__ dxt64, const double *__restrict__ x0, Ctl *ctl,
               double *part, IterConsts ic) {
   extern __shared__ double smem[];
-  if (ctl->status != kRunning) return;
-  const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
+  if (ctl->status != kRunning || ctl->stage != 0) return;
   const int restart = ctl->restart_pending;
+  if (restart != MODE) return;
+  const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
   const double w = ctl->w, sigma = ctl->sigma;
   const float wf = (float)w, sigf = (float)sigma;
   const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
   const bool rp = (k == 0 && n_ep >= 1);
   const int m_eq = ic.m_eq;
-  double *my64 = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
-  float *my32 = reinterpret_cast<float *>(my64);
+  // staging: FP64 walks use (32 L + 4) doubles per warp, FP32 walks (32 L + 4) floats (the
+  // FP32-only kernels are launched with half the shared memory)
+  double *my64 = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
+  float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
   Acc<6, 3> a, al;
   a.zero();
   al.zero();
   F3 fa, fl;
+  const unsigned smask = 0x7u | (check ? 0x18u : 0u) | (rp ? 0x20u : 0u);
+  const unsigned mmask = rp ? 0x7u : 0u;
 
-  if (restart) {
+  if constexpr (MODE == 1) {
     // Restart point z^{n+1,0} = T(z^{n,k}).  First K x0' with the FP64 matrix (x0' was formed by
     // the preceding column kernel); then, in FP64 throughout, K dxt (dxt = x~ - x0' of this
     // iteration, exact in dxt64) and the dual step, so the restart point's T(z) - z, which
@@ -106,7 +114,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       if (lg) body(i, kd, al);
       else body(i, kd, a);
     };
-    auto gdone = [&](int grp) { store_group(al, wb.group_part, grp); };
+    auto gdone = [&](int grp) { store_group(al, smask, mmask, wb.group_part, grp); };
     auto gB = [&](int j) { return dxt64[j]; };
     walk_tiles<double, double>(lay, v64, gB, my64, wb, epi, gdone);
   } else {
@@ -147,42 +155,54 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       al.s[1] += (double)fl.b;
       al.s[2] += (double)fl.c;
       fl = F3();
-      store_group(al, wb.group_part, grp);
+      store_group(al, smask, mmask, wb.group_part, grp);
     };
     auto gB = [&](int j) { return dxt[j]; };
     walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone);
   }
-  a.s[0] += (double)fa.a;
-  a.s[1] += (double)fa.b;
-  a.s[2] += (double)fa.c;
+  // the FP32 sums (zero in restart mode) are reduced over the warp in FP32, then widened
+  unsigned prewarp = 0u;
+  if constexpr (MODE == 0) {
+    const float f0 = warp_sum(fa.a), f1 = warp_sum(fa.b), f2 = warp_sum(fa.c);
+    a.s[0] = (double)f0;
+    a.s[1] = (double)f1;
+    a.s[2] = (double)f2;
+    prewarp = 0x7u;
+  }
 
-  if (cta_reduce_and_ticket(a, part, &ctl->cnt_row)) {
+  if (cta_reduce_and_ticket(a, smask, mmask, prewarp, part, &ctl->cnt_row)) {
     double r[9];
-    grid_finish<6, 3>(part, r, wb.group_part, lay.n_long_tiles);
+    grid_finish<6, 3>(part, r, smask, mmask, wb.group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma);
   }
 }
 
-template <int RHO2>
+// MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
+template <int RHO2, int MODE>
 __global__ void __launch_bounds__(kBlockThreads)
 k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
               const double *__restrict__ dyt64, const double *__restrict__ y0, Ctl *ctl,
               double *part, IterConsts ic, int phase) {
   extern __shared__ double smem[];
-  if (ctl->status != kRunning) return;
+  if (ctl->status != kRunning || ctl->stage != 1) return;
   const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
   const int restart = ctl->restart_pending;
+  const bool rp = phase == 0 && (k == 0 && n_ep >= 1);
+  if ((restart || rp) != (MODE == 1)) return;
   const double w = ctl->w, tau = ctl->tau;
   const float wf = (float)w, tauf = (float)tau;
   const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
-  const bool rp = phase == 0 && (k == 0 && n_ep >= 1);
-  double *my64 = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
-  float *my32 = reinterpret_cast<float *>(my64);
+  // staging: FP64 walks use (32 L + 4) doubles per warp, FP32 walks (32 L + 4) floats (the
+  // FP32-only kernels are launched with half the shared memory)
+  double *my64 = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
+  float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
   Acc<8, 4> a, al;
   a.zero();
   al.zero();
   F3 fa, fl;
+  const unsigned smask = 0x3u | (check ? 0x1Cu : 0u) | (rp ? 0xE0u : 0u);
+  const unsigned mmask = rp ? 0xFu : 0u;
 
   // checks and certificates at (x~_t, y~_t) given x~_t - x0 (xo), K^T y~_t (kty) and
   // K^T (y~_t - y_t) (ktd), all FP64
@@ -216,10 +236,11 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     al.s[0] += (double)fl.a;
     al.s[1] += (double)fl.b;
     fl = F3();
-    store_group(al, (restart ? wa : wb).group_part, grp);
+    store_group(al, smask, mmask, (restart ? wa : wb).group_part, grp);
   };
 
-  if (restart) {
+  if constexpr (MODE == 1) {
+   if (restart) {
     // z^{n+1,0} = T(z^{n,k}): K^T y0' exactly (FP64 matrix, gathered y0 + dyt), x0' = x0 + dxt,
     // and the next PDHG point x~_{t+1} - x0' in FP64 (kept in dxt64 for the restart point's
     // certificate test)
@@ -247,7 +268,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     };
     auto gA = [&](int i) { return y0[i] + (double)dyt[i]; };
     walk_tiles<double, double>(lay, v64, gA, my64, wa, epi, gdone);
-  } else if (rp) {
+   } else {
     // first iteration of an epoch: K^T (y~ - y0) in FP64 from the exact dyt64 of the row kernel
     auto body = [&](int j, double ktd, Acc<8, 4> &A, F3 &F) {
       const double xo = v.dxt64[j];
@@ -277,6 +298,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     };
     auto gA = [&](int i) { return dyt64[i]; };
     walk_tiles<double, double>(lay, v64, gA, my64, wb, epi, gdone);
+   }
   } else {
     auto body = [&](int j, float ktdyt, Acc<8, 4> &A, F3 &F) {
       const float dxtj = v.dxt[j];
@@ -307,12 +329,17 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     auto gB = [&](int i) { return dyt[i]; };
     walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone);
   }
-  a.s[0] += (double)fa.a;
-  a.s[1] += (double)fa.b;
+  unsigned prewarp = 0u;
+  if (!restart) {       // MODE 0, and the restart-point iterations of MODE 1, sum in FP32
+    const float f0 = warp_sum(fa.a), f1 = warp_sum(fa.b);
+    a.s[0] = (double)f0;
+    a.s[1] = (double)f1;
+    prewarp = 0x3u;
+  }
 
-  if (cta_reduce_and_ticket(a, part, &ctl->cnt_col)) {
+  if (cta_reduce_and_ticket(a, smask, mmask, prewarp, part, &ctl->cnt_col)) {
     double r[12];
-    grid_finish<8, 4>(part, r, (restart ? wa : wb).group_part, lay.n_long_tiles);
+    grid_finish<8, 4>(part, r, smask, mmask, (restart ? wa : wb).group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, phase);
   }
 }
@@ -340,27 +367,41 @@ __global__ void k_zero_f32(int n, float *x) {
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int smem) {
-  if (ic.rho2)
-    k_row_iter_mx<1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                         side.wb, v, dxt, dxt64, x0, ctl, part,
-                                                         ic);
-  else
-    k_row_iter_mx<0><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                         side.wb, v, dxt, dxt64, x0, ctl, part,
-                                                         ic);
+  if (ic.rho2) {
+    k_row_iter_mx<1, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dxt, dxt64, x0, ctl,
+                                                            part, ic);
+    k_row_iter_mx<1, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dxt, dxt64, x0, ctl,
+                                                            part, ic);
+  } else {
+    k_row_iter_mx<0, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dxt, dxt64, x0, ctl,
+                                                            part, ic);
+    k_row_iter_mx<0, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dxt, dxt64, x0, ctl,
+                                                            part, ic);
+  }
 }
 
 void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx &v,
                         const float *dyt, const double *dyt64, const double *y0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int smem, int phase) {
-  if (ic.rho2)
-    k_col_iter_mx<1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                         side.wb, v, dyt, dyt64, y0, ctl, part,
-                                                         ic, phase);
-  else
-    k_col_iter_mx<0><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                         side.wb, v, dyt, dyt64, y0, ctl, part,
-                                                         ic, phase);
+  if (ic.rho2) {
+    k_col_iter_mx<1, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dyt, dyt64, y0, ctl,
+                                                            part, ic, phase);
+    k_col_iter_mx<1, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dyt, dyt64, y0, ctl,
+                                                            part, ic, phase);
+  } else {
+    k_col_iter_mx<0, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dyt, dyt64, y0, ctl,
+                                                            part, ic, phase);
+    k_col_iter_mx<0, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
+                                                            side.wb, v, dyt, dyt64, y0, ctl,
+                                                            part, ic, phase);
+  }
 }
 
 void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const double *xs,
@@ -376,18 +417,24 @@ void zero_f32(cudaStream_t st, int n, float *x) {
 }
 
 void allow_large_smem_mx(int bytes) {
-  cudaFuncSetAttribute(k_row_iter_mx<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_row_iter_mx<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter_mx<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter_mx<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_row_iter_mx<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_row_iter_mx<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_row_iter_mx<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_row_iter_mx<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_col_iter_mx<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_col_iter_mx<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_col_iter_mx<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_col_iter_mx<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// Blocks per SM of the ordinary-iteration kernels (the restart kernels run with the same grid;
+// they are resident-limited too but run rarely).
 int iter_mx_blocks_per_sm(int smem) {
   int b[4] = {0, 0, 0, 0};
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_row_iter_mx<0>, kBlockThreads, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_row_iter_mx<1>, kBlockThreads, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col_iter_mx<0>, kBlockThreads, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[3], k_col_iter_mx<1>, kBlockThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_row_iter_mx<0, 0>, kBlockThreads, smem / 2);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_row_iter_mx<1, 0>, kBlockThreads, smem / 2);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col_iter_mx<0, 0>, kBlockThreads, smem / 2);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[3], k_col_iter_mx<1, 0>, kBlockThreads, smem / 2);
   int mn = b[0];
   for (int i = 1; i < 4; ++i) mn = b[i] < mn ? b[i] : mn;
   return mn;

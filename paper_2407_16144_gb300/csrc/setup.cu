@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <vector>
 
 #include "internal.h"
@@ -106,70 +107,29 @@ __global__ void k_scale_update(int n, const double *stat, double *scale) {
   if (s > 0.0) scale[i] = scale[i] / sqrt(s);
 }
 
-__global__ void k_short_lengths(int nrows, const int *ptr, int L, int *len_s, int *is_long) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r > nrows) return;
-  if (r == nrows) { len_s[r] = 0; return; }
-  int len = ptr[r + 1] - ptr[r];
-  len_s[r] = len <= L ? len : 0;
-  is_long[r] = len > L ? 1 : 0;
-}
-
-__global__ void k_long_lengths(int n_long, const int *long_rows, const int *ptr, int *len_l) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > n_long) return;
-  if (i == n_long) { len_l[i] = 0; return; }
-  int r = long_rows[i];
-  len_l[i] = ptr[r + 1] - ptr[r];
-}
-
-__global__ void k_copy_short(int nrows, const int *ptr, const int *idx, const double *val,
-                             const double *rs, const double *cs, const int *ptr_s, int *idx_s,
-                             double *val_s, float *val32_s, int L) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
-  int b = ptr[r], e = ptr[r + 1];
-  if (e - b > L) return;
-  int o = ptr_s[r];
-  const double sr = rs[r];
-  for (int p = b; p < e; ++p, ++o) {
-    int j = idx[p];
-    idx_s[o] = j;
-    const double v = sr * val[p] * cs[j];
-    val_s[o] = v;
-    if (val32_s) val32_s[o] = (float)v;
-  }
-}
-
-__global__ void k_copy_long(int n_long, const int *long_rows, const int *ptr, const int *idx,
-                            const double *val, const double *rs, const double *cs,
-                            const int *ptr_l, int *idx_l, double *val_l, float *val32_l) {
-  // one warp per long row
-  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (w >= n_long) return;
-  int r = long_rows[w];
-  int b = ptr[r], e = ptr[r + 1];
-  int o = ptr_l[w];
+// copy each row's entries, scaled, to its place in the short or long arrays (warp per row)
+template <bool W32>
+__global__ void k_copy_rows(int nrows, const int *ptr, const int *idx, const double *val,
+                            const double *rs, const double *cs, const int *dst,
+                            const uint32_t *long_mask, int *idx_s, double *val_s, float *val32_s,
+                            int *idx_l, double *val_l, float *val32_l) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const int r = (int)w;
+  const bool lg = (long_mask[r >> 5] >> (r & 31)) & 1u;
+  int *ix = lg ? idx_l : idx_s;
+  double *vx = lg ? val_l : val_s;
+  float *vf = lg ? val32_l : val32_s;
+  const int b = ptr[r], e = ptr[r + 1], o = dst[r];
   const double sr = rs[r];
   for (int p = b + lane; p < e; p += 32) {
-    int j = idx[p];
-    idx_l[o + (p - b)] = j;
+    const int j = idx[p];
     const double v = sr * val[p] * cs[j];
-    val_l[o + (p - b)] = v;
-    if (val32_l) val32_l[o + (p - b)] = (float)v;
+    ix[o + (p - b)] = j;
+    vx[o + (p - b)] = v;
+    if (W32) vf[o + (p - b)] = (float)v;
   }
-}
-
-__global__ void k_long_mask(int nrows, int ntiles, const int *is_long, uint32_t *mask) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
-  uint32_t mk = 0;
-  for (int r = 0; r < 32; ++r) {
-    int row = t * 32 + r;
-    if (row < nrows && is_long[row]) mk |= (1u << r);
-  }
-  mask[t] = mk;
 }
 
 __global__ void k_sumsq_part(int n, const double *x, double *part) {
@@ -228,7 +188,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 k_side_spmv(SideLayout lay, SideVals<double> vals, WalkScratch ws,
             const double *__restrict__ src, double *out) {
   extern __shared__ double smem[];
-  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L);
+  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
   auto epi = [&](int row, double dot, bool) { out[row] = dot; };
   auto gather = [&](int j) { return src[j]; };
   auto gdone = [&](int) {};
@@ -328,115 +288,123 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
                        const double *val, const double *rscale, const double *cscale, int L,
                        bool with32, SideStore *out) {
-  cudaError_t err;
+  (void)nnz;
   SideStore s;
-  int *len_s = nullptr, *is_long = nullptr, *iota = nullptr, *nsel = nullptr, *len_l = nullptr;
-  void *tmp = nullptr;
-  size_t tb = 0, tb2 = 0, tb3 = 0;
-  int h_nlong = 0, h_nnz_s = 0, h_nnz_l = 0;
+  cudaError_t err = cudaSuccess;
   const int ntiles = (nrows + kTileRows - 1) / kTileRows;
+  // ---- structure, on the host -------------------------------------------------------------
+  std::vector<int> hp(nrows + 1);
+  if ((err = cudaMemcpy(hp.data(), ptr, (nrows + 1) * sizeof(int), cudaMemcpyDeviceToHost)))
+    return err;
+  std::vector<int> ptr_s(std::max(nrows, 1)), tile_end(std::max(ntiles, 1)), dst(std::max(nrows, 1));
+  std::vector<uint32_t> mask(std::max(ntiles, 1), 0u);
+  std::vector<int> long_rows, beg_l, end_l, chunk_ptr(1, 0), chunk_row;
+  long long cur = 0, cl = 0;
+  auto align4 = [](long long v) { return (v + 3) & ~3LL; };
+  for (int t = 0; t < ntiles; ++t) {
+    cur = align4(cur);
+    for (int r = t * kTileRows; r < std::min(nrows, (t + 1) * kTileRows); ++r) {
+      const int len = hp[r + 1] - hp[r];
+      ptr_s[r] = (int)cur;
+      if (len <= L) {
+        dst[r] = (int)cur;
+        cur += len;
+      } else {
+        mask[t] |= 1u << (r - t * kTileRows);
+        cl = align4(cl);
+        const int li = (int)long_rows.size();
+        long_rows.push_back(r);
+        beg_l.push_back((int)cl);
+        end_l.push_back((int)(cl + len));
+        dst[r] = (int)cl;
+        cl += len;
+        const int nc = (len + kChunk - 1) / kChunk;
+        for (int c = 0; c < nc; ++c) chunk_row.push_back(li);
+        chunk_ptr.push_back(chunk_ptr.back() + nc);
+      }
+    }
+    tile_end[t] = (int)cur;
+  }
+  const long long nnz_s = align4(cur) + 4, nnz_l = align4(cl) + kChunk;
+  if (nnz_s > INT_MAX || nnz_l > INT_MAX) return cudaErrorInvalidValue;
+  const int nlong = (int)long_rows.size(), nch = (int)chunk_row.size();
   s.lay.nrows = nrows;
   s.lay.L = L;
   s.lay.n_short_tiles = ntiles;
-  if ((err = cudaMalloc(&s.ptr_s, (size_t)(nrows + 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&len_s, (size_t)(nrows + 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&is_long, (size_t)std::max(nrows, 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&iota, (size_t)std::max(nrows, 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&nsel, sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&s.long_mask, (size_t)std::max(ntiles, 1) * sizeof(uint32_t)))) goto fail;
-  if ((err = cudaMalloc(&s.long_rows, (size_t)std::max(nrows, 1) * sizeof(int)))) goto fail;
-  cub::DeviceScan::ExclusiveSum(nullptr, tb, len_s, s.ptr_s, nrows + 1, st);
-  cub::DeviceSelect::Flagged(nullptr, tb2, iota, is_long, s.long_rows, nsel, nrows, st);
-  tb = std::max(tb, tb2);
-  if ((err = cudaMalloc(&tmp, std::max<size_t>(tb, 16)))) goto fail;
-  k_short_lengths<<<nblocks(nrows + 1, 256), 256, 0, st>>>(nrows, ptr, L, len_s, is_long);
-  k_iota<<<nblocks(nrows, 256), 256, 0, st>>>(nrows, iota);
-  cub::DeviceScan::ExclusiveSum(tmp, tb, len_s, s.ptr_s, nrows + 1, st);
-  cudaMemsetAsync(nsel, 0, sizeof(int), st);
-  if (nrows > 0) cub::DeviceSelect::Flagged(tmp, tb, iota, is_long, s.long_rows, nsel, nrows, st);
-  k_long_mask<<<nblocks(ntiles, 128), 128, 0, st>>>(nrows, ntiles, is_long, s.long_mask);
-  count_launches(3);
-  cudaMemcpyAsync(&h_nlong, nsel, sizeof(int), cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(&h_nnz_s, s.ptr_s + nrows, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if ((err = cudaStreamSynchronize(st))) goto fail;
-  s.lay.n_long = h_nlong;
-  s.lay.n_long_tiles = (h_nlong + kTileRows - 1) / kTileRows;
-  s.nnz_short = h_nnz_s;
-  if ((err = cudaMalloc(&s.idx_s, (size_t)std::max(h_nnz_s, 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&s.val64_s, (size_t)std::max(h_nnz_s, 1) * sizeof(double)))) goto fail;
-  if (with32 && (err = cudaMalloc(&s.val32_s, (size_t)std::max(h_nnz_s, 1) * sizeof(float))))
-    goto fail;
-  if ((err = cudaMalloc(&s.ptr_l, (size_t)(h_nlong + 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&len_l, (size_t)(h_nlong + 1) * sizeof(int)))) goto fail;
-  k_copy_short<<<nblocks(nrows, 128), 128, 0, st>>>(nrows, ptr, idx, val, rscale, cscale,
-                                                     s.ptr_s, s.idx_s, s.val64_s, s.val32_s, L);
-  k_long_lengths<<<nblocks(h_nlong + 1, 256), 256, 0, st>>>(h_nlong, s.long_rows, ptr, len_l);
-  count_launches(2 + (h_nlong > 0 ? 1 : 0));
-  cub::DeviceScan::ExclusiveSum(nullptr, tb3, len_l, s.ptr_l, h_nlong + 1, st);
-  if (tb3 > tb) {
-    cudaFree(tmp);
-    tmp = nullptr;
-    tb = tb3;
-    if ((err = cudaMalloc(&tmp, tb))) goto fail;
+  s.lay.n_long = nlong;
+  s.lay.n_long_tiles = (nlong + kTileRows - 1) / kTileRows;
+  s.lay.n_chunks = nch;
+  s.nnz_short = nnz_s;
+  s.nnz_long = nnz_l;
+  const size_t ng = (size_t)std::max(s.lay.n_long_tiles, 1);
+  int *d_dst = nullptr;
+  auto up = [&](int **d, const std::vector<int> &h) -> cudaError_t {
+    cudaError_t e = cudaMalloc(d, std::max<size_t>(h.size(), 1) * sizeof(int));
+    if (e == cudaSuccess && !h.empty())
+      e = cudaMemcpy(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice);
+    return e;
+  };
+#define TRY(x)                 \
+  do {                         \
+    if ((err = (x))) goto fail; \
+  } while (0)
+  TRY(up(&s.ptr_s, ptr_s));
+  TRY(up(&s.tile_end, tile_end));
+  TRY(up(&s.long_rows, long_rows));
+  TRY(up(&s.beg_l, beg_l));
+  TRY(up(&s.end_l, end_l));
+  TRY(up(&s.chunk_ptr, chunk_ptr));
+  TRY(up(&s.chunk_row, chunk_row));
+  TRY(up(&d_dst, dst));
+  TRY(cudaMalloc(&s.long_mask, mask.size() * sizeof(uint32_t)));
+  TRY(cudaMemcpy(s.long_mask, mask.data(), mask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  // ---- entries (zero padding), scaled on the device ------------------------------------------
+  TRY(cudaMalloc(&s.idx_s, nnz_s * sizeof(int)));
+  TRY(cudaMalloc(&s.val64_s, nnz_s * sizeof(double)));
+  TRY(cudaMalloc(&s.idx_l, nnz_l * sizeof(int)));
+  TRY(cudaMalloc(&s.val64_l, nnz_l * sizeof(double)));
+  TRY(cudaMemsetAsync(s.idx_s, 0, nnz_s * sizeof(int), st));
+  TRY(cudaMemsetAsync(s.val64_s, 0, nnz_s * sizeof(double), st));
+  TRY(cudaMemsetAsync(s.idx_l, 0, nnz_l * sizeof(int), st));
+  TRY(cudaMemsetAsync(s.val64_l, 0, nnz_l * sizeof(double), st));
+  if (with32) {
+    TRY(cudaMalloc(&s.val32_s, nnz_s * sizeof(float)));
+    TRY(cudaMalloc(&s.val32_l, nnz_l * sizeof(float)));
+    TRY(cudaMemsetAsync(s.val32_s, 0, nnz_s * sizeof(float), st));
+    TRY(cudaMemsetAsync(s.val32_l, 0, nnz_l * sizeof(float), st));
   }
-  cub::DeviceScan::ExclusiveSum(tmp, tb, len_l, s.ptr_l, h_nlong + 1, st);
-  cudaMemcpyAsync(&h_nnz_l, s.ptr_l + h_nlong, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if ((err = cudaStreamSynchronize(st))) goto fail;
-  s.nnz_long = h_nnz_l;
-  if ((err = cudaMalloc(&s.idx_l, (size_t)std::max(h_nnz_l, 1) * sizeof(int)))) goto fail;
-  if ((err = cudaMalloc(&s.val64_l, (size_t)std::max(h_nnz_l, 1) * sizeof(double)))) goto fail;
-  if (with32 && (err = cudaMalloc(&s.val32_l, (size_t)std::max(h_nnz_l, 1) * sizeof(float))))
-    goto fail;
-  if (h_nlong > 0)
-    k_copy_long<<<nblocks((long long)h_nlong * 32, 128), 128, 0, st>>>(
-        h_nlong, s.long_rows, ptr, idx, val, rscale, cscale, s.ptr_l, s.idx_l, s.val64_l,
-        s.val32_l);
-  if ((err = cudaStreamSynchronize(st))) goto fail;
-  if ((err = cudaGetLastError())) goto fail;
-  {
-    // chunks of the long rows (host-side: n_long + 1 offsets)
-    std::vector<int> hpl(h_nlong + 1), hcp(h_nlong + 1), hcr;
-    if ((err = cudaMemcpy(hpl.data(), s.ptr_l, (h_nlong + 1) * sizeof(int),
-                          cudaMemcpyDeviceToHost)))
-      goto fail;
-    hcp[0] = 0;
-    for (int i = 0; i < h_nlong; ++i) {
-      const int len = hpl[i + 1] - hpl[i];
-      const int nc = (len + kChunk - 1) / kChunk;
-      hcp[i + 1] = hcp[i] + nc;
-      for (int c = 0; c < nc; ++c) hcr.push_back(i);
-    }
-    const int nch = hcp[h_nlong];
-    s.lay.n_chunks = nch;
-    if ((err = cudaMalloc(&s.chunk_ptr, (size_t)(h_nlong + 1) * sizeof(int)))) goto fail;
-    if ((err = cudaMalloc(&s.chunk_row, (size_t)std::max(nch, 1) * sizeof(int)))) goto fail;
-    if ((err = cudaMalloc(&s.part_a, (size_t)std::max(nch, 1) * sizeof(double)))) goto fail;
-    if ((err = cudaMalloc(&s.part_b, (size_t)std::max(nch, 1) * sizeof(double)))) goto fail;
-    const size_t ng = (size_t)std::max(s.lay.n_long_tiles, 1);
-    if ((err = cudaMalloc(&s.done_a, ng * sizeof(unsigned int)))) goto fail;
-    if ((err = cudaMalloc(&s.done_b, ng * sizeof(unsigned int)))) goto fail;
-    if ((err = cudaMalloc(&s.gpart_a, ng * kMaxPartials * sizeof(double)))) goto fail;
-    if ((err = cudaMalloc(&s.gpart_b, ng * kMaxPartials * sizeof(double)))) goto fail;
-    if ((err = cudaMemcpy(s.chunk_ptr, hcp.data(), (h_nlong + 1) * sizeof(int),
-                          cudaMemcpyHostToDevice)))
-      goto fail;
-    if (nch > 0 && (err = cudaMemcpy(s.chunk_row, hcr.data(), nch * sizeof(int),
-                                     cudaMemcpyHostToDevice)))
-      goto fail;
-    if ((err = cudaMemset(s.done_a, 0, ng * sizeof(unsigned int)))) goto fail;
-    if ((err = cudaMemset(s.done_b, 0, ng * sizeof(unsigned int)))) goto fail;
+  if (nrows > 0) {
+    const int nb = nblocks((long long)nrows * 32, 256);
+    if (with32)
+      k_copy_rows<true><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rscale, cscale, d_dst,
+                                            s.long_mask, s.idx_s, s.val64_s, s.val32_s, s.idx_l,
+                                            s.val64_l, s.val32_l);
+    else
+      k_copy_rows<false><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rscale, cscale, d_dst,
+                                             s.long_mask, s.idx_s, s.val64_s, s.val32_s, s.idx_l,
+                                             s.val64_l, s.val32_l);
+    count_launches(1);
   }
-  cudaFree(len_s);
-  cudaFree(is_long);
-  cudaFree(iota);
-  cudaFree(nsel);
-  cudaFree(len_l);
-  cudaFree(tmp);
+  // ---- walk scratch ------------------------------------------------------------------------
+  TRY(cudaMalloc(&s.part_a, (size_t)std::max(nch, 1) * sizeof(double)));
+  TRY(cudaMalloc(&s.part_b, (size_t)std::max(nch, 1) * sizeof(double)));
+  TRY(cudaMalloc(&s.done_a, ng * sizeof(unsigned int)));
+  TRY(cudaMalloc(&s.done_b, ng * sizeof(unsigned int)));
+  TRY(cudaMalloc(&s.gpart_a, ng * kMaxPartials * sizeof(double)));
+  TRY(cudaMalloc(&s.gpart_b, ng * kMaxPartials * sizeof(double)));
+  TRY(cudaMemsetAsync(s.done_a, 0, ng * sizeof(unsigned int), st));
+  TRY(cudaMemsetAsync(s.done_b, 0, ng * sizeof(unsigned int), st));
+  TRY(cudaStreamSynchronize(st));
+  TRY(cudaGetLastError());
+#undef TRY
+  cudaFree(d_dst);
   s.lay.ptr_s = s.ptr_s;
+  s.lay.tile_end = s.tile_end;
   s.lay.idx_s = s.idx_s;
   s.lay.long_mask = s.long_mask;
   s.lay.long_rows = s.long_rows;
-  s.lay.ptr_l = s.ptr_l;
+  s.lay.beg_l = s.beg_l;
+  s.lay.end_l = s.end_l;
   s.lay.idx_l = s.idx_l;
   s.lay.chunk_ptr = s.chunk_ptr;
   s.lay.chunk_row = s.chunk_row;
@@ -453,18 +421,14 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   *out = s;
   return cudaSuccess;
 fail:
-  cudaFree(len_s);
-  cudaFree(is_long);
-  cudaFree(iota);
-  cudaFree(nsel);
-  cudaFree(len_l);
-  cudaFree(tmp);
+  cudaFree(d_dst);
   free_side(&s);
   return err;
 }
 
 void free_side(SideStore *s) {
-  void *bufs[] = {s->ptr_s, s->idx_s, s->long_mask, s->long_rows, s->ptr_l, s->idx_l,
+  void *bufs[] = {s->ptr_s, s->tile_end, s->idx_s, s->long_mask, s->long_rows, s->beg_l,
+                  s->end_l, s->idx_l,
                   s->chunk_ptr, s->chunk_row, s->val64_s, s->val64_l, s->val32_s, s->val32_l,
                   s->part_a, s->part_b, s->done_a, s->done_b, s->gpart_a, s->gpart_b};
   for (void *b : bufs) cudaFree(b);
@@ -499,7 +463,7 @@ void allow_large_smem_setup(int bytes) {
 }
 
 void side_spmv(cudaStream_t st, const SideStore &side, const double *src, double *out, int grid) {
-  int smem = kBlockWarps * kTileRows * side.lay.L * (int)sizeof(double);
+  int smem = kBlockWarps * (kTileRows * side.lay.L + 4) * (int)sizeof(double);
   k_side_spmv<<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, src, out);
   count_launches(1);
 }
