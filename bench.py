@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algorithm", type=int, default=1)
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=1,
+                    help="headline precision: 1 = FP32 iterates / FP64 restarts, 0 = FP64")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -266,6 +267,13 @@ def run_ours(args):
     ok = all(r.status == rhpdhg.STATUS_OPTIMAL for r in results)
     # e2e through host buffers
     e2e_outs, e2e_ms = timed(step_host, max(2, min(args.steps, 3)))
+    # the other precision on the same workload (reported beside the headline)
+    other = 1 - args.precision
+    oparams = dict(params, precision=other)
+    so = rhpdhg.Solver(dev, device=True, stream=sh, **oparams)
+    so.solve(1)
+    ro = so.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
+    so.close()
     # kernel timing (CUDA events around each launch of the two iteration kernels)
     s = rhpdhg.Solver(dev, device=True, stream=sh, profile=1, **params)
     s.solve(1)
@@ -303,6 +311,10 @@ def run_ours(args):
         "time_to_tol_s": ms_step / 1000.0, "solve_only_s": solve_s, "iters": iters,
         "iters_per_s": iters / solve_s, "all_optimal": ok,
         "rel_kkt": max(results[-1].rel_p, results[-1].rel_d, results[-1].rel_gap),
+        "other_precision": {"precision": "fp64" if other == 0 else "fp32 iterates, fp64 restarts",
+                            "status": ro.status_name, "iters": ro.iters,
+                            "solve_s": ro.solve_seconds,
+                            "iters_per_s": ro.iters / ro.solve_seconds},
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": problem_bytes(lp),
