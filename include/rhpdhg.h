@@ -241,6 +241,48 @@ int rhpdhg_kkt_eval(const rhpdhg_problem *lp, const double *x, const double *y,
 int rhpdhg_kkt_eval_noalloc(const rhpdhg_problem *lp, const double *x, const double *y,
                             void *cuda_stream, double *out);
 
+/* ---- batched solver ---------------------------------------------------------------------
+ * Many small LPs advance together in one persistent launch, one CTA per LP (the CTA also runs
+ * the LP's set-up: scaling, power iteration, primal weight).  Each LP's computation stays inside
+ * its CTA, so its result does not depend on which other LPs share the launch.  The method and
+ * its statuses are those of rhpdhg_solve (FP64).  Slots are described by a table in device
+ * memory, so one captured graph is replayed while LPs are added and removed. */
+typedef struct rhpdhg_batch rhpdhg_batch;
+
+/* Creates a batch with max_slots slots and a device arena of arena_bytes for the LPs' data.
+ * cuda_stream: stream of all work (NULL = a private stream). */
+int rhpdhg_batch_create(int32_t max_slots, int64_t arena_bytes, void *cuda_stream,
+                        rhpdhg_batch **out);
+
+/* Copies an LP (host memory, validated and transposed on the host) into a free slot; its set-up
+ * runs in the next step.  params: as for rhpdhg_create (precision must be 0; NULL = defaults).
+ * Returns RHPDHG_BUSY when no slot is free and RHPDHG_ERR_OOM when the arena lacks
+ * rhpdhg_batch_bytes_needed(lp) contiguous bytes. */
+int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_params *params,
+                     int32_t *slot);
+
+/* One launch: every active slot advances by up to iters PDHG evaluations (or runs its set-up and
+ * then iterates).  Synchronises the batch stream and refreshes every slot's status. */
+int rhpdhg_batch_step(rhpdhg_batch *b, int32_t iters);
+
+/* RHPDHG_BUSY while the slot's LP runs; then fills *r like rhpdhg_poll (solve_seconds = 0). */
+int rhpdhg_batch_poll(rhpdhg_batch *b, int32_t slot, rhpdhg_result *r);
+
+/* Frees a slot (finished or not) and its arena region. */
+int rhpdhg_batch_remove(rhpdhg_batch *b, int32_t slot);
+
+/* Status of a slot after the last step (RHPDHG_STATUS_*), or -1 for an empty slot. */
+int rhpdhg_batch_slot_status(const rhpdhg_batch *b, int32_t slot);
+
+/* Free arena bytes (sum of free regions), and the bytes one LP needs. */
+int64_t rhpdhg_batch_free_bytes(const rhpdhg_batch *b);
+int64_t rhpdhg_batch_bytes_needed(const rhpdhg_problem *lp);
+
+/* Kernel launches issued by the batch so far (steps and result extractions). */
+int64_t rhpdhg_batch_launch_count(const rhpdhg_batch *b);
+
+void rhpdhg_batch_free(rhpdhg_batch *b);
+
 /* Number of CUDA kernels of this library the handle has launched so far (create and every
  * solve; a replay of a captured graph counts each kernel node it runs).  Kernels of the CUB
  * library used for the transpose during create are not counted.  Returns -1 for NULL. */

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "internal.h"
 
 namespace rh {
 
@@ -114,6 +115,132 @@ __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, con
   }
   ctl->cnt_col = 0;
   ctl->stage = 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The FP64 per-row epilogues of one PDHG evaluation, shared by the tiled single-LP kernels and
+// the CTA-resident batched kernel.
+
+struct StepFlags {
+  int restart;      // the pending transition is a restart: z_t = T(z_{t-1})
+  double w;         // Halpern weight (k+1)/(k+2) of the pending blend
+  double step;      // sigma (row epilogue) or tau (column epilogue)
+  bool check;       // termination-check iteration
+  bool rp;          // restart point (k == 0, n >= 1): certificate test
+  int m_eq;
+};
+
+// Row i of K^ x~_t = dot: forms y_t and K x_t by the pending blend (eq. hpdhg / eq. hrpdhg, or
+// the restart point), takes the dual step of eq. pdhg, and accumulates the fixed-point-residual
+// parts (0 ||dy||^2, 1 dy^T (K x - K x~), 2 ||y~ - y0||^2), the check parts (3 primal residual^2,
+// 4 q^T y~) and the certificate parts (5 q^T (y~ - y), maxima 0..2).
+template <int RHO2>
+__device__ __forceinline__ void row_epilogue(int i, double dot, const RowVecs &v,
+                                             const StepFlags &f, Acc<6, 3> &a) {
+  const double ytp = v.yt[i], kxtp = v.kxt[i];
+  const double w = f.w, sigma = f.step;
+  double yi, kxi, y0i;
+  if (f.restart) {
+    yi = ytp; kxi = kxtp; y0i = yi;
+    v.y0[i] = yi; v.kx0[i] = kxi;
+    if (RHO2) { v.y[i] = yi; v.kx[i] = kxi; }
+  } else {
+    y0i = v.y0[i];
+    const double kx0i = v.kx0[i];
+    if (RHO2) {
+      yi = w * (2.0 * ytp - v.y[i]) + (1.0 - w) * y0i;
+      kxi = w * (2.0 * kxtp - v.kx[i]) + (1.0 - w) * kx0i;
+      v.y[i] = yi; v.kx[i] = kxi;
+    } else {
+      yi = w * ytp + (1.0 - w) * y0i;
+      kxi = w * kxtp + (1.0 - w) * kx0i;
+    }
+  }
+  const double qi = v.q[i];
+  double yn = yi + sigma * (qi - 2.0 * dot + kxi);
+  if (i >= f.m_eq) yn = fmax(yn, 0.0);
+  v.yt[i] = yn;
+  v.kxt[i] = dot;
+  const double dy = yi - yn;
+  a.s[0] += dy * dy;
+  a.s[1] += dy * (kxi - dot);
+  const double ya = yn - y0i;
+  a.s[2] += ya * ya;
+  if (f.check) {
+    double r = (qi - dot) * v.dinv[i];
+    if (i >= f.m_eq) r = fmax(r, 0.0);
+    a.s[3] += r * r;
+    a.s[4] += qi * yn;
+  }
+  if (f.rp) {
+    const double vy = yn - yi;            // y-part of T(z) - z at the restart point
+    a.s[5] += qi * vy;
+    const double di = v.d[i];
+    if (i >= f.m_eq) a.mx[0] = fmax(a.mx[0], fmax(-vy * di, 0.0));
+    const double kd = (dot - kxi) * v.dinv[i];   // K d (unscaled), d = x~ - x
+    if (i < f.m_eq) a.mx[1] = fmax(a.mx[1], fabs(kd));
+    else a.mx[2] = fmax(a.mx[2], fmax(-kd, 0.0));
+    v.certy[i] = vy * di;
+  }
+}
+
+// Column j of K^T y~_t = dot: the check parts at (x~_t, y~_t) (2 dual residual^2, 3 c^T x~,
+// 4 bound terms of the dual objective), the certificate parts at restart points (5 c^T d,
+// 6/7 bound terms of the ray objective, maxima 0..3), then the blend to x_{t+1} and the primal
+// step x~_{t+1} = proj_X(x_{t+1} - tau (c - K^T y_{t+1})) with parts 0 ||x - x~||^2,
+// 1 ||x~ - x0||^2.
+template <int RHO2>
+__device__ __forceinline__ void col_epilogue(int j, double dot, const ColVecs &v,
+                                             const StepFlags &f, Acc<8, 4> &a) {
+  const double xtj = v.xt[j];
+  const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
+  const double w = f.w, tau = f.step;
+  if (f.check) {
+    const double g = cj - dot;
+    const double lam = proj_lambda(g, lj, uj);
+    const double rd = (g - lam) * v.einv[j];
+    a.s[2] += rd * rd;
+    a.s[3] += cj * xtj;
+    if (lam > 0.0) a.s[4] += lj * lam;
+    else if (lam < 0.0) a.s[4] += uj * lam;
+    v.xout[j] = xtj;
+  }
+  double x0j = v.x0[j], kty0j = v.kty0[j];
+  if (f.rp) {
+    // restart point: x_t = x^{n,0} and K^T y_t = K^T y^{n,0}
+    const double dsc = xtj - x0j;               // x-part of T(z) - z (scaled)
+    a.s[5] += cj * dsc;
+    const double du = dsc * v.e[j];
+    const bool lf = isfinite(lj), uf = isfinite(uj);
+    if (lf) a.mx[0] = fmax(a.mx[0], fmax(-du, 0.0));
+    if (uf) a.mx[1] = fmax(a.mx[1], fmax(du, 0.0));
+    const double kv = dot - kty0j;              // K^T (y~ - y) (scaled)
+    if (uf) a.s[6] += fmax(kv, 0.0) * uj;
+    else a.mx[2] = fmax(a.mx[2], fmax(kv * v.einv[j], 0.0));
+    if (lf) a.s[7] += fmax(-kv, 0.0) * lj;
+    else a.mx[3] = fmax(a.mx[3], fmax(-kv * v.einv[j], 0.0));
+    v.certx[j] = du;
+  }
+  double xn, kn;
+  if (f.restart) {
+    xn = xtj; kn = dot;
+    v.x0[j] = xn; v.kty0[j] = kn;
+    x0j = xn; kty0j = kn;
+    if (RHO2) { v.x[j] = xn; v.kty[j] = kn; }
+  } else if (RHO2) {
+    xn = w * (2.0 * xtj - v.x[j]) + (1.0 - w) * x0j;
+    kn = w * (2.0 * dot - v.kty[j]) + (1.0 - w) * kty0j;
+    v.x[j] = xn; v.kty[j] = kn;
+  } else {
+    xn = w * xtj + (1.0 - w) * x0j;
+    kn = w * dot + (1.0 - w) * kty0j;
+  }
+  const double xtn = fmin(fmax(xn - tau * (cj - kn), lj), uj);
+  v.xt[j] = xtn;
+  const double dx = xn - xtn;
+  a.s[0] += dx * dx;
+  const double xa = xtn - x0j;
+  a.s[1] += xa * xa;
 }
 
 }  // namespace rh

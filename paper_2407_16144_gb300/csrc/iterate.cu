@@ -46,52 +46,8 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   al.zero();
   double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
 
-  auto body = [&](int i, double dot, RowAcc &a) {
-    const double ytp = v.yt[i], kxtp = v.kxt[i];
-    double yi, kxi, y0i;
-    if (restart) {
-      yi = ytp; kxi = kxtp; y0i = yi;
-      v.y0[i] = yi; v.kx0[i] = kxi;
-      if (RHO2) { v.y[i] = yi; v.kx[i] = kxi; }
-    } else {
-      y0i = v.y0[i];
-      const double kx0i = v.kx0[i];
-      if (RHO2) {
-        yi = w * (2.0 * ytp - v.y[i]) + (1.0 - w) * y0i;
-        kxi = w * (2.0 * kxtp - v.kx[i]) + (1.0 - w) * kx0i;
-        v.y[i] = yi; v.kx[i] = kxi;
-      } else {
-        yi = w * ytp + (1.0 - w) * y0i;
-        kxi = w * kxtp + (1.0 - w) * kx0i;
-      }
-    }
-    const double qi = v.q[i];
-    double yn = yi + sigma * (qi - 2.0 * dot + kxi);
-    if (i >= m_eq) yn = fmax(yn, 0.0);
-    v.yt[i] = yn;
-    v.kxt[i] = dot;
-    const double dy = yi - yn;
-    a.s[0] += dy * dy;
-    a.s[1] += dy * (kxi - dot);
-    const double ya = yn - y0i;
-    a.s[2] += ya * ya;
-    if (check) {
-      double r = (qi - dot) * v.dinv[i];
-      if (i >= m_eq) r = fmax(r, 0.0);
-      a.s[3] += r * r;
-      a.s[4] += qi * yn;
-    }
-    if (rp) {
-      const double vy = yn - yi;            // y-part of T(z) - z at the restart point
-      a.s[5] += qi * vy;
-      const double di = v.d[i];
-      if (i >= m_eq) a.mx[0] = fmax(a.mx[0], fmax(-vy * di, 0.0));
-      const double kd = (dot - kxi) * v.dinv[i];   // K d (unscaled), d = x~ - x
-      if (i < m_eq) a.mx[1] = fmax(a.mx[1], fabs(kd));
-      else a.mx[2] = fmax(a.mx[2], fmax(-kd, 0.0));
-      v.certy[i] = vy * di;
-    }
-  };
+  StepFlags fl{restart, w, sigma, check, rp, m_eq};
+  auto body = [&](int i, double dot, RowAcc &acc) { row_epilogue<RHO2>(i, dot, v, fl, acc); };
   auto epi = [&](int i, double dot, bool lg) {
     if (lg) body(i, dot, al);
     else body(i, dot, a);
@@ -125,56 +81,8 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   al.zero();
   double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
 
-  auto body = [&](int j, double dot, ColAcc &a) {
-    const double xtj = v.xt[j];
-    const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
-    if (check) {
-      const double g = cj - dot;
-      const double lam = proj_lambda(g, lj, uj);
-      const double rd = (g - lam) * v.einv[j];
-      a.s[2] += rd * rd;
-      a.s[3] += cj * xtj;
-      if (lam > 0.0) a.s[4] += lj * lam;
-      else if (lam < 0.0) a.s[4] += uj * lam;
-      v.xout[j] = xtj;
-    }
-    double x0j = v.x0[j], kty0j = v.kty0[j];
-    if (rp) {
-      // restart point: x_t = x^{n,0} and K^T y_t = K^T y^{n,0}
-      const double dsc = xtj - x0j;               // x-part of T(z) - z (scaled)
-      a.s[5] += cj * dsc;
-      const double du = dsc * v.e[j];
-      const bool lf = isfinite(lj), uf = isfinite(uj);
-      if (lf) a.mx[0] = fmax(a.mx[0], fmax(-du, 0.0));
-      if (uf) a.mx[1] = fmax(a.mx[1], fmax(du, 0.0));
-      const double kv = dot - kty0j;              // K^T (y~ - y) (scaled)
-      if (uf) a.s[6] += fmax(kv, 0.0) * uj;
-      else a.mx[2] = fmax(a.mx[2], fmax(kv * v.einv[j], 0.0));
-      if (lf) a.s[7] += fmax(-kv, 0.0) * lj;
-      else a.mx[3] = fmax(a.mx[3], fmax(-kv * v.einv[j], 0.0));
-      v.certx[j] = du;
-    }
-    double xn, kn;
-    if (restart) {
-      xn = xtj; kn = dot;
-      v.x0[j] = xn; v.kty0[j] = kn;
-      x0j = xn; kty0j = kn;
-      if (RHO2) { v.x[j] = xn; v.kty[j] = kn; }
-    } else if (RHO2) {
-      xn = w * (2.0 * xtj - v.x[j]) + (1.0 - w) * x0j;
-      kn = w * (2.0 * dot - v.kty[j]) + (1.0 - w) * kty0j;
-      v.x[j] = xn; v.kty[j] = kn;
-    } else {
-      xn = w * xtj + (1.0 - w) * x0j;
-      kn = w * dot + (1.0 - w) * kty0j;
-    }
-    const double xtn = fmin(fmax(xn - tau * (cj - kn), lj), uj);
-    v.xt[j] = xtn;
-    const double dx = xn - xtn;
-    a.s[0] += dx * dx;
-    const double xa = xtn - x0j;
-    a.s[1] += xa * xa;
-  };
+  StepFlags fl{restart, w, tau, check, rp, ic.m_eq};
+  auto body = [&](int j, double dot, ColAcc &acc) { col_epilogue<RHO2>(j, dot, v, fl, acc); };
   auto epi = [&](int j, double dot, bool lg) {
     if (lg) body(j, dot, al);
     else body(j, dot, a);

@@ -70,7 +70,10 @@ class rhpdhg_trace_rec(C.Structure):
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
             "rhpdhg_cancel", "rhpdhg_free", "rhpdhg_last_error", "rhpdhg_get_state",
             "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_kernel_times",
-            "rhpdhg_launch_count", "rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc"]
+            "rhpdhg_launch_count", "rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc",
+            "rhpdhg_batch_create", "rhpdhg_batch_add", "rhpdhg_batch_step", "rhpdhg_batch_poll",
+            "rhpdhg_batch_remove", "rhpdhg_batch_slot_status", "rhpdhg_batch_free_bytes",
+            "rhpdhg_batch_bytes_needed", "rhpdhg_batch_launch_count", "rhpdhg_batch_free"]
 
 _lib = None
 
@@ -105,6 +108,17 @@ def load(path: str = LIB_PATH):
                                       C.c_void_p, _dp]),
         "rhpdhg_kkt_eval_noalloc": (C.c_int, [C.POINTER(rhpdhg_problem), C.c_void_p,
                                               C.c_void_p, C.c_void_p, _dp]),
+        "rhpdhg_batch_create": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.POINTER(H)]),
+        "rhpdhg_batch_add": (C.c_int, [H, C.POINTER(rhpdhg_problem), C.POINTER(rhpdhg_params),
+                                       C.POINTER(C.c_int32)]),
+        "rhpdhg_batch_step": (C.c_int, [H, C.c_int32]),
+        "rhpdhg_batch_poll": (C.c_int, [H, C.c_int32, C.POINTER(rhpdhg_result)]),
+        "rhpdhg_batch_remove": (C.c_int, [H, C.c_int32]),
+        "rhpdhg_batch_slot_status": (C.c_int, [H, C.c_int32]),
+        "rhpdhg_batch_free_bytes": (C.c_int64, [H]),
+        "rhpdhg_batch_bytes_needed": (C.c_int64, [C.POINTER(rhpdhg_problem)]),
+        "rhpdhg_batch_launch_count": (C.c_int64, [H]),
+        "rhpdhg_batch_free": (None, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -193,6 +207,158 @@ def rhpdhg_kkt_eval_noalloc(lp: rhpdhg_problem, x, y, stream: int = 0):
     rc = load().rhpdhg_kkt_eval_noalloc(C.byref(lp), C.c_void_p(x), C.c_void_p(y or None),
                                         C.c_void_p(stream or None), out)
     return rc, list(out)
+
+
+def rhpdhg_batch_create(max_slots: int, arena_bytes: int, stream: int = 0):
+    h = C.c_void_p()
+    rc = load().rhpdhg_batch_create(max_slots, arena_bytes, C.c_void_p(stream or None),
+                                    C.byref(h))
+    return rc, h
+
+
+def rhpdhg_batch_add(b, lp: rhpdhg_problem, params: Optional[rhpdhg_params]):
+    slot = C.c_int32(-1)
+    rc = load().rhpdhg_batch_add(b, C.byref(lp), C.byref(params) if params else None,
+                                 C.byref(slot))
+    return rc, slot.value
+
+
+def rhpdhg_batch_step(b, iters: int) -> int:
+    return load().rhpdhg_batch_step(b, iters)
+
+
+def rhpdhg_batch_poll(b, slot: int, r: rhpdhg_result) -> int:
+    return load().rhpdhg_batch_poll(b, slot, C.byref(r))
+
+
+def rhpdhg_batch_remove(b, slot: int) -> int:
+    return load().rhpdhg_batch_remove(b, slot)
+
+
+def rhpdhg_batch_slot_status(b, slot: int) -> int:
+    return load().rhpdhg_batch_slot_status(b, slot)
+
+
+def rhpdhg_batch_free_bytes(b) -> int:
+    return load().rhpdhg_batch_free_bytes(b)
+
+
+def rhpdhg_batch_bytes_needed(lp: rhpdhg_problem) -> int:
+    return load().rhpdhg_batch_bytes_needed(C.byref(lp))
+
+
+def rhpdhg_batch_launch_count(b) -> int:
+    return load().rhpdhg_batch_launch_count(b)
+
+
+def rhpdhg_batch_free(b) -> None:
+    load().rhpdhg_batch_free(b)
+
+
+def host_problem(lp, keep: list) -> rhpdhg_problem:
+    """rhpdhg_problem over an lpgen.LP's host arrays (contiguous copies appended to keep)."""
+    prob = rhpdhg_problem()
+    prob.m_eq, prob.m_ineq, prob.n = int(lp.m_eq), int(lp.m_ineq), int(lp.n)
+    prob.memory = MEM_HOST
+    prob.obj_offset = float(getattr(lp, "obj_offset", 0.0))
+    arrs = dict(row_ptr=np.ascontiguousarray(lp.row_ptr, dtype=np.int64),
+                col_idx=np.ascontiguousarray(lp.col_idx, dtype=np.int32),
+                val=np.ascontiguousarray(lp.val, dtype=np.float64),
+                c=np.ascontiguousarray(lp.c, dtype=np.float64),
+                rhs=np.ascontiguousarray(lp.q, dtype=np.float64),
+                l=np.ascontiguousarray(lp.l, dtype=np.float64),
+                u=np.ascontiguousarray(lp.u, dtype=np.float64))
+    keep.append(arrs)
+    prob.nnz = int(arrs["row_ptr"][-1])
+    for f, a in arrs.items():
+        setattr(prob, f, a.ctypes.data if a.size else None)
+    if prob.row_ptr is None:
+        prob.row_ptr = arrs["row_ptr"].ctypes.data
+    return prob
+
+
+class Batch:
+    """Owns a batched solver (rhpdhg_batch_*): add LPs, step, poll results."""
+
+    def __init__(self, max_slots: int, arena_bytes: int, stream: int = 0):
+        rc, self.b = rhpdhg_batch_create(max_slots, arena_bytes, stream)
+        _check(rc, None, "rhpdhg_batch_create")
+        self._keep = {}
+        self._shape = {}
+
+    def add(self, lp, **params) -> int:
+        keep = []
+        prob = host_problem(lp, keep)
+        p = default_params(**params)
+        rc, slot = rhpdhg_batch_add(self.b, prob, p)
+        if rc == BUSY:
+            return -1
+        _check(rc, None, "rhpdhg_batch_add")
+        self._keep[slot] = keep
+        self._shape[slot] = (int(lp.n), int(lp.m_eq) + int(lp.m_ineq))
+        return slot
+
+    def step(self, iters: int = 64):
+        _check(rhpdhg_batch_step(self.b, iters), None, "rhpdhg_batch_step")
+
+    def status(self, slot: int) -> int:
+        return rhpdhg_batch_slot_status(self.b, slot)
+
+    def poll(self, slot: int, remove: bool = True):
+        n, m = self._shape[slot]
+        r = rhpdhg_result()
+        x, y = np.empty(n), np.empty(max(m, 1))
+        cx, cy = np.zeros(n), np.zeros(max(m, 1))
+        r.x, r.y, r.cert_x, r.cert_y = x.ctypes.data, y.ctypes.data, cx.ctypes.data, cy.ctypes.data
+        rc = rhpdhg_batch_poll(self.b, slot, r)
+        if rc == BUSY:
+            return None
+        _check(rc, None, "rhpdhg_batch_poll")
+        res = Result(status=r.status, iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
+                     rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
+                     dual_obj=r.dual_obj, solve_seconds=0.0, eta=r.eta, omega=r.omega,
+                     sigma_max=r.sigma_max, x=x, y=y[:m], cert_x=cx, cert_y=cy[:m])
+        if remove:
+            self.remove(slot)
+        return res
+
+    def remove(self, slot: int):
+        _check(rhpdhg_batch_remove(self.b, slot), None, "rhpdhg_batch_remove")
+        self._keep.pop(slot, None)
+
+    def free_bytes(self) -> int:
+        return rhpdhg_batch_free_bytes(self.b)
+
+    def launch_count(self) -> int:
+        return rhpdhg_batch_launch_count(self.b)
+
+    def run_all(self, slots, iters: int = 64, max_steps: int = 100_000):
+        out = {}
+        for _ in range(max_steps):
+            self.step(iters)
+            for s in slots:
+                if s not in out and self.status(s) != STATUS_RUNNING:
+                    out[s] = self.poll(s)
+            if len(out) == len(slots):
+                return out
+        raise RHPDHGError("batch did not finish")
+
+    def close(self):
+        if getattr(self, "b", None):
+            rhpdhg_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def device_problem(lp) -> rhpdhg_problem:

@@ -1,0 +1,119 @@
+"""Batched solver (one CTA per LP, one persistent launch for many LPs) against the FP64 oracle
+and against itself in different mixes.
+
+Parity: the batched path runs the same FP64 method as the single-LP path, so its PDHG points
+after T iterations match the oracle's to 1e-10 (max-norm relative) and its solutions reach the
+same objective to 1e-8; an LP's result is bit-identical alone and in any mix of other LPs,
+because nothing in its CTA depends on them."""
+import numpy as np
+import pytest
+
+from oracle import rhpdhg_oracle as O
+from paper_2407_16144_gb300 import lpgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_16144_gb300 import _build, rhpdhg
+    _build.build()
+    rhpdhg.load()
+    return rhpdhg
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(1.0, np.abs(b).max()))
+
+
+def mix(seed0=0, k=6):
+    lps = [lpgen.make_standard_planted(seed=seed0 + i, m=60 + 37 * i, n=150 + 90 * i)
+           for i in range(k)]
+    lps.append(lpgen.make_tiny_general(3, 3, 4, 9))
+    lps.append(lpgen.make_c2(7, scale=0.004))
+    return lps
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_batch_iterates_match_oracle(rh, alg):
+    lps = mix()
+    T = 150
+    with rh.Batch(16, 256 << 20) as b:
+        slots = [b.add(lp, algorithm=alg, eps_rel_kkt=1e-14, max_iters=T, check_every=16,
+                       first_epoch_len=20) for lp in lps]
+        res = b.run_all(slots, iters=40)
+    for lp, s in zip(lps, slots):
+        r = res[s]
+        o = O.solve(lp, O.OracleParams(algorithm=alg, eps_rel_kkt=1e-14, max_iters=T,
+                                       check_every=16, first_epoch_len=20))
+        assert r.status == rh.STATUS_ITERATION_LIMIT and r.iters == T
+        assert rel(r.x, o.x) < 1e-10 and rel(r.y, o.y) < 1e-10, (lp.name, rel(r.x, o.x))
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_batch_solves_to_1e8(rh, alg):
+    lps = mix(seed0=20)
+    with rh.Batch(16, 256 << 20) as b:
+        slots = [b.add(lp, algorithm=alg, eps_rel_kkt=1e-8) for lp in lps]
+        res = b.run_all(slots, iters=64)
+    for lp, s in zip(lps, slots):
+        r = res[s]
+        o = O.solve(lp, O.OracleParams(algorithm=alg, eps_rel_kkt=1e-8, max_iters=400_000))
+        assert r.status == rh.STATUS_OPTIMAL == o.status, lp.name
+        assert abs(r.primal_obj - o.primal_obj) <= 1e-8 * (1 + abs(o.primal_obj))
+        k = O.rel_kkt(lp, O.csr_matrix(lp), r.x, r.y)
+        assert k["rel_kkt"] <= 1e-8 * 1.0001
+        # iteration counts to tolerance are not pinned (restart decisions near ties diverge)
+
+
+def test_batch_alone_equals_in_mix(rh):
+    target = lpgen.make_standard_planted(seed=77, m=300, n=750)
+    with rh.Batch(4, 64 << 20) as b:
+        s = b.add(target, eps_rel_kkt=1e-8)
+        alone = b.run_all([s], iters=64)[s]
+    others = mix(seed0=40)
+    with rh.Batch(32, 512 << 20) as b:
+        first = [b.add(lp, eps_rel_kkt=1e-8) for lp in others[:4]]
+        b.step(100)                                   # others are mid-solve when it arrives
+        s = b.add(target, eps_rel_kkt=1e-8)
+        rest = [b.add(lp, eps_rel_kkt=1e-8) for lp in others[4:]]
+        res = b.run_all(first + [s] + rest, iters=37)
+    inmix = res[s]
+    assert alone.status == inmix.status == rh.STATUS_OPTIMAL
+    assert alone.iters == inmix.iters
+    assert np.array_equal(alone.x, inmix.x) and np.array_equal(alone.y, inmix.y)
+
+
+def test_batch_certificates(rh):
+    lps = [lpgen.make_primal_infeasible(3, 500, 1000), lpgen.make_dual_infeasible(3, 500, 1000)]
+    with rh.Batch(4, 128 << 20) as b:
+        slots = [b.add(lp, max_iters=50_000, max_epoch_len=200) for lp in lps]
+        res = b.run_all(slots, iters=256)
+    K = [O.csr_matrix(lp) for lp in lps]
+    r = res[slots[0]]
+    assert r.status == rh.STATUS_PRIMAL_INFEASIBLE
+    by = lps[0].q @ r.cert_y
+    assert by > 0 and (K[0].T @ r.cert_y).max() / by <= 1e-8
+    r = res[slots[1]]
+    assert r.status == rh.STATUS_DUAL_INFEASIBLE
+    cd = lps[1].c @ r.cert_x
+    assert cd < 0 and np.abs(K[1] @ r.cert_x).max() / -cd <= 1e-8
+
+
+def test_batch_capacity_limits(rh):
+    lp = lpgen.make_c1(0)
+    keep = []
+    need = rh.rhpdhg_batch_bytes_needed(rh.host_problem(lp, keep))
+    with rh.Batch(2, int(need * 1.5)) as b:
+        s0 = b.add(lp)
+        assert s0 >= 0
+        with pytest.raises(rh.RHPDHGError, match="arena full"):
+            b.add(lp)                                  # arena has room for one
+    with rh.Batch(1, int(need * 3)) as b:
+        assert b.add(lp) >= 0
+        assert b.add(lp) == -1                         # no free slot (BUSY)
+        b.remove(0)
+        assert b.add(lp) == 0 and b.free_bytes() >= 0
