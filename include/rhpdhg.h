@@ -283,6 +283,40 @@ int64_t rhpdhg_batch_launch_count(const rhpdhg_batch *b);
 
 void rhpdhg_batch_free(rhpdhg_batch *b);
 
+/* ---- serving: continuous batching under a device-memory budget ---------------------------
+ * A worker thread admits submitted LPs first-come first-served while the budget allows (a
+ * later request may pass one that does not fit yet).  LPs with at most small_nnz nonzeros and
+ * precision 0 become slots of an internal batched solver (its arena, budget_bytes / 4 at most,
+ * counts against the budget); the others get their own single-LP handle, solved on its own
+ * stream concurrently with the batch.  Memory is released as each request finishes, and waiting
+ * requests are admitted in the next turn.  Results are kept until polled. */
+typedef struct rhpdhg_server rhpdhg_server;
+
+/* budget_bytes: device memory the server may use; small_nnz: largest LP sent to the batched
+ * solver; max_slots: batched slots; iters_per_step: iterations per batched launch. */
+int rhpdhg_server_create(int64_t budget_bytes, int64_t small_nnz, int32_t max_slots,
+                         int32_t iters_per_step, rhpdhg_server **out);
+
+/* Copies the LP (host memory) and params (NULL = defaults) and queues it; *ticket identifies
+ * it.  The submitter may free its arrays on return. */
+int rhpdhg_server_submit(rhpdhg_server *s, const rhpdhg_problem *lp, const rhpdhg_params *params,
+                         int64_t *ticket);
+
+/* RHPDHG_BUSY until the request is finished; then fills *r (host arrays given in r, as in
+ * rhpdhg_poll; solve_seconds = time from admission to completion), sets *latency_s (may be
+ * NULL) to the time from submission to completion, and forgets the request. */
+int rhpdhg_server_poll(rhpdhg_server *s, int64_t ticket, rhpdhg_result *r, double *latency_s);
+
+/* Cancels a request (pending or running); its poll then reports RHPDHG_STATUS_CANCELLED. */
+int rhpdhg_server_cancel(rhpdhg_server *s, int64_t ticket);
+
+/* out[10]: pending, running batched, running single, completed, bytes in use, peak bytes in
+ * use, budget, batched launches, admitted batched, admitted single. */
+int rhpdhg_server_stats(rhpdhg_server *s, int64_t *out);
+
+/* Stops the worker (running solves are abandoned) and frees everything.  NULL-safe. */
+void rhpdhg_server_free(rhpdhg_server *s);
+
 /* Number of CUDA kernels of this library the handle has launched so far (create and every
  * solve; a replay of a captured graph counts each kernel node it runs).  Kernels of the CUB
  * library used for the transpose during create are not counted.  Returns -1 for NULL. */

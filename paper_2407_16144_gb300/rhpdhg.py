@@ -73,7 +73,9 @@ EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_po
             "rhpdhg_launch_count", "rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc",
             "rhpdhg_batch_create", "rhpdhg_batch_add", "rhpdhg_batch_step", "rhpdhg_batch_poll",
             "rhpdhg_batch_remove", "rhpdhg_batch_slot_status", "rhpdhg_batch_free_bytes",
-            "rhpdhg_batch_bytes_needed", "rhpdhg_batch_launch_count", "rhpdhg_batch_free"]
+            "rhpdhg_batch_bytes_needed", "rhpdhg_batch_launch_count", "rhpdhg_batch_free",
+            "rhpdhg_server_create", "rhpdhg_server_submit", "rhpdhg_server_poll",
+            "rhpdhg_server_cancel", "rhpdhg_server_stats", "rhpdhg_server_free"]
 
 _lib = None
 
@@ -119,6 +121,14 @@ def load(path: str = LIB_PATH):
         "rhpdhg_batch_bytes_needed": (C.c_int64, [C.POINTER(rhpdhg_problem)]),
         "rhpdhg_batch_launch_count": (C.c_int64, [H]),
         "rhpdhg_batch_free": (None, [H]),
+        "rhpdhg_server_create": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                           C.POINTER(H)]),
+        "rhpdhg_server_submit": (C.c_int, [H, C.POINTER(rhpdhg_problem),
+                                           C.POINTER(rhpdhg_params), C.POINTER(C.c_int64)]),
+        "rhpdhg_server_poll": (C.c_int, [H, C.c_int64, C.POINTER(rhpdhg_result), _dp]),
+        "rhpdhg_server_cancel": (C.c_int, [H, C.c_int64]),
+        "rhpdhg_server_stats": (C.c_int, [H, C.POINTER(C.c_int64)]),
+        "rhpdhg_server_free": (None, [H]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -253,6 +263,104 @@ def rhpdhg_batch_launch_count(b) -> int:
 
 def rhpdhg_batch_free(b) -> None:
     load().rhpdhg_batch_free(b)
+
+
+def rhpdhg_server_create(budget_bytes: int, small_nnz: int, max_slots: int,
+                         iters_per_step: int):
+    h = C.c_void_p()
+    rc = load().rhpdhg_server_create(budget_bytes, small_nnz, max_slots, iters_per_step,
+                                     C.byref(h))
+    return rc, h
+
+
+def rhpdhg_server_submit(s, lp: rhpdhg_problem, params: Optional[rhpdhg_params]):
+    t = C.c_int64(0)
+    rc = load().rhpdhg_server_submit(s, C.byref(lp), C.byref(params) if params else None,
+                                     C.byref(t))
+    return rc, t.value
+
+
+def rhpdhg_server_poll(s, ticket: int, r: rhpdhg_result):
+    lat = C.c_double(0.0)
+    rc = load().rhpdhg_server_poll(s, ticket, C.byref(r), C.byref(lat))
+    return rc, lat.value
+
+
+def rhpdhg_server_cancel(s, ticket: int) -> int:
+    return load().rhpdhg_server_cancel(s, ticket)
+
+
+def rhpdhg_server_stats(s) -> dict:
+    out = (C.c_int64 * 10)()
+    load().rhpdhg_server_stats(s, out)
+    keys = ["pending", "running_batched", "running_single", "completed", "bytes_in_use",
+            "peak_bytes_in_use", "budget", "batched_launches", "admitted_batched",
+            "admitted_single"]
+    return dict(zip(keys, list(out)))
+
+
+def rhpdhg_server_free(s) -> None:
+    load().rhpdhg_server_free(s)
+
+
+class Server:
+    """Owns a serving loop (rhpdhg_server_*)."""
+
+    def __init__(self, budget_bytes: int, small_nnz: int = 200_000, max_slots: int = 256,
+                 iters_per_step: int = 64):
+        rc, self.s = rhpdhg_server_create(budget_bytes, small_nnz, max_slots, iters_per_step)
+        _check(rc, None, "rhpdhg_server_create")
+        self._shape = {}
+
+    def submit(self, lp, **params) -> int:
+        keep = []
+        prob = host_problem(lp, keep)
+        p = default_params(**params)
+        rc, t = rhpdhg_server_submit(self.s, prob, p)
+        _check(rc, None, "rhpdhg_server_submit")
+        self._shape[t] = (int(lp.n), int(lp.m_eq) + int(lp.m_ineq))
+        return t
+
+    def poll(self, ticket: int):
+        n, m = self._shape[ticket]
+        r = rhpdhg_result()
+        x, y = np.empty(n), np.empty(max(m, 1))
+        cx, cy = np.zeros(n), np.zeros(max(m, 1))
+        r.x, r.y, r.cert_x, r.cert_y = x.ctypes.data, y.ctypes.data, cx.ctypes.data, cy.ctypes.data
+        rc, lat = rhpdhg_server_poll(self.s, ticket, r)
+        if rc == BUSY:
+            return None
+        _check(rc, None, "rhpdhg_server_poll")
+        self._shape.pop(ticket)
+        res = Result(status=r.status, iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
+                     rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
+                     dual_obj=r.dual_obj, solve_seconds=r.solve_seconds, eta=r.eta,
+                     omega=r.omega, sigma_max=r.sigma_max, x=x, y=y[:m], cert_x=cx,
+                     cert_y=cy[:m])
+        return res, lat
+
+    def cancel(self, ticket: int):
+        rhpdhg_server_cancel(self.s, ticket)
+
+    def stats(self) -> dict:
+        return rhpdhg_server_stats(self.s)
+
+    def close(self):
+        if getattr(self, "s", None):
+            rhpdhg_server_free(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def host_problem(lp, keep: list) -> rhpdhg_problem:
