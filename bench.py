@@ -47,6 +47,10 @@ def parse():
                     help="headline precision: 1 = FP32 iterates / FP64 restarts, 0 = FP64")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=40,
+                    help="requests of the 50/s Poisson stream replayed through the serving loop "
+                         "(0 = skip)")
+    ap.add_argument("--serve-max-iters", type=int, default=10_000)
     return ap.parse_args()
 
 
@@ -139,6 +143,82 @@ def cpu_oracle_sample(lp, algorithm, tol, iters_to_tol, sample_iters=100):
     t_tol = setup + iters_to_tol * per_iter
     return dict(setup_s=setup, s_per_iter=per_iter, time_to_tol_s=t_tol,
                 value=1.0 / t_tol, wall_s=time.perf_counter() - t0)
+
+
+def sgm10(times):
+    import math
+    return math.exp(sum(math.log(t + 10.0) for t in times) / len(times)) - 10.0
+
+
+def run_serving(args, rhpdhg, lpgen):
+    """Replays the first requests of the serving stream (Poisson arrivals at 50/s, m log-uniform
+    in [100, 200k], n = 2.5 m, C1 structure, tolerance 1e-4 or 1e-6 each) through the serving loop
+    and, for comparison, one at a time through the plain FP64 single-LP path."""
+    import threading
+    import numpy as np
+    nreq = args.serve_requests
+    reqs = lpgen.make_batch_stream(4, count=nreq)
+    lps = [lpgen.make_standard_planted(seed=r["seed"], m=r["m"], n=r["n"]) for r in reqs]
+    small_nnz = 20_000
+    cap = args.serve_max_iters
+    results = {}
+    with rhpdhg.Server(150 << 30, small_nnz=small_nnz, max_slots=256, iters_per_step=64) as srv:
+        tick = {}
+        start = time.perf_counter()
+
+        def producer():
+            for i, (r, lp) in enumerate(zip(reqs, lps)):
+                now = time.perf_counter() - start
+                if r["arrival_s"] > now:
+                    time.sleep(r["arrival_s"] - now)
+                prec = 0 if lp.nnz <= small_nnz else 1
+                tick[i] = srv.submit(lp, eps_rel_kkt=r["tol"], precision=prec, max_iters=cap)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        while len(results) < nreq:
+            for i in list(tick.keys()):
+                if i not in results:
+                    out = srv.poll(tick[i])
+                    if out is not None:
+                        results[i] = out
+            time.sleep(0.0005)
+        th.join()
+        makespan = time.perf_counter() - start
+        st = srv.stats()
+    lat = np.array([results[i][1] for i in range(nreq)])
+    solved = sum(results[i][0].status == rhpdhg.STATUS_OPTIMAL for i in range(nreq))
+    # the same stream through the plain FP64 single-LP path, one LP at a time
+    svc, solved_b = [], 0
+    for r, lp in zip(reqs, lps):
+        t0 = time.perf_counter()
+        with rhpdhg.Solver(lp, eps_rel_kkt=r["tol"], precision=0, max_iters=cap) as s:
+            rr = s.run()
+        svc.append(time.perf_counter() - t0)
+        solved_b += rr.status == rhpdhg.STATUS_OPTIMAL
+    fin, lat_b = 0.0, []
+    for r, sv in zip(reqs, svc):
+        st_ = max(fin, r["arrival_s"])
+        fin = st_ + sv
+        lat_b.append(fin - r["arrival_s"])
+    lat_b = np.array(lat_b)
+    return {
+        "workload": f"first {nreq} requests of the stream: Poisson arrivals at 50/s, m log-uniform "
+                    "in [100, 200k], n = 2.5 m, 5 nnz per column, tol 1e-4 or 1e-6 (seed 4), "
+                    f"at most {cap} iterations each",
+        "lps_per_s": nreq / makespan, "makespan_s": makespan,
+        "p50_latency_s": float(np.percentile(lat, 50)),
+        "p99_latency_s": float(np.percentile(lat, 99)),
+        "sgm10_latency_s": sgm10(list(lat)), "solved": int(solved), "requests": nreq,
+        "policy": f"nnz <= {small_nnz}: batched slots (FP64, one CTA each); larger: own handle, "
+                  "FP32 iterates / FP64 restarts",
+        "admitted_batched": st["admitted_batched"], "admitted_single": st["admitted_single"],
+        "peak_bytes_in_use": st["peak_bytes_in_use"],
+        "plain_fp64_single_lp": {"lps_per_s": nreq / fin, "makespan_s": fin,
+                                 "p50_latency_s": float(np.percentile(lat_b, 50)),
+                                 "p99_latency_s": float(np.percentile(lat_b, 99)),
+                                 "sgm10_latency_s": sgm10(list(lat_b)), "solved": int(solved_b)},
+    }
 
 
 def run_reference(args):
@@ -328,6 +408,8 @@ def run_ours(args):
                      "profiled_iters": rp.iters},
         "clocks": clk,
     }
+    if world == 1 and args.serve_requests > 0:
+        line["serving"] = run_serving(args, rhpdhg, lpgen)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_oracle_sample(lp, args.algorithm, args.tol, iters)
         line["cpu_baseline"] = {
