@@ -92,7 +92,10 @@ typedef struct {
   int32_t algorithm;            /* 0 = rHPDHG (Algorithm 1, eq. hpdhg); 1 = r2HPDHG
                                    (Algorithm 2, eq. hrpdhg).                        default 1 */
   int32_t precision;            /* 0 = FP64 throughout; 1 = FP32 matrix values and iterates with
-                                   FP64 anchors, restart norms, residuals and checks. default 0 */
+                                   FP64 anchors, restart norms, residuals and checks.  When a
+                                   certificate candidate at a restart point comes within 1e-3 of
+                                   eps_infeas's test, the solve continues in FP64 from that
+                                   restart point (iterations and epochs carry on). default 0 */
   double  eps_rel_kkt;          /* stop when max(rel_p, rel_d, rel_gap) <= eps.   default 1e-4  */
   double  eps_infeas;           /* certificate tolerance (normalised violation).  default 1e-8  */
   int64_t max_iters;            /* PDHG evaluations T(z).                         default 1e7   */

@@ -84,6 +84,8 @@ struct rhpdhg_handle {
   double ms_row = 0, ms_col = 0;
   long long n_row = 0, n_col = 0;
   long long launches = 0;      // kernels launched by create and solves
+  bool escalated = false;      // this solve switched from mixed precision to FP64
+  bool created_mixed = false;  // precision requested at create
   double bytes_row = 0, bytes_col = 0;
 };
 
@@ -232,10 +234,47 @@ int reset_state(rhpdhg_handle *h) {
   return RHPDHG_OK;
 }
 
+// Mixed precision -> FP64 for the rest of the solve, from the current restart point (the FP64
+// anchor z^{n,0}): the FP64 state is set up as at the start of a solve with that point as the
+// initial point, and the iteration and epoch counters, the primal weight and the step carry on.
+int escalate_to_fp64(rhpdhg_handle *h) {
+  Ctl c{};
+  CK(cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  h->mixed = false;
+  h->ic.mixed = 0;
+  for (auto &g : h->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  CK(cudaMemcpyAsync(h->xt, h->x0, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  if (h->m)
+    CK(cudaMemcpyAsync(h->yt, h->y0, h->m * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  c.status = kRunning;
+  c.restart_pending = 1;
+  c.stage = 1;
+  c.k = 0;
+  c.k_next = 0;
+  c.n_next = c.n;
+  c.cnt_row = c.cnt_col = 0;
+  CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
+  side_spmv(h->st, h->rows, h->xt, h->kxt, h->grid_row);
+  launch_col(h, 1);
+  h->launches += 2;
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
+  h->escalated = true;
+  return RHPDHG_OK;
+}
+
 // Runs the solve to completion (in the caller's thread or the handle's thread).
 void drive(rhpdhg_handle *h) {
   cudaSetDevice(h->dev);
   Timer timer;
+  if (h->created_mixed && !h->mixed) {      // a previous solve escalated: back to mixed
+    h->mixed = true;
+    h->ic.mixed = 1;
+    for (auto &g : h->gexec)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  }
+  h->escalated = false;
   int rc = reset_state(h);
   h->launches += h->mixed ? 8 : 2;   // set-up kernels of the solve
   const bool graphs = h->p.use_graphs && !h->p.profile;
@@ -261,64 +300,83 @@ void drive(rhpdhg_handle *h) {
   // own pinned mirror; the host reads mirror g only after chunk g's event, and relaunches g
   // only after that read.
   const long long depth = h->p.profile ? 1 : 2;
-  long long launched = 0, done = 0, last_t = 0;
+  long long last_t = 0;
   int host_status = kRunning;
-  bool stop = false;
-  while (true) {
-    while (!stop && launched - done < depth) {
-      if (h->cancel.load()) { host_status = kCancelled; stop = true; break; }
-      if (timer.s() > h->p.time_limit_s) { host_status = kTimeLimit; stop = true; break; }
-      const int g = (int)(launched & 1);
-      if (graphs) {
-        cudaGraphLaunch(h->gexec[g], h->st);
-      } else {
-        for (int i = 0; i < h->p.check_every; ++i) {
-          if (h->p.profile) cudaEventRecord(pev[3 * i], h->st);
-          launch_row(h);
-          if (h->p.profile) cudaEventRecord(pev[3 * i + 1], h->st);
-          launch_col(h, 0);
-          if (h->p.profile) cudaEventRecord(pev[3 * i + 2], h->st);
+  for (;;) {
+    long long launched = 0, done = 0;
+    bool stop = false;
+    int dev_status = kRunning;
+    while (true) {
+      while (!stop && launched - done < depth) {
+        if (h->cancel.load()) { host_status = kCancelled; stop = true; break; }
+        if (timer.s() > h->p.time_limit_s) { host_status = kTimeLimit; stop = true; break; }
+        const int g = (int)(launched & 1);
+        if (graphs) {
+          cudaGraphLaunch(h->gexec[g], h->st);
+        } else {
+          for (int i = 0; i < h->p.check_every; ++i) {
+            if (h->p.profile) cudaEventRecord(pev[3 * i], h->st);
+            launch_row(h);
+            if (h->p.profile) cudaEventRecord(pev[3 * i + 1], h->st);
+            launch_col(h, 0);
+            if (h->p.profile) cudaEventRecord(pev[3 * i + 2], h->st);
+          }
+          cudaMemcpyAsync(h->h_mirror + g, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
         }
-        cudaMemcpyAsync(h->h_mirror + g, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
+        cudaEventRecord(ev[g], h->st);
+        ++launched;
+        h->launches += (h->mixed ? 4LL : 2LL) * h->p.check_every;
       }
-      cudaEventRecord(ev[g], h->st);
-      ++launched;
-      h->launches += (h->mixed ? 4LL : 2LL) * h->p.check_every;
+      if (done >= launched) break;
+      const int g = (int)(done & 1);
+      cudaError_t e = cudaEventSynchronize(ev[g]);
+      ++done;
+      if (e != cudaSuccess) {
+        h->drive_err = RHPDHG_ERR_CUDA;
+        h->err = std::string("solve: ") + cudaGetErrorString(e);
+        stop = true;
+        continue;
+      }
+      const Ctl &mc = h->h_mirror[g];
+      if (h->p.profile) {
+        // count only the launches that did work (the rest returned at entry)
+        long long ran = mc.t - last_t;
+        if (mc.status == kNumericalError) ran += 1;
+        last_t = mc.t;
+        for (long long i = 0; i < ran && i < h->p.check_every; ++i) {
+          float a = 0, b = 0;
+          cudaEventElapsedTime(&a, pev[3 * i], pev[3 * i + 1]);
+          cudaEventElapsedTime(&b, pev[3 * i + 1], pev[3 * i + 2]);
+          h->ms_row += a;
+          h->ms_col += b;
+          h->n_row++;
+          h->n_col++;
+        }
+      }
+      if (mc.status != kRunning) {
+        stop = true;
+        dev_status = mc.status;
+      }
     }
-    if (done >= launched) break;
-    const int g = (int)(done & 1);
-    cudaError_t e = cudaEventSynchronize(ev[g]);
-    ++done;
-    if (e != cudaSuccess) {
+    cudaStreamSynchronize(h->st);
+    if (dev_status == kEscalate && host_status == kRunning && !h->drive_err) {
+      if (escalate_to_fp64(h) == RHPDHG_OK && (!graphs || capture_graphs(h) == RHPDHG_OK)) {
+        Ctl c{};
+        cudaMemcpy(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+        last_t = c.t;
+        continue;
+      }
       h->drive_err = RHPDHG_ERR_CUDA;
-      h->err = std::string("solve: ") + cudaGetErrorString(e);
-      stop = true;
-      continue;
     }
-    const Ctl &mc = h->h_mirror[g];
-    if (h->p.profile) {
-      // count only the launches that did work (the rest returned at entry)
-      long long ran = mc.t - last_t;
-      if (mc.status == kNumericalError) ran += 1;
-      last_t = mc.t;
-      for (long long i = 0; i < ran && i < h->p.check_every; ++i) {
-        float a = 0, b = 0;
-        cudaEventElapsedTime(&a, pev[3 * i], pev[3 * i + 1]);
-        cudaEventElapsedTime(&b, pev[3 * i + 1], pev[3 * i + 2]);
-        h->ms_row += a;
-        h->ms_col += b;
-        h->n_row++;
-        h->n_col++;
-      }
-    }
-    if (mc.status != kRunning) stop = true;
+    break;
   }
   cudaStreamSynchronize(h->st);
   Ctl fin{};
   cudaMemcpy(&fin, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
   h->final_ctl = fin;
   h->final_status = fin.status != kRunning ? fin.status : host_status;
-  if (h->final_status == kRunning) h->final_status = kNumericalError;
+  if (h->final_status == kRunning || h->final_status == kEscalate)
+    h->final_status = kNumericalError;
   if (h->mixed)
     launch_unscale_mx(h->st, h->n, h->m, h->E, h->xout, h->D, h->y0, h->dyt, h->xres, h->yres,
                       h->yt);
@@ -408,6 +466,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   h = new rhpdhg_handle();
   h->p = P;
   h->mixed = P.precision == 1;
+  h->created_mixed = h->mixed;
   h->m = m;
   h->m_eq = lp->m_eq;
   h->m_ineq = lp->m_ineq;
@@ -674,6 +733,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   ic.obj_offset = h->obj_offset;
   ic.trace_cap = h->trace ? P.trace_capacity : 0;
   ic.trace = h->trace;
+  ic.mixed = h->mixed ? 1 : 0;
   h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv};
   h->cv = ColVecs{h->x, h->xt, h->x0, h->kty, h->kty0, h->xout, h->certx, h->c, h->l, h->u,
                   h->E, h->Einv};

@@ -33,7 +33,8 @@ constexpr int kStageUnroll = 2;        // 4-entry groups staged per lane per rou
 
 enum Status : int {
   kRunning = 0, kOptimal = 1, kPrimalInfeasible = 2, kDualInfeasible = 3, kIterLimit = 4,
-  kTimeLimit = 5, kNumericalError = 6, kCancelled = 7
+  kTimeLimit = 5, kNumericalError = 6, kCancelled = 7,
+  kEscalate = 100   // internal: the mixed-precision solve continues in FP64 (never returned)
 };
 
 // Split-CSR structure of one side (see file comment).  The values live in separate arrays
@@ -127,6 +128,7 @@ struct IterConsts {
   double obj_offset;
   long long trace_cap;
   TraceRec *trace;
+  int mixed;                  // 1 = FP32-offset iterates (certificates escalate to FP64)
 };
 
 // ---------------------------------------------------------------------------------------------

@@ -88,6 +88,11 @@ __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, con
     const double vx = fmax(fmax(ctl->inf_kd_eq, ctl->inf_kd_in), fmax(r[8], r[9]));
     if (obj > 0.0 && vy / obj <= ic.eps_infeas) st = kPrimalInfeasible;
     else if (cd < 0.0 && vx / (-cd) <= ic.eps_infeas) st = kDualInfeasible;
+    // With FP32 offsets a diverging iterate carries about 1e-5 relative rounding, so a
+    // certificate cannot reach eps_infeas; once the candidate comes within 1e-3 of certifying,
+    // the solve continues in FP64 from this restart point.
+    else if (ic.mixed && ((obj > 0.0 && vy / obj <= 1e-3) || (cd < 0.0 && vx / (-cd) <= 1e-3)))
+      st = kEscalate;
   }
   if (st == kRunning && check) {
     const double rel_p = sqrt(ctl->rp_sq) / ic.qn1;
@@ -108,7 +113,7 @@ __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, con
   }
   if (st == kRunning && !isfinite(r[0])) st = kNumericalError;
   if (st != kRunning) ctl->status = st;
-  ctl->t = (phase == 0) ? t + 1 : 0;
+  ctl->t = (phase == 0) ? t + 1 : t;
   if (st == kRunning) {     // a final iteration keeps its own (k, n)
     ctl->k = ctl->k_next;
     ctl->n = ctl->n_next;

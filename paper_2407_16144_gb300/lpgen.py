@@ -363,6 +363,27 @@ def make_dual_infeasible(seed: int = 3, m: int = 50_000, n: int = 100_000, col_n
               ray_d=d)
 
 
+def make_dual_infeasible_twin(seed: int = 3, m: int = 50_000, n: int = 100_000,
+                              col_nnz: int = 6) -> LP:
+    """The LP dual of ``make_primal_infeasible(seed, m, n)``'s matrix, made dual infeasible with
+    the planted Farkas vector y_F as its unbounded ray.  Variables w (m, free); n inequality rows
+    -A^T w >= -(A^T y_bar + s) with y_bar ~ N(0, 1) and s ~ U(0, 1), so w = y_bar is feasible;
+    objective min -b^T w.  Along d = y_F: -A^T d >= 0 and -b^T d = -1."""
+    p = make_primal_infeasible(seed, m, n, col_nnz)
+    rng = np.random.default_rng(seed + 200)
+    y_bar = rng.standard_normal(m)
+    s = rng.uniform(0.0, 1.0, size=n)
+    aty = csr_rmatvec(p.row_ptr, p.col_idx, p.val, y_bar, n)
+    # transpose of A by a stable sort on the column index (rows of A^T in order)
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(p.row_ptr))
+    order = np.argsort(p.col_idx, kind="stable")
+    t_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(p.col_idx, minlength=n), out=t_ptr[1:])
+    return LP(m_eq=0, m_ineq=n, n=m, row_ptr=t_ptr, col_idx=rows[order].astype(np.int32),
+              val=-p.val[order], c=-p.q, q=-(aty + s), l=np.full(m, -INF), u=np.full(m, INF),
+              name=f"dual_infeasible_twin_{n}x{m}_s{seed}", ray_d=p.farkas_y.copy())
+
+
 # ---------------------------------------------------------------------------------------------
 # Tiny LPs for brute-force checks
 # ---------------------------------------------------------------------------------------------

@@ -143,25 +143,65 @@ def test_full_size_c2_first_iterations(rh, alg):
     assert rel(xt, sn["xt"]) < 1e-10 and rel(yt, sn["yt"]) < 1e-10
 
 
+def _check_certificate(rh, lp, r, kind):
+    """Host verification at 1e-8 against the unscaled data: a Farkas y (A^T y <= 0 on the
+    equality-form instances, b^T y > 0) or a ray d (c^T d < 0, equality rows K d = 0, inequality
+    rows K d >= 0, bound signs)."""
+    K = O.csr_matrix(lp)
+    if kind == "primal":
+        assert r.status == rh.STATUS_PRIMAL_INFEASIBLE, r.status_name
+        by = lp.q @ r.cert_y
+        assert by > 0 and (K.T @ r.cert_y).max() / by <= 1e-8
+        return
+    assert r.status == rh.STATUS_DUAL_INFEASIBLE, r.status_name
+    d = r.cert_x
+    cd = lp.c @ d
+    Kd = K @ d
+    assert cd < 0
+    if lp.m_eq:
+        assert np.abs(Kd[:lp.m_eq]).max() / -cd <= 1e-8
+    if lp.m_ineq:
+        assert (-Kd[lp.m_eq:]).max() / -cd <= 1e-8
+    lf, uf = np.isfinite(lp.l), np.isfinite(lp.u)
+    if lf.any():
+        assert (-d[lf]).max() / -cd <= 1e-8
+    if uf.any():
+        assert d[uf].max() / -cd <= 1e-8
+
+
+_INFEASIBLE_KINDS = {
+    "primal": ("primal", lpgen.make_primal_infeasible),
+    "dual": ("dual", lpgen.make_dual_infeasible),
+    "twin": ("dual", lpgen.make_dual_infeasible_twin),
+}
+
+
 @pytest.mark.parametrize("alg", [0, 1])
 def test_infeasibility_certificates(rh, alg):
-    for kind in ("primal", "dual"):
-        lp = (lpgen.make_primal_infeasible(3, 500, 1000) if kind == "primal"
-              else lpgen.make_dual_infeasible(3, 500, 1000))
+    for name, (kind, make) in _INFEASIBLE_KINDS.items():
+        lp = make(3, 500, 1000)
         o = O.solve(lp, O.OracleParams(algorithm=alg, max_iters=50_000, max_epoch_len=200))
         with rh.Solver(lp, algorithm=alg, max_iters=50_000, max_epoch_len=200) as s:
             r = s.run()
-        K = O.csr_matrix(lp)
-        if kind == "primal":
-            assert r.status == rh.STATUS_PRIMAL_INFEASIBLE == o.status
-            by = lp.q @ r.cert_y
-            assert by > 0 and (K.T @ r.cert_y).max() / by <= 1e-8
-        else:
-            assert r.status == rh.STATUS_DUAL_INFEASIBLE == o.status
-            cd = lp.c @ r.cert_x
-            assert cd < 0 and np.abs(K @ r.cert_x).max() / -cd <= 1e-8
-            assert (-r.cert_x).max() / -cd <= 1e-8
-        print(f"{kind} alg={alg}: detected at {r.iters} (oracle {o.iters})")
+        _check_certificate(rh, lp, r, kind)
+        assert r.status == o.status and r.iters == o.iters
+        print(f"{name} alg={alg}: detected at {r.iters} (oracle {o.iters})")
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_infeasibility_full_size(rh, precision):
+    """The 50k x 100k (600k nonzeros) primal-infeasible instance and its dual twin (the
+    transposed matrix, 100k inequality rows over 50k free variables, with the planted Farkas
+    vector as its ray): certificates verified on the host at 1e-8 against the unscaled data."""
+    for name in ("primal", "twin"):
+        kind, make = _INFEASIBLE_KINDS[name]
+        lp = make()
+        with rh.Solver(lp, algorithm=1, precision=precision, max_iters=200_000,
+                       time_limit_s=120.0) as s:
+            r = s.run()
+        _check_certificate(rh, lp, r, kind)
+        print(f"full-size {name} precision={precision}: detected at {r.iters} iterations, "
+              f"{r.restarts} restarts, {r.solve_seconds:.2f} s")
 
 
 @pytest.mark.parametrize("alg", [0, 1])
@@ -315,26 +355,21 @@ def test_mixed_precision_full_size_c2(rh):
     assert abs(r.primal_obj - ref) <= 1e-5 * (1 + abs(ref))
 
 
-@pytest.mark.xfail(reason="FP32 offsets of diverging iterates limit the mixed-precision "
-                          "certificate to ~1e-5; detection needs the planned FP64 escalation",
-                   strict=False)
 @pytest.mark.parametrize("alg", [0, 1])
 def test_mixed_precision_certificates(rh, alg):
-    for kind in ("primal", "dual"):
-        lp = (lpgen.make_primal_infeasible(3, 500, 1000) if kind == "primal"
-              else lpgen.make_dual_infeasible(3, 500, 1000))
+    """FP32 offsets limit a certificate to about 1e-5; a near-certificate at a restart point
+    moves the solve to FP64 from that point, which then certifies at 1e-8.  A second solve on
+    the same handle starts in mixed precision again and repeats the first exactly."""
+    for name, (kind, make) in _INFEASIBLE_KINDS.items():
+        lp = make(3, 500, 1000)
         with rh.Solver(lp, algorithm=alg, precision=1, max_iters=100_000,
                        max_epoch_len=200) as s:
             r = s.run()
-        K = O.csr_matrix(lp)
-        if kind == "primal":
-            assert r.status == rh.STATUS_PRIMAL_INFEASIBLE, r.status_name
-            by = lp.q @ r.cert_y
-            assert by > 0 and (K.T @ r.cert_y).max() / by <= 1e-8
-        else:
-            assert r.status == rh.STATUS_DUAL_INFEASIBLE, r.status_name
-            cd = lp.c @ r.cert_x
-            assert cd < 0 and np.abs(K @ r.cert_x).max() / -cd <= 1e-8
+            r2 = s.run()
+        assert (r2.status, r2.iters, r2.restarts) == (r.status, r.iters, r.restarts)
+        assert np.array_equal(r2.cert_x, r.cert_x) and np.array_equal(r2.cert_y, r.cert_y)
+        _check_certificate(rh, lp, r, kind)
+        print(f"mixed {name} alg={alg}: detected at {r.iters} iterations")
 
 
 def test_mixed_first_iterations_close_to_fp64(rh):

@@ -105,6 +105,22 @@ def test_dual_infeasible_ray():
     assert abs(lp.c @ d + 1.0) < 1e-9
 
 
+def test_dual_infeasible_twin():
+    """The twin is the transposed matrix of the primal-infeasible instance with its Farkas
+    vector as a ray; it is primal feasible at the planted point."""
+    p = lpgen.make_primal_infeasible(3, m=300, n=600)
+    lp = lpgen.make_dual_infeasible_twin(3, m=300, n=600)
+    assert (lp.m_eq, lp.m_ineq, lp.n) == (0, 600, 300)
+    G = _K(lp)
+    assert np.abs(G.toarray() + _K(p).toarray().T).max() == 0.0
+    d = lp.ray_d
+    assert (G @ d).min() >= -1e-12 and abs(lp.c @ d + 1.0) < 1e-9
+    assert np.isinf(lp.l).all() and np.isinf(lp.u).all()
+    rng = np.random.default_rng(3 + 200)
+    y_bar = rng.standard_normal(300)
+    assert (G @ y_bar - lp.q).min() > 0.0
+
+
 def test_tiny_and_box_generators():
     for s in range(5):
         lp = lpgen.make_tiny_standard(s)

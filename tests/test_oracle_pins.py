@@ -354,6 +354,18 @@ def test_dual_infeasible_certificate(alg):
     assert np.abs(K @ d).max() / -cd <= 1e-8 and (-d).max() / -cd <= 1e-8
 
 
+@pytest.mark.parametrize("alg", [0, 1])
+def test_dual_infeasible_twin_certificate(alg):
+    """Free variables and inequality rows: the ray d must satisfy G d >= 0 and c^T d < 0."""
+    lp = lpgen.make_dual_infeasible_twin(3, m=500, n=1000)
+    r = O.solve(lp, O.OracleParams(algorithm=alg, max_iters=50_000))
+    assert r.status == O.DUAL_INFEASIBLE
+    d = r.cert_x
+    cd = lp.c @ d
+    assert cd < 0
+    assert (-(O.csr_matrix(lp) @ d)).max() / -cd <= 1e-8
+
+
 def test_iteration_limit_status():
     lp = lpgen.make_c1(0)
     r = O.solve(lp, O.OracleParams(eps_rel_kkt=1e-12, max_iters=100))
