@@ -4,8 +4,10 @@
         [--algorithm 0|1] [--max-iters N] [--scale S] [--repeat R]
 
 Workloads (all from lpgen, seeded): c1 = 200 x 500 planted standard form; c2 = 100k x 250k
-general form with power-law columns (--scale shrinks it); c4p / c4d = 50k x 100k primal /
-dual infeasible LPs with planted certificates.  Prints one JSON line per solve.
+general form with power-law columns (--scale shrinks it); c4p = 50k x 100k primal-infeasible
+LP with a planted Farkas vector; c4d = its dual twin (100k inequality rows over 50k free
+variables, unbounded along the planted vector); c4s = a 50k x 100k standard-form LP unbounded
+along a sparse planted ray.  Prints one JSON line per solve.
 """
 from __future__ import annotations
 
@@ -23,6 +25,8 @@ def make(workload: str, scale: float):
     if workload == "c4p":
         return lpgen.make_primal_infeasible(3, int(50_000 * scale), int(100_000 * scale))
     if workload == "c4d":
+        return lpgen.make_dual_infeasible_twin(3, int(50_000 * scale), int(100_000 * scale))
+    if workload == "c4s":
         return lpgen.make_dual_infeasible(3, int(50_000 * scale), int(100_000 * scale))
     raise SystemExit(f"unknown workload {workload}")
 

@@ -593,11 +593,9 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     std::vector<int> hrp(m + 1), hcp(n + 1);
     CKT(cudaMemcpy(hrp.data(), rp, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost));
     CKT(cudaMemcpy(hcp.data(), cp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
-    const int Lr = choose_short_threshold(hrp.data(), m);
-    const int Lc = choose_short_threshold(hcp.data(), n);
     const bool with32 = P.precision == 1;
-    CKT(build_side(st, m, nnz, rp, col, val, h->D, h->E, Lr, with32, &h->rows));
-    CKT(build_side(st, n, nnz, cp, ridx, cval, h->E, h->D, Lc, with32, &h->cols));
+    CKT(build_side(st, m, nnz, rp, col, val, h->D, h->E, with32, &h->rows));
+    CKT(build_side(st, n, nnz, cp, ridx, cval, h->E, h->D, with32, &h->cols));
   }
   // ---- scaled vectors ----
   CKT(dalloc(&h->c, n));
@@ -627,8 +625,8 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   free_tmp();
 
   // ---- launch geometry ----
-  h->smem_row = kBlockWarps * (kTileRows * h->rows.lay.L + 4) * (int)sizeof(double);
-  h->smem_col = kBlockWarps * (kTileRows * h->cols.lay.L + 4) * (int)sizeof(double);
+  h->smem_row = kBlockWarps * h->rows.lay.seg * (int)sizeof(double);
+  h->smem_col = kBlockWarps * h->cols.lay.seg * (int)sizeof(double);
   allow_large_smem(kMaxTileSmem);
   allow_large_smem_setup(kMaxTileSmem);
   allow_large_smem_mx(kMaxTileSmem);

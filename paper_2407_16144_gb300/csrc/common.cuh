@@ -3,9 +3,10 @@
 // Data layout in device memory (one LP):
 //   * Each side of the bilinear form is one "row operator": the row side is K^ (m rows, used
 //     for K^ x~) and the column side is K^T (n rows, used for K^T y~).  Each is stored in a
-//     tiled split-CSR layout (SideLayout): rows with at most L entries live in a short CSR
-//     (long rows have zero length there) processed 32 rows per warp, one lane per row; rows
-//     with more than L entries live in a long CSR processed by a whole warp per row.  Both kinds
+//     tiled split-CSR layout (SideLayout): each tile of 32 consecutive rows keeps its rows of
+//     at most kShortMax entries in a short CSR segment of at most kSegBudget entries (the
+//     tile's longest rows move out until it fits), processed by one warp, one lane per row;
+//     the other rows live in a long CSR cut into chunks that are whole-warp tasks.  Both kinds
 //     end in the same per-row epilogue, executed by one lane per row so the FP64 work of the
 //     epilogue (the method's elementwise part) runs with all 32 lanes active.
 //   * Vectors are plain arrays indexed by row (m) or column (n) in the original order.
@@ -26,8 +27,9 @@ constexpr int kTileRows = 32;          // rows per tile = lanes per warp
 constexpr int kBlockWarps = 4;         // warps per CTA of the tile kernels
 constexpr int kBlockThreads = kBlockWarps * kWarp;
 constexpr int kMaxPartials = 16;       // reduction slots per CTA
-constexpr int kMaxTileL = 64;          // largest short-row threshold
-constexpr int kMaxTileSmem = kBlockWarps * (kTileRows * kMaxTileL + 4) * 8;   // bytes
+constexpr int kShortMax = 128;         // rows with more entries are always long
+constexpr int kSegBudget = 1024;       // entries of one tile's short segment (staging area)
+constexpr int kMaxTileSmem = kBlockWarps * (kSegBudget + 8) * 8;   // bytes, FP64 staging
 constexpr int kChunk = 256;            // entries per long-row chunk (8 per lane)
 constexpr int kStageUnroll = 2;        // 4-entry groups staged per lane per round
 
@@ -44,7 +46,8 @@ enum Status : int {
 // rows are further cut into chunks of at most kChunk entries; a chunk is one warp task.
 struct SideLayout {
   int nrows = 0;
-  int L = 32;                // short-row threshold: rows with <= L entries are short
+  int seg = 8;               // per-warp staging stride (entries): longest tile segment,
+                             // rounded up to 4, plus 4
   int n_short_tiles = 0;     // ceil(nrows / 32)
   int n_long = 0;            // number of long rows
   int n_long_tiles = 0;      // ceil(n_long / 32): groups of 32 long rows sharing an epilogue
@@ -249,7 +252,9 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) v[i] = 0.0;
   const unsigned all = smask | (mmask << NS);
-  // thread t sums blocks t, t + blockDim, ... then groups t, t + blockDim, ... (fixed order)
+  // thread t sums blocks t, t + blockDim, ... then groups t, t + blockDim, ... (fixed order);
+  // unrolled so that several blocks' loads are in flight at once
+#pragma unroll 4
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const double *src = part + (size_t)b * kMaxPartials;
 #pragma unroll

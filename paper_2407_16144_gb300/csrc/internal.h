@@ -77,14 +77,13 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
                      int ruiz_iters, double alpha, double *D, double *E, double *tmp_m,
                      double *tmp_n);
 // Build a split-CSR side from a CSR (nrows rows) with values scaled as
-// val * rscale[row] * cscale[col] (FP64, plus an FP32 copy when with32).  Allocates device
-// buffers (cudaMalloc).
+// val * rscale[row] * cscale[col] (FP64, plus an FP32 copy when with32).  Rows longer than
+// kShortMax, and the longest rows of any tile whose short segment would exceed kSegBudget,
+// go to the long CSR.  Allocates device buffers (cudaMalloc).
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
-                       const double *val, const double *rscale, const double *cscale, int L,
+                       const double *val, const double *rscale, const double *cscale,
                        bool with32, SideStore *out);
 void free_side(SideStore *s);
-// Choose the short-row threshold L from the row-length distribution (host copy of ptr).
-int choose_short_threshold(const int *h_ptr, int nrows);
 // Launch geometry of the tile kernels for a side with L.
 int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm);
 // out = side * src   (plain product, FP64)

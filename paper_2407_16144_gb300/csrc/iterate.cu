@@ -44,7 +44,7 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   RowAcc a, al;   // al: contributions of long rows (see walk_tiles)
   a.zero();
   al.zero();
-  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
+  double *my = smem + (threadIdx.x >> 5) * lay.seg;
 
   StepFlags fl{restart, w, sigma, check, rp, m_eq};
   auto body = [&](int i, double dot, RowAcc &acc) { row_epilogue<RHO2>(i, dot, v, fl, acc); };
@@ -79,7 +79,7 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   ColAcc a, al;
   a.zero();
   al.zero();
-  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
+  double *my = smem + (threadIdx.x >> 5) * lay.seg;
 
   StepFlags fl{restart, w, tau, check, rp, ic.m_eq};
   auto body = [&](int j, double dot, ColAcc &acc) { col_epilogue<RHO2>(j, dot, v, fl, acc); };

@@ -60,8 +60,8 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   const int m_eq = ic.m_eq;
   // staging: FP64 walks use (32 L + 4) doubles per warp, FP32 walks (32 L + 4) floats (the
   // FP32-only kernels are launched with half the shared memory)
-  double *my64 = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
-  float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
+  double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
+  float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
   Acc<6, 3> a, al;
   a.zero();
   al.zero();
@@ -195,8 +195,8 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
   // staging: FP64 walks use (32 L + 4) doubles per warp, FP32 walks (32 L + 4) floats (the
   // FP32-only kernels are launched with half the shared memory)
-  double *my64 = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
-  float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
+  double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
+  float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
   Acc<8, 4> a, al;
   a.zero();
   al.zero();

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kBlockThreads)
 k_side_spmv(SideLayout lay, SideVals<double> vals, WalkScratch ws,
             const double *__restrict__ src, double *out) {
   extern __shared__ double smem[];
-  double *my = smem + (threadIdx.x >> 5) * (kTileRows * lay.L + 4);
+  double *my = smem + (threadIdx.x >> 5) * lay.seg;
   auto epi = [&](int row, double dot, bool) { out[row] = dot; };
   auto gather = [&](int j) { return src[j]; };
   auto gdone = [&](int) {};
@@ -286,7 +286,7 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
 }
 
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
-                       const double *val, const double *rscale, const double *cscale, int L,
+                       const double *val, const double *rscale, const double *cscale,
                        bool with32, SideStore *out) {
   (void)nnz;
   SideStore s;
@@ -299,18 +299,36 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   std::vector<int> ptr_s(std::max(nrows, 1)), tile_end(std::max(ntiles, 1)), dst(std::max(nrows, 1));
   std::vector<uint32_t> mask(std::max(ntiles, 1), 0u);
   std::vector<int> long_rows, beg_l, end_l, chunk_ptr(1, 0), chunk_row;
-  long long cur = 0, cl = 0;
+  long long cur = 0, cl = 0, maxseg = 0;
   auto align4 = [](long long v) { return (v + 3) & ~3LL; };
   for (int t = 0; t < ntiles; ++t) {
+    const int r0 = t * kTileRows, r1 = std::min(nrows, (t + 1) * kTileRows);
+    // membership: rows over kShortMax are long; then, while the tile's short segment exceeds
+    // kSegBudget, its longest short row (the first of equal ones) becomes long
+    long long sum = 0;
+    for (int r = r0; r < r1; ++r) {
+      const int len = hp[r + 1] - hp[r];
+      if (len > kShortMax) mask[t] |= 1u << (r - r0);
+      else sum += len;
+    }
+    while (sum > kSegBudget) {
+      int best = -1, blen = -1;
+      for (int r = r0; r < r1; ++r) {
+        const int len = hp[r + 1] - hp[r];
+        if (!((mask[t] >> (r - r0)) & 1u) && len > blen) { best = r; blen = len; }
+      }
+      mask[t] |= 1u << (best - r0);
+      sum -= blen;
+    }
     cur = align4(cur);
-    for (int r = t * kTileRows; r < std::min(nrows, (t + 1) * kTileRows); ++r) {
+    const long long seg_b = cur;
+    for (int r = r0; r < r1; ++r) {
       const int len = hp[r + 1] - hp[r];
       ptr_s[r] = (int)cur;
-      if (len <= L) {
+      if (!((mask[t] >> (r - r0)) & 1u)) {
         dst[r] = (int)cur;
         cur += len;
       } else {
-        mask[t] |= 1u << (r - t * kTileRows);
         cl = align4(cl);
         const int li = (int)long_rows.size();
         long_rows.push_back(r);
@@ -324,12 +342,13 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
       }
     }
     tile_end[t] = (int)cur;
+    maxseg = std::max(maxseg, cur - seg_b);
   }
   const long long nnz_s = align4(cur) + 4, nnz_l = align4(cl) + kChunk;
   if (nnz_s > INT_MAX || nnz_l > INT_MAX) return cudaErrorInvalidValue;
   const int nlong = (int)long_rows.size(), nch = (int)chunk_row.size();
   s.lay.nrows = nrows;
-  s.lay.L = L;
+  s.lay.seg = (int)align4(maxseg) + 4;
   s.lay.n_short_tiles = ntiles;
   s.lay.n_long = nlong;
   s.lay.n_long_tiles = (nlong + kTileRows - 1) / kTileRows;
@@ -435,22 +454,6 @@ void free_side(SideStore *s) {
   *s = SideStore();
 }
 
-int choose_short_threshold(const int *h_ptr, int nrows) {
-  // Short rows are staged for a whole 32-row tile in shared memory (32 * L products per warp);
-  // longer rows go to the chunked warp-per-chunk path.  Pick the smallest L in {8, 16, 32, 64}
-  // that keeps at least 90% of the rows short.
-  if (nrows <= 0) return 8;
-  std::vector<int> len(nrows);
-  for (int i = 0; i < nrows; ++i) len[i] = h_ptr[i + 1] - h_ptr[i];
-  const int cands[4] = {8, 16, 32, 64};
-  for (int L : cands) {
-    long long nshort = 0;
-    for (int i = 0; i < nrows; ++i) nshort += (len[i] <= L);
-    if (nshort >= (long long)(0.90 * nrows)) return L;
-  }
-  return 64;
-}
-
 int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm) {
   long long need = ((long long)lay.total_items() + kBlockWarps - 1) / kBlockWarps;
   long long cap = (long long)sm_count * std::max(blocks_per_sm, 1);
@@ -463,7 +466,7 @@ void allow_large_smem_setup(int bytes) {
 }
 
 void side_spmv(cudaStream_t st, const SideStore &side, const double *src, double *out, int grid) {
-  int smem = kBlockWarps * (kTileRows * side.lay.L + 4) * (int)sizeof(double);
+  int smem = kBlockWarps * side.lay.seg * (int)sizeof(double);
   k_side_spmv<<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, src, out);
   count_launches(1);
 }
