@@ -55,6 +55,16 @@ extern "C" {
 #define RHPDHG_STATUS_NUMERICAL_ERROR    6   /* a residual norm became NaN or infinite         */
 #define RHPDHG_STATUS_CANCELLED          7
 
+/* ---- certificate sources (rhpdhg_result.cert_source) ------------------------------------ */
+/* The two certificate candidates are the limits of Lemma sublinear-infeas that Theorem infeas
+ * carries over to restarts: the displacement T(z) - z (tested at every restart point z^{n,0},
+ * n >= 1, and at every check iteration) and the anchor movement z^{n+1,0} - z^{n,0} (tested at
+ * every restart).  The first that passes the Farkas test is returned. */
+#define RHPDHG_CERT_NONE            0
+#define RHPDHG_CERT_RESTART_POINT   1   /* T(z) - z at a restart point                     */
+#define RHPDHG_CERT_CHECK           2   /* T(z) - z at a check iteration                   */
+#define RHPDHG_CERT_ANCHOR_MOVE     3   /* z^{n+1,0} - z^{n,0}                              */
+
 /* ---- memory kinds ---------------------------------------------------------------------- */
 #define RHPDHG_MEM_HOST    0
 #define RHPDHG_MEM_DEVICE  1
@@ -128,6 +138,8 @@ typedef struct {
 typedef struct {
   int32_t status;               /* RHPDHG_STATUS_*                                             */
   int32_t out_memory;           /* memory kind of x, y, cert_x, cert_y below (input to poll)   */
+  int32_t cert_source;          /* RHPDHG_CERT_*: candidate behind an infeasibility status     */
+  int32_t reserved;
   int64_t iters;                /* PDHG evaluations performed                                  */
   int64_t restarts;             /* outer iterations n (restarts performed)                     */
   double  rel_p, rel_d, rel_gap;/* relative KKT parts at the returned point (last check)       */

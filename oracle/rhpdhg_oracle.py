@@ -30,8 +30,11 @@ Readings of silent or ambiguous passages (each listed with its reason in the des
     "k > tau^0" as printed;
   * rel-KKT termination (Section 7, Termination criteria) is the l2 relative primal residual,
     dual residual and duality gap at the PDHG point (x~, y~), evaluated every C iterations;
-  * the infeasibility candidate is the displacement T(z^{n,0}) - z^{n,0} at each restart
-    point, the quantity Theorem (infeas) proves converges linearly to v.
+  * two infeasibility candidates, the two limits of Lemma (sublinear-infeas) that Theorem
+    (infeas) carries over to restarts: the displacement T(z) - z at each restart point
+    z^{n,0} (n >= 1) and at each check iteration, and the anchor movement
+    z^{n+1,0} - z^{n,0} at each restart; the first that passes the Farkas test is returned
+    with its source (CERT_*).
 Parity pinned by tests/test_oracle_pins.py (vertex enumeration, closed-form box LPs, an
 independent LP solver's optimum, Proposition 1, Lemma (sublinear-feas), Corollary
 (sublinear-feas-reflected), Lemma (iterates-feas)(i), planted optima and planted Farkas
@@ -50,6 +53,9 @@ import scipy.sparse as sp
 # status codes (same meaning as the C library's)
 RUNNING, OPTIMAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, ITERATION_LIMIT, TIME_LIMIT, \
     NUMERICAL_ERROR, CANCELLED = range(8)
+# which candidate certified infeasibility: T(z) - z at a restart point, T(z) - z at a check
+# iteration, or the anchor movement z^{n+1,0} - z^{n,0}
+CERT_NONE, CERT_RESTART_POINT, CERT_CHECK, CERT_ANCHOR_MOVE = range(4)
 
 
 @dataclasses.dataclass
@@ -243,6 +249,18 @@ def dual_infeasibility_violation(lp, K, d):
     return viol, cd
 
 
+def infeasibility_test(lp, K, cx, cy, eps):
+    """Farkas tests of one candidate (cx, cy) (unscaled): the y-part as a primal-infeasibility
+    certificate first, then the x-part as an unbounded ray.  Returns (status, cert_x, cert_y)."""
+    vy, _ = primal_infeasibility_violation(lp, K, cy)
+    if vy <= eps:
+        return PRIMAL_INFEASIBLE, None, cy
+    vx, _ = dual_infeasibility_violation(lp, K, cx)
+    if vx <= eps:
+        return DUAL_INFEASIBLE, cx, None
+    return RUNNING, None, None
+
+
 # ---------------------------------------------------------------------------------------------
 # the solver
 # ---------------------------------------------------------------------------------------------
@@ -261,6 +279,7 @@ class OracleResult:
     y: np.ndarray
     cert_x: Optional[np.ndarray]
     cert_y: Optional[np.ndarray]
+    cert_source: int
     eta: float
     omega: float
     sigma_max: float
@@ -321,6 +340,7 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
     xt = yt = None
     kkt = None
     cert_x = cert_y = None
+    cert_source = CERT_NONE
     t = 0
     while True:
         xt, yt = pdhg_T(Kh, KhT, c, q, l, u, m_eq, tau, sigma, x, y)
@@ -334,19 +354,18 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
             snaps[t] = dict(x=x.copy(), y=y.copy(), xt=xt.copy(), yt=yt.copy(), x0=x0.copy(),
                             y0=y0.copy(), n=n_ep, k=k, omega=omega, fpr2=fpr2)
         last = (t + 1 >= params.max_iters)
-        # infeasibility at restart points: Theorem (infeas) bounds the distance of the
-        # displacement T(z^{n,0}) - z^{n,0} from the infimal displacement vector v, whose
-        # y-part certifies primal and x-part dual infeasibility (Proposition full-infeas)
-        if status == RUNNING and k == 0 and n_ep >= 1:
-            cx, cy = E * (xt - x), D * (yt - y)
-            vy, _ = primal_infeasibility_violation(lp, K, cy)
-            if vy <= params.eps_infeas:
-                status, cert_y = PRIMAL_INFEASIBLE, cy
-            else:
-                vx, _ = dual_infeasibility_violation(lp, K, cx)
-                if vx <= params.eps_infeas:
-                    status, cert_x = DUAL_INFEASIBLE, cx
-        if status == RUNNING and ((t + 1) % params.check_every == 0 or last):
+        is_check = (t + 1) % params.check_every == 0 or last
+        # infeasibility, first candidate: the displacement T(z) - z, which tends to the
+        # infimal displacement vector v (Lemma sublinear-infeas; linearly at restart points by
+        # Theorem infeas), whose y-part certifies primal and x-part dual infeasibility
+        # (Proposition full-infeas); tested at restart points and at check iterations
+        if status == RUNNING and ((k == 0 and n_ep >= 1) or is_check):
+            st, cx, cy = infeasibility_test(lp, K, E * (xt - x), D * (yt - y),
+                                            params.eps_infeas)
+            if st != RUNNING:
+                status, cert_x, cert_y = st, cx, cy
+                cert_source = CERT_RESTART_POINT if (k == 0 and n_ep >= 1) else CERT_CHECK
+        if status == RUNNING and is_check:
             kkt = rel_kkt(lp, K, E * xt, D * yt)
             if kkt["rel_kkt"] <= params.eps_rel_kkt:
                 status = OPTIMAL
@@ -367,7 +386,15 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
         if status != RUNNING:
             break
         if restart:
-            # z^{n+1,0} <- T(z^{n,k})
+            # z^{n+1,0} <- T(z^{n,k}).  Second candidate: the anchor movement
+            # z^{n+1,0} - z^{n,0}, the restarted form of the normalised iterate
+            # (2/k)(z^k - z^0) of Lemma sublinear-infeas (the test is scale free)
+            st, cx, cy = infeasibility_test(lp, K, E * (xt - x0), D * (yt - y0),
+                                            params.eps_infeas)
+            if st != RUNNING:
+                status, cert_x, cert_y, cert_source = st, cx, cy, CERT_ANCHOR_MOVE
+                n_ep += 1          # the restart took place: z^{n+1,0} is the new anchor
+                break
             if params.primal_weight_update:
                 dxa = np.linalg.norm(xt - x0)
                 dya = np.linalg.norm(yt - y0)
@@ -396,7 +423,8 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
     return OracleResult(status=status, iters=t, restarts=n_ep, rel_p=kkt["rel_p"],
                         rel_d=kkt["rel_d"], rel_gap=kkt["rel_gap"],
                         primal_obj=kkt["primal_obj"], dual_obj=kkt["dual_obj"], x=E * xt,
-                        y=D * yt, cert_x=cert_x, cert_y=cert_y, eta=eta, omega=omega,
+                        y=D * yt, cert_x=cert_x, cert_y=cert_y, cert_source=cert_source,
+                        eta=eta, omega=omega,
                         sigma_max=sigma_max, D=D, E=E,
                         solve_seconds=time.perf_counter() - t_start, trace=tr,
                         snapshots=snaps)

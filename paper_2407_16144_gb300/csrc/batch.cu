@@ -279,16 +279,21 @@ __device__ void batch_col_pass(const BatchDesc &d, const IterConsts &ic, int pha
   const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
   const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
   const bool rp = phase == 0 && (k == 0 && n_ep >= 1);
-  StepFlags fl{ctl->restart_pending, ctl->w, ctl->tau, check, rp, ic.m_eq};
-  Acc<8, 4> a;
+  const bool cert = rp || check;
+  const int restart = ctl->restart_pending;
+  const bool move = phase == 0 && restart;
+  const long long tn = phase == 0 ? t + 1 : t;
+  const bool stash = ((tn + 1) % ic.check_every == 0) || (tn + 1 >= ic.max_iters);
+  StepFlags fl{restart, ctl->w, ctl->tau, check, cert, rp, move, stash, ic.m_eq};
+  ColAcc a;
   a.zero();
-  auto fn = [&](int j, double dot) { col_epilogue<RHO2>(j, dot, d.cv_, fl, a); };
+  auto fn = [&](int j, double dot) { col_epilogue<RHO2>(j, dot, d.cv_, fl, a, a); };
   const double *yt = d.rv_.yt;
   auto gs = [&](int i) { return yt[i]; };
   rows_apply(d.n, d.cp, d.ri, d.cv, d.gc, gs, fn);
-  double r[12];
-  block_reduce(a, r, sh, 0x3u | (check ? 0x1Cu : 0u) | (rp ? 0xE0u : 0u), rp ? 0xFu : 0u);
-  if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, phase);
+  double r[19];
+  block_reduce(a, r, sh, col_smask(check, cert, move), col_mmask(cert, move));
+  if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, cert, rp, move, phase);
   __syncthreads();
 }
 
@@ -298,17 +303,20 @@ __device__ void batch_row_pass(const BatchDesc &d, const IterConsts &ic, double 
   const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
   const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
   const bool rp = (k == 0 && n_ep >= 1);
+  const bool cert = rp || check;
+  const int restart = ctl->restart_pending;
+  const bool move = restart && ctl->mv_ready;
   const double sigma = ctl->sigma;
-  StepFlags fl{ctl->restart_pending, ctl->w, sigma, check, rp, ic.m_eq};
-  Acc<6, 3> a;
+  StepFlags fl{restart, ctl->w, sigma, check, cert, rp, move, false, ic.m_eq};
+  RowAcc a;
   a.zero();
-  auto fn = [&](int i, double dot) { row_epilogue<RHO2>(i, dot, d.rv_, fl, a); };
+  auto fn = [&](int i, double dot) { row_epilogue<RHO2>(i, dot, d.rv_, fl, a, a); };
   const double *xt = d.cv_.xt;
   auto gs = [&](int j) { return xt[j]; };
   rows_apply(d.m, d.rp, d.ci, d.rv, d.gr, gs, fn);
-  double r[9];
-  block_reduce(a, r, sh, 0x7u | (check ? 0x18u : 0u) | (rp ? 0x20u : 0u), rp ? 0x7u : 0u);
-  if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma);
+  double r[13];
+  block_reduce(a, r, sh, row_smask(check, cert, move), row_mmask(cert, move));
+  if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
   __syncthreads();
 }
 
@@ -402,7 +410,7 @@ size_t slot_bytes(int m, int n, long long nnz) {
   size_t b = 0;
   b += align256((m + 1) * sizeof(int)) + align256(nnz * sizeof(int)) + align256(nnz * 8);
   b += align256((n + 1) * sizeof(int)) + align256(nnz * sizeof(int)) + align256(nnz * 8);
-  b += 14 * align256((size_t)std::max(n, 1) * 8) + 12 * align256((size_t)std::max(m, 1) * 8);
+  b += 15 * align256((size_t)std::max(n, 1) * 8) + 13 * align256((size_t)std::max(m, 1) * 8);
   b += align256(sizeof(rh::IterConsts)) + align256(16);
   return b;
 }
@@ -575,18 +583,18 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
          *kty = (double *)take(nb), *kty0 = (double *)take(nb), *xout = (double *)take(nb),
          *certx = (double *)take(nb), *c = (double *)take(nb), *l = (double *)take(nb),
          *u = (double *)take(nb), *E = (double *)take(nb), *Einv = (double *)take(nb),
-         *tmp_n = (double *)take(nb);
+         *tmp_n = (double *)take(nb), *certx2 = (double *)take(nb);
   double *y = (double *)take(mb), *yt = (double *)take(mb), *y0 = (double *)take(mb),
          *kx = (double *)take(mb), *kxt = (double *)take(mb), *kx0 = (double *)take(mb),
          *certy = (double *)take(mb), *q = (double *)take(mb), *D = (double *)take(mb),
-         *Dinv = (double *)take(mb), *tmp_m = (double *)take(mb);
+         *Dinv = (double *)take(mb), *tmp_m = (double *)take(mb), *certy2 = (double *)take(mb);
   rh::Ctl *ctl = b->d_ctls + slot;
   rh::IterConsts *ic = (rh::IterConsts *)take(sizeof(rh::IterConsts));
   double *setup_out = (double *)take(16);
   d.tmp_m = tmp_m;
   d.tmp_n = tmp_n;
-  d.rv_ = rh::RowVecs{y, yt, y0, kx, kxt, kx0, certy, q, D, Dinv};
-  d.cv_ = rh::ColVecs{x, xt, x0, kty, kty0, xout, certx, c, l, u, E, Einv};
+  d.rv_ = rh::RowVecs{y, yt, y0, kx, kxt, kx0, certy, q, D, Dinv, certy2};
+  d.cv_ = rh::ColVecs{x, xt, x0, kty, kty0, xout, certx, c, l, u, E, Einv, certx2};
   d.ctl = ctl;
   d.ic = ic;
   d.setup_out = setup_out;
@@ -605,6 +613,8 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   if (m) cudaMemcpyAsync(q, lp->rhs, m * 8, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(certx, 0, nb, st);
   cudaMemsetAsync(certy, 0, mb, st);
+  cudaMemsetAsync(certx2, 0, nb, st);
+  cudaMemsetAsync(certy2, 0, mb, st);
   rh::Ctl c0{};
   c0.status = rh::kRunning;
   c0.stage = 2;                     // set-up pending
@@ -699,8 +709,11 @@ int rhpdhg_batch_poll(rhpdhg_batch *b, int32_t slot, rhpdhg_result *r) {
       r->out_memory == RHPDHG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (r->x) cudaMemcpyAsync(r->x, xo, n * 8, kind, b->st);
   if (r->y && m) cudaMemcpyAsync(r->y, yo, m * 8, kind, b->st);
-  if (r->cert_x) cudaMemcpyAsync(r->cert_x, d.cv_.certx, n * 8, kind, b->st);
-  if (r->cert_y && m) cudaMemcpyAsync(r->cert_y, d.rv_.certy, m * 8, kind, b->st);
+  const bool mv = c.cert_src == rh::kCertAnchorMove;
+  r->cert_source = c.cert_src;
+  if (r->cert_x) cudaMemcpyAsync(r->cert_x, mv ? d.cv_.certx2 : d.cv_.certx, n * 8, kind, b->st);
+  if (r->cert_y && m)
+    cudaMemcpyAsync(r->cert_y, mv ? d.rv_.certy2 : d.rv_.certy, m * 8, kind, b->st);
   cudaError_t e = cudaStreamSynchronize(b->st);
   cudaFree(xo);
   cudaFree(yo);

@@ -46,9 +46,9 @@ struct rhpdhg_handle {
   double *D = nullptr, *E = nullptr, *Dinv = nullptr, *Einv = nullptr;
   double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr;
   double *x = nullptr, *xt = nullptr, *x0 = nullptr, *kty = nullptr, *kty0 = nullptr,
-         *xout = nullptr, *certx = nullptr;
+         *xout = nullptr, *certx = nullptr, *certx2 = nullptr;
   double *y = nullptr, *yt = nullptr, *y0 = nullptr, *kx = nullptr, *kxt = nullptr,
-         *kx0 = nullptr, *certy = nullptr;
+         *kx0 = nullptr, *certy = nullptr, *certy2 = nullptr;
   double *x_init = nullptr, *y_init = nullptr, *xres = nullptr, *yres = nullptr;
   // mixed precision: FP32 offsets and anchor images
   bool mixed = false;
@@ -121,7 +121,7 @@ void destroy(rhpdhg_handle *h) {
   double *bufs[] = {h->D, h->E, h->Dinv, h->Einv, h->c, h->q, h->l, h->u, h->x, h->xt, h->x0,
                     h->kty, h->kty0, h->xout, h->certx, h->y, h->yt, h->y0, h->kx, h->kxt,
                     h->kx0, h->certy, h->x_init, h->y_init, h->xres, h->yres, h->part_row,
-                    h->part_col, h->dxt64, h->dyt64};
+                    h->part_col, h->dxt64, h->dyt64, h->certx2, h->certy2};
   for (double *b : bufs) cudaFree(b);
   float *fbufs[] = {h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi,
                     h->dyt, h->kdxt, h->dy, h->kdx, h->r0, h->ylo};
@@ -254,6 +254,7 @@ int escalate_to_fp64(rhpdhg_handle *h) {
   c.k_next = 0;
   c.n_next = c.n;
   c.cnt_row = c.cnt_col = 0;
+  c.mv_ready = 0;
   CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
   side_spmv(h->st, h->rows, h->xt, h->kxt, h->grid_row);
   launch_col(h, 1);
@@ -672,10 +673,12 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   else h->omega0 = (chn > 1e-10 && qhn > 1e-10) ? chn / qhn : 1.0;
 
   // ---- iteration state ----
-  double **nv[] = {&h->x, &h->xt, &h->x0, &h->kty, &h->kty0, &h->xout, &h->certx, &h->x_init,
+  double **nv[] = {&h->x, &h->xt, &h->x0, &h->kty, &h->kty0, &h->xout, &h->certx, &h->certx2,
+                   &h->x_init,
                    &h->xres};
   for (double **b : nv) CKC(dalloc(b, n));
-  double **mv[] = {&h->y, &h->yt, &h->y0, &h->kx, &h->kxt, &h->kx0, &h->certy, &h->y_init,
+  double **mv[] = {&h->y, &h->yt, &h->y0, &h->kx, &h->kxt, &h->kx0, &h->certy, &h->certy2,
+                   &h->y_init,
                    &h->yres};
   for (double **b : mv) CKC(dalloc(b, m));
   if (h->mixed) {
@@ -687,7 +690,9 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     CKC(dalloc(&h->dyt64, m));
   }
   CKC(cudaMemsetAsync(h->certx, 0, n * sizeof(double), st));
+  CKC(cudaMemsetAsync(h->certx2, 0, n * sizeof(double), st));
   if (m) CKC(cudaMemsetAsync(h->certy, 0, m * sizeof(double), st));
+  if (m) CKC(cudaMemsetAsync(h->certy2, 0, m * sizeof(double), st));
   CKC(dalloc(&h->ctl, 1));
   CKC(cudaHostAlloc((void **)&h->h_mirror, 2 * sizeof(Ctl), cudaHostAllocDefault));
   std::memset(h->h_mirror, 0, 2 * sizeof(Ctl));
@@ -732,13 +737,14 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   ic.trace_cap = h->trace ? P.trace_capacity : 0;
   ic.trace = h->trace;
   ic.mixed = h->mixed ? 1 : 0;
-  h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv};
+  h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv,
+                  h->certy2};
   h->cv = ColVecs{h->x, h->xt, h->x0, h->kty, h->kty0, h->xout, h->certx, h->c, h->l, h->u,
-                  h->E, h->Einv};
+                  h->E, h->Einv, h->certx2};
   h->rvm = RowVecsMx{h->dyt, h->kdxt, h->dy, h->kdx, h->r0, h->ylo, h->y0, h->kx0, h->certy,
-                     h->dyt64, h->q, h->D, h->Dinv};
+                     h->dyt64, h->q, h->D, h->Dinv, h->certy2};
   h->cvm = ColVecsMx{h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi, h->x0, h->kty0, h->xout,
-                     h->certx, h->dxt64, h->c, h->l, h->u, h->E, h->Einv};
+                     h->certx, h->dxt64, h->c, h->l, h->u, h->E, h->Einv, h->certx2};
   algorithmic_bytes(h);
   h->launches = launches_so_far() - launches0;
   CKC(cudaStreamSynchronize(st));
@@ -788,9 +794,12 @@ int rhpdhg_poll(rhpdhg_handle *h, rhpdhg_result *r) {
       r->out_memory == RHPDHG_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (r->x) CK(cudaMemcpyAsync(r->x, h->xres, h->n * sizeof(double), kind, h->st));
   if (r->y && h->m) CK(cudaMemcpyAsync(r->y, h->yres, h->m * sizeof(double), kind, h->st));
-  if (r->cert_x) CK(cudaMemcpyAsync(r->cert_x, h->certx, h->n * sizeof(double), kind, h->st));
+  r->cert_source = c.cert_src;
+  const bool mv = c.cert_src == kCertAnchorMove;
+  if (r->cert_x)
+    CK(cudaMemcpyAsync(r->cert_x, mv ? h->certx2 : h->certx, h->n * sizeof(double), kind, h->st));
   if (r->cert_y && h->m)
-    CK(cudaMemcpyAsync(r->cert_y, h->certy, h->m * sizeof(double), kind, h->st));
+    CK(cudaMemcpyAsync(r->cert_y, mv ? h->certy2 : h->certy, h->m * sizeof(double), kind, h->st));
   CK(cudaStreamSynchronize(h->st));
   return RHPDHG_OK;
 }

@@ -26,12 +26,15 @@ constexpr int kWarp = 32;
 constexpr int kTileRows = 32;          // rows per tile = lanes per warp
 constexpr int kBlockWarps = 4;         // warps per CTA of the tile kernels
 constexpr int kBlockThreads = kBlockWarps * kWarp;
-constexpr int kMaxPartials = 16;       // reduction slots per CTA
+constexpr int kMaxPartials = 20;       // reduction slots per CTA
 constexpr int kShortMax = 128;         // rows with more entries are always long
 constexpr int kSegBudget = 1024;       // entries of one tile's short segment (staging area)
 constexpr int kMaxTileSmem = kBlockWarps * (kSegBudget + 8) * 8;   // bytes, FP64 staging
 constexpr int kChunk = 256;            // entries per long-row chunk (8 per lane)
 constexpr int kStageUnroll = 2;        // 4-entry groups staged per lane per round
+
+// Infeasibility certificate candidates (rhpdhg_result.cert_source).
+enum CertSource : int { kCertNone = 0, kCertRestartPoint = 1, kCertCheck = 2, kCertAnchorMove = 3 };
 
 enum Status : int {
   kRunning = 0, kOptimal = 1, kPrimalInfeasible = 2, kDualInfeasible = 3, kIterLimit = 4,
@@ -102,6 +105,12 @@ struct Ctl {
   double rel_p, rel_d, rel_gap, pobj, dobj;
   long long check_t;
   long long restarts;
+  // column parts of the anchor-movement certificate candidate z^{n+1,0} - z^{n,0}, staged by
+  // the column kernel of a restart decision (mv_ready = 1) for the row kernel that applies the
+  // restart, which completes the test
+  double mv_cd, mv_u, mv_l, mv_dlb, mv_dub, mv_au, mv_al;
+  int mv_ready;
+  int cert_src;          // candidate that certified infeasibility (kCert*)
   unsigned int cnt_row, cnt_col;   // last-CTA tickets
   int stage;             // 0: the row stage of iteration t is next; 1: the column stage is next
                          // (each finalisation advances it, so of two kernels launched for the
@@ -218,23 +227,18 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, unsigned smask, unsigned m
   return last;
 }
 
-// Warp-collective: reduce the long-row accumulator al of every lane and store it as group grp's
-// partials (lane 0), then clear al.  Same slot masks as cta_reduce_and_ticket.
-template <int NS, int NM>
-__device__ __forceinline__ void store_group(Acc<NS, NM> &al, unsigned smask, unsigned mmask,
-                                            double *gpart, int grp) {
+// Warp-collective: reduce the long-row sums al of every lane and store them as group grp's
+// partials (lane 0), then clear al.  Only sums need this (their order decides the rounding);
+// long-row maxima are taken into the finishing warp's own accumulator.
+template <int NS>
+__device__ __forceinline__ void store_group(Acc<NS, 0> &al, unsigned smask, double *gpart,
+                                            int grp) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     if (!((smask >> i) & 1u)) continue;
     const double v = warp_sum(al.s[i]);
     if (lane == 0) gpart[(size_t)grp * kMaxPartials + i] = v;
-  }
-#pragma unroll
-  for (int i = 0; i < NM; ++i) {
-    if (!((mmask >> i) & 1u)) continue;
-    const double v = warp_max(al.mx[i]);
-    if (lane == 0) gpart[(size_t)grp * kMaxPartials + NS + i] = v;
   }
   al.zero();
 }
@@ -264,13 +268,13 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
       v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
     }
   }
+  // groups hold sums only (long-row maxima go straight to the finishing warp's CTA partials)
   for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
     const double *src = gpart + (size_t)g * kMaxPartials;
 #pragma unroll
-    for (int i = 0; i < NS + NM; ++i) {
-      if (!((all >> i) & 1u)) continue;
-      const double p = __ldcg(src + i);
-      v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
+    for (int i = 0; i < NS; ++i) {
+      if (!((smask >> i) & 1u)) continue;
+      v[i] += __ldcg(src + i);
     }
   }
 #pragma unroll

@@ -33,23 +33,27 @@ struct SideStore {
 struct RowVecs {      // m-vectors used by the row kernel (K^ x~ and the dual step)
   double *y, *yt, *y0, *kx, *kxt, *kx0, *certy;
   const double *q, *d, *dinv;
+  double *certy2;     // y-part of the anchor-movement candidate
 };
 
 struct ColVecs {      // n-vectors used by the column kernel (K^T y~ and the primal step)
   double *x, *xt, *x0, *kty, *kty0, *xout, *certx;
   const double *c, *l, *u, *e, *einv;
+  double *certx2;     // x-part of the anchor-movement candidate
 };
 
 struct RowVecsMx {    // mixed precision, m-vectors (offsets from the FP64 anchor y0)
   float *dyt, *kdxt, *dy, *kdx, *r0, *ylo;
   double *y0, *kx0, *certy, *dyt64;
   const double *q, *d, *dinv;
+  double *certy2;
 };
 
 struct ColVecsMx {    // mixed precision, n-vectors (offsets from the FP64 anchor x0)
   float *dxt, *dx, *ktdy, *s0, *xlo, *xhi;
   double *x0, *kty0, *xout, *certx, *dxt64;
   const double *c, *l, *u, *e, *einv;
+  double *certx2;
 };
 
 // Message for rhpdhg_last_error(NULL) (calls without a handle).

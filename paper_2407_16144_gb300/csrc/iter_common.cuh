@@ -17,13 +17,63 @@ __device__ __forceinline__ double proj_lambda(double g, double l, double u) {
   return 0.0;
 }
 
-// Row-kernel slots: sums 0 dy2, 1 cross, 2 ya2, 3 rp2, 4 qy, 5 qv ; maxima 6 yneg, 7 kd_eq,
-// 8 kd_in.  Completes ||z_t - T(z_t)||_P^2 = ||dx||^2/tau + ||dy||^2/sigma + 2 dy^T K dx, applies
-// the restart rule of eq. adaptive-restart (first epoch: k > tau^0; later: FPR <= beta FPR_0;
-// plus the epoch cap, or the fixed frequency of eq. fixed-restart) and the primal-weight update.
+// Reduction slots.  Row kernel: sums 0 ||dy||^2, 1 dy^T (K dx), 2 ||y~ - y0||^2, 3 primal
+// residual^2, 4 q^T y~, 5 q^T (y-part of T(z) - z), 6 q^T (y-part of z^{n+1,0} - z^{n,0});
+// maxima 7..9 the T(z) - z row tests (y_G sign, |K d| on A rows, (K d)^- on G rows) and
+// 10..12 the same for the anchor movement.
+using RowAcc = Acc<7, 6>;
+using RowAccL = Acc<7, 0>;     // long-row sums (see store_group)
+// Column kernel: sums 0 ||dx||^2, 1 ||x~ - x0||^2, 2 dual residual^2, 3 c^T x~, 4 bound terms of
+// the dual objective, 5 c^T d, 6/7 bound terms of the ray objective for T(z) - z, 8..10 the same
+// for the anchor movement; maxima 11..14 the T(z) - z column tests (d bound signs, (K^T y)^+ on
+// infinite u, (K^T y)^- on infinite l) and 15..18 the same for the anchor movement.
+using ColAcc = Acc<11, 8>;
+using ColAccL = Acc<11, 0>;
+
+__device__ __forceinline__ unsigned row_smask(bool check, bool cert, bool move) {
+  return 0x7u | (check ? 0x18u : 0u) | (cert ? 0x20u : 0u) | (move ? 0x40u : 0u);
+}
+__device__ __forceinline__ unsigned row_mmask(bool cert, bool move) {
+  return (cert ? 0x7u : 0u) | (move ? 0x38u : 0u);
+}
+__device__ __forceinline__ unsigned col_smask(bool check, bool cert, bool move) {
+  return 0x3u | (check ? 0x1Cu : 0u) | (cert ? 0xE0u : 0u) | (move ? 0x700u : 0u);
+}
+__device__ __forceinline__ unsigned col_mmask(bool cert, bool move) {
+  return (cert ? 0xFu : 0u) | (move ? 0xF0u : 0u);
+}
+
+// Farkas tests of one candidate from its reduced parts (Proposition full-infeas, normalised so
+// that the ray objective is 1): the y-part first, then the x-part.
+__device__ __forceinline__ int farkas_status(double qv, double uterm, double lterm, double vy_max,
+                                             double cd, double vx_max, double eps) {
+  const double obj = qv - uterm + lterm;
+  if (obj > 0.0 && vy_max / obj <= eps) return kPrimalInfeasible;
+  if (cd < 0.0 && vx_max / (-cd) <= eps) return kDualInfeasible;
+  return kRunning;
+}
+
+// Completes ||z_t - T(z_t)||_P^2 = ||dx||^2/tau + ||dy||^2/sigma + 2 dy^T K dx, applies the
+// restart rule of eq. adaptive-restart (first epoch: k > tau^0; later: FPR <= beta FPR_0; plus
+// the epoch cap, or the fixed frequency of eq. fixed-restart) and the primal-weight update.
+// With move set (the restart applied by this kernel was decided by a phase-0 column kernel that
+// staged its parts) it first completes the anchor-movement candidate's test.
 __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, const double *r,
                                              long long t, long long k, long long n_ep,
-                                             double sigma) {
+                                             double sigma, bool move) {
+  if (move) {
+    ctl->mv_ready = 0;
+    const int st = farkas_status(r[6], ctl->mv_u, ctl->mv_l,
+                                 fmax(fmax(ctl->mv_au, ctl->mv_al), r[10]), ctl->mv_cd,
+                                 fmax(fmax(r[11], r[12]), fmax(ctl->mv_dlb, ctl->mv_dub)),
+                                 ic.eps_infeas);
+    if (st != kRunning) {
+      ctl->status = st;
+      ctl->cert_src = kCertAnchorMove;
+      ctl->cnt_row = 0;
+      return;
+    }
+  }
   const double tau = ctl->tau, omega = ctl->omega;
   const double fpr2 = ctl->dx_sq / tau + r[0] / sigma + 2.0 * r[1];
   const double fpr0 = (k == 0) ? fpr2 : ctl->fpr0_sq;
@@ -45,9 +95,9 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
   ctl->rp_sq = r[3];
   ctl->qy = r[4];
   ctl->inf_qv = r[5];
-  ctl->inf_yneg = r[6];
-  ctl->inf_kd_eq = r[7];
-  ctl->inf_kd_in = r[8];
+  ctl->inf_yneg = r[7];
+  ctl->inf_kd_eq = r[8];
+  ctl->inf_kd_in = r[9];
   if (!isfinite(fpr2)) ctl->status = kNumericalError;
   if (rs) {
     if (ic.pw_update) {
@@ -72,27 +122,39 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
   ctl->stage = 1;
 }
 
-// Column-kernel slots: sums 0 dx2, 1 xa2, 2 rd2, 3 cx, 4 bnd, 5 cd, 6 uterm, 7 lterm ;
-// maxima 8 dlb, 9 dub, 10 ainf_u, 11 ainf_l.  Certificate tests at restart points (the
-// displacement T(z^{n,0}) - z^{n,0}, Theorem infeas; normalised so the ray objective is 1),
-// then the rel-KKT termination test on check iterations, then the iteration counters.
+// Certificate test of the displacement T(z) - z (cert: at restart points, Theorem infeas, and
+// at check iterations), then the rel-KKT termination test on check iterations, then the
+// iteration counters.  With move set (this kernel applied a restart decision) the column parts
+// of the anchor-movement candidate are staged for the next row kernel.
 __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, const double *r,
-                                             long long t, bool check, bool rp, int phase) {
+                                             long long t, bool check, bool cert, bool rp,
+                                             bool move, int phase) {
   ctl->dx_sq = r[0];
   ctl->xa_sq = r[1];
   int st = kRunning;
-  if (rp) {
-    const double obj = ctl->inf_qv - r[6] + r[7];
-    const double vy = fmax(fmax(r[10], r[11]), ctl->inf_yneg);
-    const double cd = r[5];
-    const double vx = fmax(fmax(ctl->inf_kd_eq, ctl->inf_kd_in), fmax(r[8], r[9]));
-    if (obj > 0.0 && vy / obj <= ic.eps_infeas) st = kPrimalInfeasible;
-    else if (cd < 0.0 && vx / (-cd) <= ic.eps_infeas) st = kDualInfeasible;
-    // With FP32 offsets a diverging iterate carries about 1e-5 relative rounding, so a
-    // certificate cannot reach eps_infeas; once the candidate comes within 1e-3 of certifying,
-    // the solve continues in FP64 from this restart point.
-    else if (ic.mixed && ((obj > 0.0 && vy / obj <= 1e-3) || (cd < 0.0 && vx / (-cd) <= 1e-3)))
+  if (cert) {
+    const double vy = fmax(fmax(r[13], r[14]), ctl->inf_yneg);
+    const double vx = fmax(fmax(ctl->inf_kd_eq, ctl->inf_kd_in), fmax(r[11], r[12]));
+    st = farkas_status(ctl->inf_qv, r[6], r[7], vy, r[5], vx, ic.eps_infeas);
+    if (st != kRunning) {
+      ctl->cert_src = rp ? kCertRestartPoint : kCertCheck;
+    } else if (ic.mixed && rp &&
+               farkas_status(ctl->inf_qv, r[6], r[7], vy, r[5], vx, 1e-3) != kRunning) {
+      // With FP32 offsets a diverging iterate carries about 1e-5 relative rounding, so this
+      // candidate cannot reach eps_infeas; once it comes within 1e-3 of certifying, the solve
+      // continues in FP64 from this restart point.
       st = kEscalate;
+    }
+  }
+  if (move) {
+    ctl->mv_cd = r[8];
+    ctl->mv_u = r[9];
+    ctl->mv_l = r[10];
+    ctl->mv_dlb = r[15];
+    ctl->mv_dub = r[16];
+    ctl->mv_au = r[17];
+    ctl->mv_al = r[18];
+    ctl->mv_ready = 1;
   }
   if (st == kRunning && check) {
     const double rel_p = sqrt(ctl->rp_sq) / ic.qn1;
@@ -124,28 +186,43 @@ __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, con
 
 // ---------------------------------------------------------------------------------------------
 // The FP64 per-row epilogues of one PDHG evaluation, shared by the tiled single-LP kernels and
-// the CTA-resident batched kernel.
+// the CTA-resident batched kernel.  Sums go to S (the lane's own accumulator, or the long-row
+// accumulator whose order is fixed per group), maxima always to M.
 
 struct StepFlags {
   int restart;      // the pending transition is a restart: z_t = T(z_{t-1})
   double w;         // Halpern weight (k+1)/(k+2) of the pending blend
   double step;      // sigma (row epilogue) or tau (column epilogue)
   bool check;       // termination-check iteration
-  bool rp;          // restart point (k == 0, n >= 1): certificate test
+  bool cert;        // certificate test of T(z) - z at this iteration (restart point or check)
+  bool rp;          // restart point (k == 0, n >= 1): z_t is the anchor
+  bool move;        // this restart's anchor movement z^{n+1,0} - z^{n,0} is tested
+  bool stash;       // rHPDHG: keep x_{t+1}, K^T y_{t+1} (the next iteration is a check)
   int m_eq;
 };
 
 // Row i of K^ x~_t = dot: forms y_t and K x_t by the pending blend (eq. hpdhg / eq. hrpdhg, or
-// the restart point), takes the dual step of eq. pdhg, and accumulates the fixed-point-residual
-// parts (0 ||dy||^2, 1 dy^T (K x - K x~), 2 ||y~ - y0||^2), the check parts (3 primal residual^2,
-// 4 q^T y~) and the certificate parts (5 q^T (y~ - y), maxima 0..2).
-template <int RHO2>
+// the restart point), takes the dual step of eq. pdhg, and accumulates the fixed-point-residual,
+// check and certificate parts (slots above).  At a restart with move set, the old anchor gives
+// the row parts of z^{n+1,0} - z^{n,0} before it is replaced.
+template <int RHO2, class AS, class AM>
 __device__ __forceinline__ void row_epilogue(int i, double dot, const RowVecs &v,
-                                             const StepFlags &f, Acc<6, 3> &a) {
+                                             const StepFlags &f, AS &S, AM &M) {
   const double ytp = v.yt[i], kxtp = v.kxt[i];
   const double w = f.w, sigma = f.step;
+  const double qi = v.q[i];
   double yi, kxi, y0i;
   if (f.restart) {
+    if (f.move) {
+      const double dyb = ytp - v.y0[i];                  // y^{n+1,0} - y^{n,0} (scaled)
+      const double kdb = (kxtp - v.kx0[i]) * v.dinv[i];  // K (x^{n+1,0} - x^{n,0}) (unscaled)
+      const double di = v.d[i];
+      S.s[6] += qi * dyb;
+      if (i >= f.m_eq) M.mx[3] = fmax(M.mx[3], fmax(-dyb * di, 0.0));
+      if (i < f.m_eq) M.mx[4] = fmax(M.mx[4], fabs(kdb));
+      else M.mx[5] = fmax(M.mx[5], fmax(-kdb, 0.0));
+      v.certy2[i] = dyb * di;
+    }
     yi = ytp; kxi = kxtp; y0i = yi;
     v.y0[i] = yi; v.kx0[i] = kxi;
     if (RHO2) { v.y[i] = yi; v.kx[i] = kxi; }
@@ -161,42 +238,59 @@ __device__ __forceinline__ void row_epilogue(int i, double dot, const RowVecs &v
       kxi = w * kxtp + (1.0 - w) * kx0i;
     }
   }
-  const double qi = v.q[i];
   double yn = yi + sigma * (qi - 2.0 * dot + kxi);
   if (i >= f.m_eq) yn = fmax(yn, 0.0);
   v.yt[i] = yn;
   v.kxt[i] = dot;
   const double dy = yi - yn;
-  a.s[0] += dy * dy;
-  a.s[1] += dy * (kxi - dot);
+  S.s[0] += dy * dy;
+  S.s[1] += dy * (kxi - dot);
   const double ya = yn - y0i;
-  a.s[2] += ya * ya;
+  S.s[2] += ya * ya;
   if (f.check) {
     double r = (qi - dot) * v.dinv[i];
     if (i >= f.m_eq) r = fmax(r, 0.0);
-    a.s[3] += r * r;
-    a.s[4] += qi * yn;
+    S.s[3] += r * r;
+    S.s[4] += qi * yn;
   }
-  if (f.rp) {
-    const double vy = yn - yi;            // y-part of T(z) - z at the restart point
-    a.s[5] += qi * vy;
+  if (f.cert) {
+    const double vy = yn - yi;            // y-part of T(z) - z
+    S.s[5] += qi * vy;
     const double di = v.d[i];
-    if (i >= f.m_eq) a.mx[0] = fmax(a.mx[0], fmax(-vy * di, 0.0));
+    if (i >= f.m_eq) M.mx[0] = fmax(M.mx[0], fmax(-vy * di, 0.0));
     const double kd = (dot - kxi) * v.dinv[i];   // K d (unscaled), d = x~ - x
-    if (i < f.m_eq) a.mx[1] = fmax(a.mx[1], fabs(kd));
-    else a.mx[2] = fmax(a.mx[2], fmax(-kd, 0.0));
+    if (i < f.m_eq) M.mx[1] = fmax(M.mx[1], fabs(kd));
+    else M.mx[2] = fmax(M.mx[2], fmax(-kd, 0.0));
     v.certy[i] = vy * di;
   }
 }
 
-// Column j of K^T y~_t = dot: the check parts at (x~_t, y~_t) (2 dual residual^2, 3 c^T x~,
-// 4 bound terms of the dual objective), the certificate parts at restart points (5 c^T d,
-// 6/7 bound terms of the ray objective, maxima 0..3), then the blend to x_{t+1} and the primal
-// step x~_{t+1} = proj_X(x_{t+1} - tau (c - K^T y_{t+1})) with parts 0 ||x - x~||^2,
-// 1 ||x~ - x0||^2.
-template <int RHO2>
+// Column parts of one certificate candidate: d (scaled x-part), kv = K^T of its y-part
+// (scaled); sums at s0 (c^T d), s0+1 / s0+2 (bound terms of the ray objective), maxima at
+// m0..m0+3.  Writes the unscaled d to cert.
+template <class V, class AS, class AM>
+__device__ __forceinline__ void col_cert_parts(int j, double d, double kv, const V &v,
+                                               double cj, double lj, double uj, AS &S, AM &M,
+                                               int s0, int m0, double *cert) {
+  S.s[s0] += cj * d;
+  const double du = d * v.e[j];
+  const bool lf = isfinite(lj), uf = isfinite(uj);
+  if (lf) M.mx[m0] = fmax(M.mx[m0], fmax(-du, 0.0));
+  if (uf) M.mx[m0 + 1] = fmax(M.mx[m0 + 1], fmax(du, 0.0));
+  if (uf) S.s[s0 + 1] += fmax(kv, 0.0) * uj;
+  else M.mx[m0 + 2] = fmax(M.mx[m0 + 2], fmax(kv * v.einv[j], 0.0));
+  if (lf) S.s[s0 + 2] += fmax(-kv, 0.0) * lj;
+  else M.mx[m0 + 3] = fmax(M.mx[m0 + 3], fmax(-kv * v.einv[j], 0.0));
+  cert[j] = du;
+}
+
+// Column j of K^T y~_t = dot: the check parts at (x~_t, y~_t), the T(z) - z certificate parts
+// (z_t is the anchor at a restart point, else the stored x_t, K^T y_t), then the blend to
+// x_{t+1} (at a restart with move set, first the anchor-movement parts against the old
+// anchor) and the primal step x~_{t+1} = proj_X(x_{t+1} - tau (c - K^T y_{t+1})).
+template <int RHO2, class AS, class AM>
 __device__ __forceinline__ void col_epilogue(int j, double dot, const ColVecs &v,
-                                             const StepFlags &f, Acc<8, 4> &a) {
+                                             const StepFlags &f, AS &S, AM &M) {
   const double xtj = v.xt[j];
   const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
   const double w = f.w, tau = f.step;
@@ -204,30 +298,21 @@ __device__ __forceinline__ void col_epilogue(int j, double dot, const ColVecs &v
     const double g = cj - dot;
     const double lam = proj_lambda(g, lj, uj);
     const double rd = (g - lam) * v.einv[j];
-    a.s[2] += rd * rd;
-    a.s[3] += cj * xtj;
-    if (lam > 0.0) a.s[4] += lj * lam;
-    else if (lam < 0.0) a.s[4] += uj * lam;
+    S.s[2] += rd * rd;
+    S.s[3] += cj * xtj;
+    if (lam > 0.0) S.s[4] += lj * lam;
+    else if (lam < 0.0) S.s[4] += uj * lam;
     v.xout[j] = xtj;
   }
   double x0j = v.x0[j], kty0j = v.kty0[j];
-  if (f.rp) {
-    // restart point: x_t = x^{n,0} and K^T y_t = K^T y^{n,0}
-    const double dsc = xtj - x0j;               // x-part of T(z) - z (scaled)
-    a.s[5] += cj * dsc;
-    const double du = dsc * v.e[j];
-    const bool lf = isfinite(lj), uf = isfinite(uj);
-    if (lf) a.mx[0] = fmax(a.mx[0], fmax(-du, 0.0));
-    if (uf) a.mx[1] = fmax(a.mx[1], fmax(du, 0.0));
-    const double kv = dot - kty0j;              // K^T (y~ - y) (scaled)
-    if (uf) a.s[6] += fmax(kv, 0.0) * uj;
-    else a.mx[2] = fmax(a.mx[2], fmax(kv * v.einv[j], 0.0));
-    if (lf) a.s[7] += fmax(-kv, 0.0) * lj;
-    else a.mx[3] = fmax(a.mx[3], fmax(-kv * v.einv[j], 0.0));
-    v.certx[j] = du;
+  if (f.cert) {
+    const double xc = f.rp ? x0j : v.x[j];
+    const double kc = f.rp ? kty0j : v.kty[j];
+    col_cert_parts(j, xtj - xc, dot - kc, v, cj, lj, uj, S, M, 5, 0, v.certx);
   }
   double xn, kn;
   if (f.restart) {
+    if (f.move) col_cert_parts(j, xtj - x0j, dot - kty0j, v, cj, lj, uj, S, M, 8, 4, v.certx2);
     xn = xtj; kn = dot;
     v.x0[j] = xn; v.kty0[j] = kn;
     x0j = xn; kty0j = kn;
@@ -240,12 +325,13 @@ __device__ __forceinline__ void col_epilogue(int j, double dot, const ColVecs &v
     xn = w * xtj + (1.0 - w) * x0j;
     kn = w * dot + (1.0 - w) * kty0j;
   }
+  if (!RHO2 && f.stash) { v.x[j] = xn; v.kty[j] = kn; }
   const double xtn = fmin(fmax(xn - tau * (cj - kn), lj), uj);
   v.xt[j] = xtn;
   const double dx = xn - xtn;
-  a.s[0] += dx * dx;
+  S.s[0] += dx * dx;
   const double xa = xtn - x0j;
-  a.s[1] += xa * xa;
+  S.s[1] += xa * xa;
 }
 
 }  // namespace rh

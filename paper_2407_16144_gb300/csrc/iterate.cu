@@ -8,9 +8,11 @@
 //     rule of eq. adaptive-restart (Section 3) and the primal-weight update, and records the
 //     decision for the next blend.
 //   column kernel, iteration t: K^T y~_t (tiled SpMV over the rows of K^T), the termination test
-//     at (x~_t, y~_t) on check iterations, the certificate test at restart points
-//     (Theorem infeas), then the primal blend to x_{t+1} and the primal step of eq. pdhg,
-//     x~_{t+1} = proj_X(x_{t+1} - tau (c - K^T y_{t+1})).
+//     at (x~_t, y~_t) on check iterations, the certificate test of T(z_t) - z_t at restart points
+//     (Theorem infeas) and check iterations, then the primal blend to x_{t+1} and the primal step
+//     of eq. pdhg, x~_{t+1} = proj_X(x_{t+1} - tau (c - K^T y_{t+1})).  At a restart decision it
+//     also forms the column parts of the second candidate, the anchor movement
+//     z^{n+1,0} - z^{n,0}; the next row kernel adds the row parts and completes its test.
 //
 // K x and K^T y of the blended iterates are never recomputed: the blends are linear, so the
 // products are blended with the same weights from the products of the PDHG points, which the
@@ -23,12 +25,6 @@ namespace rh {
 
 namespace {
 
-// sums: 0 dy2, 1 cross, 2 ya2, 3 rp2, 4 qy, 5 qv ; maxima: 0 yneg, 1 kd_eq, 2 kd_in
-using RowAcc = Acc<6, 3>;
-// sums: 0 dx2, 1 xa2, 2 rd2, 3 cx, 4 bnd, 5 cd, 6 uterm, 7 lterm ;
-// maxima: 0 dlb, 1 dub, 2 ainf_u, 3 ainf_l
-using ColAcc = Acc<8, 4>;
-
 template <int RHO2>
 __global__ void __launch_bounds__(kBlockThreads)
 k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ xt,
@@ -40,28 +36,29 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   const double w = ctl->w, sigma = ctl->sigma;
   const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
   const bool rp = (k == 0 && n_ep >= 1);
-  const int m_eq = ic.m_eq;
-  RowAcc a, al;   // al: contributions of long rows (see walk_tiles)
+  const bool cert = rp || check;
+  const bool move = restart && ctl->mv_ready;
+  RowAcc a;
+  RowAccL al;     // long-row sums (see walk_tiles)
   a.zero();
   al.zero();
   double *my = smem + (threadIdx.x >> 5) * lay.seg;
 
-  StepFlags fl{restart, w, sigma, check, rp, m_eq};
-  auto body = [&](int i, double dot, RowAcc &acc) { row_epilogue<RHO2>(i, dot, v, fl, acc); };
+  StepFlags fl{restart, w, sigma, check, cert, rp, (bool)move, false, ic.m_eq};
   auto epi = [&](int i, double dot, bool lg) {
-    if (lg) body(i, dot, al);
-    else body(i, dot, a);
+    if (lg) row_epilogue<RHO2>(i, dot, v, fl, al, a);
+    else row_epilogue<RHO2>(i, dot, v, fl, a, a);
   };
-  const unsigned smask = 0x7u | (check ? 0x18u : 0u) | (rp ? 0x20u : 0u);
-  const unsigned mmask = rp ? 0x7u : 0u;
-  auto gdone = [&](int grp) { store_group(al, smask, mmask, ws.group_part, grp); };
+  const unsigned smask = row_smask(check, cert, move);
+  const unsigned mmask = row_mmask(cert, move);
+  auto gdone = [&](int grp) { store_group(al, smask, ws.group_part, grp); };
   auto gather = [&](int j) { return xt[j]; };
   walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
-    double r[9];
-    grid_finish<6, 3>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
-    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma);
+    double r[13];
+    grid_finish<7, 6>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
+    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
   }
 }
 
@@ -76,27 +73,31 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   const double w = ctl->w, tau = ctl->tau;
   const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
   const bool rp = phase == 0 && (k == 0 && n_ep >= 1);
-  ColAcc a, al;
+  const bool cert = rp || check;
+  const bool move = phase == 0 && restart;
+  const long long tn = phase == 0 ? t + 1 : t;     // the iteration this kernel's x_{t+1} opens
+  const bool stash = ((tn + 1) % ic.check_every == 0) || (tn + 1 >= ic.max_iters);
+  ColAcc a;
+  ColAccL al;
   a.zero();
   al.zero();
   double *my = smem + (threadIdx.x >> 5) * lay.seg;
 
-  StepFlags fl{restart, w, tau, check, rp, ic.m_eq};
-  auto body = [&](int j, double dot, ColAcc &acc) { col_epilogue<RHO2>(j, dot, v, fl, acc); };
+  StepFlags fl{restart, w, tau, check, cert, rp, move, stash, ic.m_eq};
   auto epi = [&](int j, double dot, bool lg) {
-    if (lg) body(j, dot, al);
-    else body(j, dot, a);
+    if (lg) col_epilogue<RHO2>(j, dot, v, fl, al, a);
+    else col_epilogue<RHO2>(j, dot, v, fl, a, a);
   };
-  const unsigned smask = 0x3u | (check ? 0x1Cu : 0u) | (rp ? 0xE0u : 0u);
-  const unsigned mmask = rp ? 0xFu : 0u;
-  auto gdone = [&](int grp) { store_group(al, smask, mmask, ws.group_part, grp); };
+  const unsigned smask = col_smask(check, cert, move);
+  const unsigned mmask = col_mmask(cert, move);
+  auto gdone = [&](int grp) { store_group(al, smask, ws.group_part, grp); };
   auto gather = [&](int j) { return ytv[j]; };
   walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
-    double r[12];
-    grid_finish<8, 4>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
-    if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, phase);
+    double r[19];
+    grid_finish<11, 8>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
+    if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, cert, rp, move, phase);
   }
 }
 

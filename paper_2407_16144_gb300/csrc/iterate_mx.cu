@@ -57,28 +57,49 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   const float wf = (float)w, sigf = (float)sigma;
   const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
   const bool rp = (k == 0 && n_ep >= 1);
+  const bool move = restart && ctl->mv_ready;
   const int m_eq = ic.m_eq;
   // staging: FP64 walks use (32 L + 4) doubles per warp, FP32 walks (32 L + 4) floats (the
   // FP32-only kernels are launched with half the shared memory)
   double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
   float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
-  Acc<6, 3> a, al;
+  RowAcc a;
+  RowAccL al;     // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
   F3 fa, fl;
-  const unsigned smask = 0x7u | (check ? 0x18u : 0u) | (rp ? 0x20u : 0u);
-  const unsigned mmask = rp ? 0x7u : 0u;
+  const unsigned smask = row_smask(check, rp, move);
+  const unsigned mmask = row_mmask(rp, move);
 
   if constexpr (MODE == 1) {
     // Restart point z^{n+1,0} = T(z^{n,k}).  First K x0' with the FP64 matrix (x0' was formed by
     // the preceding column kernel); then, in FP64 throughout, K dxt (dxt = x~ - x0' of this
     // iteration, exact in dxt64) and the dual step, so the restart point's T(z) - z, which
     // Theorem infeas uses as the certificate candidate, carries no FP32 rounding.
-    auto epiA = [&](int i, double dot, bool) { v.kx0[i] = dot; };
+    // With move set, the old anchor first gives the row parts of the anchor movement
+    // z^{n+1,0} - z^{n,0} (y0' = y0 + dyt, K x0' from this walk), in FP64.
+    auto moveparts = [&](int i, double dot, auto &S) {
+      const double y0i = v.y0[i];
+      const double dyb = (y0i + (double)v.dyt[i]) - y0i;
+      const double kdb = (dot - v.kx0[i]) * v.dinv[i];
+      const double di = v.d[i];
+      S.s[6] += v.q[i] * dyb;
+      if (i >= m_eq) a.mx[3] = fmax(a.mx[3], fmax(-dyb * di, 0.0));
+      if (i < m_eq) a.mx[4] = fmax(a.mx[4], fabs(kdb));
+      else a.mx[5] = fmax(a.mx[5], fmax(-kdb, 0.0));
+      v.certy2[i] = dyb * di;
+    };
+    auto epiA = [&](int i, double dot, bool lg) {
+      if (move) {
+        if (lg) moveparts(i, dot, al);
+        else moveparts(i, dot, a);
+      }
+      v.kx0[i] = dot;
+    };
     auto gA = [&](int j) { return x0[j]; };
-    auto nop = [&](int) {};
-    walk_tiles<double, double>(lay, v64, gA, my64, wa, epiA, nop);
-    auto body = [&](int i, double kd, Acc<6, 3> &A) {
+    auto gdoneA = [&](int grp) { store_group(al, smask & 0x40u, wb.group_part, grp); };
+    walk_tiles<double, double>(lay, v64, gA, my64, wa, epiA, gdoneA);
+    auto body = [&](int i, double kd, auto &A) {
       const double y0i = v.y0[i] + (double)v.dyt[i];     // y0' = y~ of the restart iteration
       v.y0[i] = y0i;
       const double kx0i = __ldcg(v.kx0 + i);              // may come from another warp
@@ -103,10 +124,10 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       if (rp) {
         A.s[5] += qi * nd;
         const double di = v.d[i];
-        if (i >= m_eq) A.mx[0] = fmax(A.mx[0], fmax(-nd * di, 0.0));
+        if (i >= m_eq) a.mx[0] = fmax(a.mx[0], fmax(-nd * di, 0.0));
         const double kdd = kd * v.dinv[i];
-        if (i < m_eq) A.mx[1] = fmax(A.mx[1], fabs(kdd));
-        else A.mx[2] = fmax(A.mx[2], fmax(-kdd, 0.0));
+        if (i < m_eq) a.mx[1] = fmax(a.mx[1], fabs(kdd));
+        else a.mx[2] = fmax(a.mx[2], fmax(-kdd, 0.0));
         v.certy[i] = nd * di;
       }
     };
@@ -114,11 +135,11 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       if (lg) body(i, kd, al);
       else body(i, kd, a);
     };
-    auto gdone = [&](int grp) { store_group(al, smask, mmask, wb.group_part, grp); };
+    auto gdone = [&](int grp) { store_group(al, smask & ~0x40u, wb.group_part, grp); };
     auto gB = [&](int j) { return dxt64[j]; };
     walk_tiles<double, double>(lay, v64, gB, my64, wb, epi, gdone);
   } else {
-    auto body = [&](int i, float kd, Acc<6, 3> &A, F3 &F) {
+    auto body = [&](int i, float kd, auto &A, F3 &F) {
       const float dytp = v.dyt[i], kdxtp = v.kdxt[i];
       float dy, kdx;
       if (RHO2) {
@@ -155,7 +176,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       al.s[1] += (double)fl.b;
       al.s[2] += (double)fl.c;
       fl = F3();
-      store_group(al, smask, mmask, wb.group_part, grp);
+      store_group(al, smask, wb.group_part, grp);
     };
     auto gB = [&](int j) { return dxt[j]; };
     walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone);
@@ -171,9 +192,9 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   }
 
   if (cta_reduce_and_ticket(a, smask, mmask, prewarp, part, &ctl->cnt_row)) {
-    double r[9];
-    grid_finish<6, 3>(part, r, smask, mmask, wb.group_part, lay.n_long_tiles);
-    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma);
+    double r[13];
+    grid_finish<7, 6>(part, r, smask, mmask, wb.group_part, lay.n_long_tiles);
+    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
   }
 }
 
@@ -190,6 +211,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   const int restart = ctl->restart_pending;
   const bool rp = phase == 0 && (k == 0 && n_ep >= 1);
   if ((restart || rp) != (MODE == 1)) return;
+  const bool move = phase == 0 && restart;
   const double w = ctl->w, tau = ctl->tau;
   const float wf = (float)w, tauf = (float)tau;
   const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
@@ -197,16 +219,17 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   // FP32-only kernels are launched with half the shared memory)
   double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
   float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
-  Acc<8, 4> a, al;
+  ColAcc a;
+  ColAccL al;     // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
   F3 fa, fl;
-  const unsigned smask = 0x3u | (check ? 0x1Cu : 0u) | (rp ? 0xE0u : 0u);
-  const unsigned mmask = rp ? 0xFu : 0u;
+  const unsigned smask = col_smask(check, rp, move);
+  const unsigned mmask = col_mmask(rp, move);
 
   // checks and certificates at (x~_t, y~_t) given x~_t - x0 (xo), K^T y~_t (kty) and
   // K^T (y~_t - y_t) (ktd), all FP64
-  auto checks = [&](int j, double x0j, double xo, double kty, double ktd, Acc<8, 4> &A) {
+  auto checks = [&](int j, double x0j, double xo, double kty, double ktd, auto &A) {
     const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
     if (check) {
       const double g = cj - kty;
@@ -219,24 +242,14 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       else if (lam < 0.0) A.s[4] += uj * lam;
       v.xout[j] = xt;
     }
-    if (rp) {
-      A.s[5] += cj * xo;                        // x-part of T(z) - z at the restart point
-      const double du = xo * v.e[j];
-      const bool lf = isfinite(lj), uf = isfinite(uj);
-      if (lf) A.mx[0] = fmax(A.mx[0], fmax(-du, 0.0));
-      if (uf) A.mx[1] = fmax(A.mx[1], fmax(du, 0.0));
-      if (uf) A.s[6] += fmax(ktd, 0.0) * uj;
-      else A.mx[2] = fmax(A.mx[2], fmax(ktd * v.einv[j], 0.0));
-      if (lf) A.s[7] += fmax(-ktd, 0.0) * lj;
-      else A.mx[3] = fmax(A.mx[3], fmax(-ktd * v.einv[j], 0.0));
-      v.certx[j] = du;
-    }
+    // x-part of T(z) - z at the restart point, and K^T of its y-part
+    if (rp) col_cert_parts(j, xo, ktd, v, cj, lj, uj, A, a, 5, 0, v.certx);
   };
   auto gdone = [&](int grp) {
     al.s[0] += (double)fl.a;
     al.s[1] += (double)fl.b;
     fl = F3();
-    store_group(al, smask, mmask, (restart ? wa : wb).group_part, grp);
+    store_group(al, smask, (restart ? wa : wb).group_part, grp);
   };
 
   if constexpr (MODE == 1) {
@@ -244,11 +257,15 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     // z^{n+1,0} = T(z^{n,k}): K^T y0' exactly (FP64 matrix, gathered y0 + dyt), x0' = x0 + dxt,
     // and the next PDHG point x~_{t+1} - x0' in FP64 (kept in dxt64 for the restart point's
     // certificate test)
-    auto body = [&](int j, double kty, Acc<8, 4> &A) {
+    auto body = [&](int j, double kty, auto &A) {
       const double x0j = v.x0[j];
       const float dxtj = v.dxt[j];
-      checks(j, x0j, (double)dxtj, kty, kty - v.kty0[j], A);
+      const double ktd = kty - v.kty0[j];
+      checks(j, x0j, (double)dxtj, kty, ktd, A);
       const double x0n = x0j + (double)dxtj;
+      // column parts of the anchor movement z^{n+1,0} - z^{n,0}, against the old anchor
+      if (move)
+        col_cert_parts(j, x0n - x0j, ktd, v, v.c[j], v.l[j], v.u[j], A, a, 8, 4, v.certx2);
       v.x0[j] = x0n;
       v.kty0[j] = kty;
       const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
@@ -270,7 +287,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     walk_tiles<double, double>(lay, v64, gA, my64, wa, epi, gdone);
    } else {
     // first iteration of an epoch: K^T (y~ - y0) in FP64 from the exact dyt64 of the row kernel
-    auto body = [&](int j, double ktd, Acc<8, 4> &A, F3 &F) {
+    auto body = [&](int j, double ktd, auto &A, F3 &F) {
       const double xo = v.dxt64[j];
       const double x0j = check ? v.x0[j] : 0.0;
       const double kty = check ? v.kty0[j] + ktd : 0.0;
@@ -300,7 +317,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     walk_tiles<double, double>(lay, v64, gA, my64, wb, epi, gdone);
    }
   } else {
-    auto body = [&](int j, float ktdyt, Acc<8, 4> &A, F3 &F) {
+    auto body = [&](int j, float ktdyt, auto &A, F3 &F) {
       const float dxtj = v.dxt[j];
       if (check) {
         const double x0j = v.x0[j];
@@ -338,9 +355,9 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   }
 
   if (cta_reduce_and_ticket(a, smask, mmask, prewarp, part, &ctl->cnt_col)) {
-    double r[12];
-    grid_finish<8, 4>(part, r, smask, mmask, (restart ? wa : wb).group_part, lay.n_long_tiles);
-    if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, phase);
+    double r[19];
+    grid_finish<11, 8>(part, r, smask, mmask, (restart ? wa : wb).group_part, lay.n_long_tiles);
+    if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, rp, move, phase);
   }
 }
 

@@ -26,6 +26,8 @@ ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_STATE = -1, -2, -3, 
 MEM_HOST, MEM_DEVICE = 0, 1
 STATUS_NAMES = ["RUNNING", "OPTIMAL", "PRIMAL_INFEASIBLE", "DUAL_INFEASIBLE",
                 "ITERATION_LIMIT", "TIME_LIMIT", "NUMERICAL_ERROR", "CANCELLED"]
+# which candidate certified infeasibility (rhpdhg_result.cert_source)
+CERT_NONE, CERT_RESTART_POINT, CERT_CHECK, CERT_ANCHOR_MOVE = range(4)
 
 _dp = C.POINTER(C.c_double)
 
@@ -53,7 +55,8 @@ class rhpdhg_params(C.Structure):
 
 
 class rhpdhg_result(C.Structure):
-    _fields_ = [("status", C.c_int32), ("out_memory", C.c_int32), ("iters", C.c_int64),
+    _fields_ = [("status", C.c_int32), ("out_memory", C.c_int32), ("cert_source", C.c_int32),
+                ("reserved", C.c_int32), ("iters", C.c_int64),
                 ("restarts", C.c_int64), ("rel_p", C.c_double), ("rel_d", C.c_double),
                 ("rel_gap", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("solve_seconds", C.c_double), ("eta", C.c_double), ("omega", C.c_double),
@@ -332,7 +335,8 @@ class Server:
             return None
         _check(rc, None, "rhpdhg_server_poll")
         self._shape.pop(ticket)
-        res = Result(status=r.status, iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
+        res = Result(status=r.status, cert_source=r.cert_source,
+                     iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
                      rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
                      dual_obj=r.dual_obj, solve_seconds=r.solve_seconds, eta=r.eta,
                      omega=r.omega, sigma_max=r.sigma_max, x=x, y=y[:m], cert_x=cx,
@@ -422,7 +426,8 @@ class Batch:
         if rc == BUSY:
             return None
         _check(rc, None, "rhpdhg_batch_poll")
-        res = Result(status=r.status, iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
+        res = Result(status=r.status, cert_source=r.cert_source,
+                     iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
                      rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
                      dual_obj=r.dual_obj, solve_seconds=0.0, eta=r.eta, omega=r.omega,
                      sigma_max=r.sigma_max, x=x, y=y[:m], cert_x=cx, cert_y=cy[:m])
@@ -534,6 +539,7 @@ class Result:
     y: np.ndarray
     cert_x: np.ndarray
     cert_y: np.ndarray
+    cert_source: int = 0     # CERT_* of an infeasibility status
 
     @property
     def status_name(self) -> str:
@@ -614,7 +620,8 @@ class Solver:
         if rc == BUSY:
             return None
         _check(rc, self.h, "rhpdhg_poll")
-        return Result(status=r.status, iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
+        return Result(status=r.status, cert_source=r.cert_source,
+                      iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
                       rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
                       dual_obj=r.dual_obj, solve_seconds=r.solve_seconds, eta=r.eta,
                       omega=r.omega, sigma_max=r.sigma_max, x=x, y=y, cert_x=cert_x,

@@ -87,20 +87,28 @@ def test_batch_alone_equals_in_mix(rh):
     assert np.array_equal(alone.x, inmix.x) and np.array_equal(alone.y, inmix.y)
 
 
-def test_batch_certificates(rh):
-    lps = [lpgen.make_primal_infeasible(3, 500, 1000), lpgen.make_dual_infeasible(3, 500, 1000)]
-    with rh.Batch(4, 128 << 20) as b:
-        slots = [b.add(lp, max_iters=50_000, max_epoch_len=200) for lp in lps]
+@pytest.mark.parametrize("C", [64, 100_000])
+def test_batch_certificates(rh, C):
+    """Batched slots detect infeasibility at the oracle's iteration with the oracle's
+    certificate source (T(z) - z at checks or restart points, or the anchor movement)."""
+    lps = [lpgen.make_primal_infeasible(3, 500, 1000), lpgen.make_dual_infeasible(3, 500, 1000),
+           lpgen.make_dual_infeasible_twin(3, 500, 1000)]
+    with rh.Batch(4, 256 << 20) as b:
+        slots = [b.add(lp, max_iters=50_000, max_epoch_len=200, check_every=C) for lp in lps]
         res = b.run_all(slots, iters=256)
-    K = [O.csr_matrix(lp) for lp in lps]
-    r = res[slots[0]]
-    assert r.status == rh.STATUS_PRIMAL_INFEASIBLE
-    by = lps[0].q @ r.cert_y
-    assert by > 0 and (K[0].T @ r.cert_y).max() / by <= 1e-8
-    r = res[slots[1]]
-    assert r.status == rh.STATUS_DUAL_INFEASIBLE
-    cd = lps[1].c @ r.cert_x
-    assert cd < 0 and np.abs(K[1] @ r.cert_x).max() / -cd <= 1e-8
+    for lp, sl in zip(lps, slots):
+        r = res[sl]
+        o = O.solve(lp, O.OracleParams(algorithm=1, max_iters=50_000, max_epoch_len=200,
+                                       check_every=C))
+        assert (r.status, r.iters, r.cert_source) == (o.status, o.iters, o.cert_source)
+        K = O.csr_matrix(lp)
+        if r.status == rh.STATUS_PRIMAL_INFEASIBLE:
+            by = lp.q @ r.cert_y
+            assert by > 0 and (K.T @ r.cert_y).max() / by <= 1e-8
+        else:
+            assert r.status == rh.STATUS_DUAL_INFEASIBLE
+            v, cd = O.dual_infeasibility_violation(lp, K, r.cert_x)
+            assert cd < 0 and v <= 1e-8
 
 
 def test_batch_capacity_limits(rh):

@@ -177,15 +177,24 @@ _INFEASIBLE_KINDS = {
 
 
 @pytest.mark.parametrize("alg", [0, 1])
-def test_infeasibility_certificates(rh, alg):
+@pytest.mark.parametrize("cadence", [(64, 200), (100_000, 200), (100_000, 1000)])
+def test_infeasibility_certificates(rh, alg, cadence):
+    """Same status, iteration, restart count and certificate source as the oracle: with checks
+    every 64 iterations T(z) - z at a check usually certifies first; without checks the restart
+    point or the anchor movement does."""
+    C, cap = cadence
     for name, (kind, make) in _INFEASIBLE_KINDS.items():
         lp = make(3, 500, 1000)
-        o = O.solve(lp, O.OracleParams(algorithm=alg, max_iters=50_000, max_epoch_len=200))
-        with rh.Solver(lp, algorithm=alg, max_iters=50_000, max_epoch_len=200) as s:
+        o = O.solve(lp, O.OracleParams(algorithm=alg, max_iters=50_000, max_epoch_len=cap,
+                                       check_every=C))
+        with rh.Solver(lp, algorithm=alg, max_iters=50_000, max_epoch_len=cap,
+                       check_every=C) as s:
             r = s.run()
         _check_certificate(rh, lp, r, kind)
-        assert r.status == o.status and r.iters == o.iters
-        print(f"{name} alg={alg}: detected at {r.iters} (oracle {o.iters})")
+        assert (r.status, r.iters, r.restarts, r.cert_source) == \
+            (o.status, o.iters, o.restarts, o.cert_source)
+        print(f"{name} alg={alg} C={C} cap={cap}: detected at {r.iters} "
+              f"(oracle {o.iters}), source {r.cert_source}")
 
 
 @pytest.mark.parametrize("precision", [0, 1])

@@ -366,6 +366,42 @@ def test_dual_infeasible_twin_certificate(alg):
     assert (-(O.csr_matrix(lp) @ d)).max() / -cd <= 1e-8
 
 
+@pytest.mark.parametrize("case", [
+    # (generator, algorithm, check cadence, epoch cap, expected source)
+    ("primal", 0, 64, 200, O.CERT_CHECK),
+    ("primal", 0, 100_000, 200, O.CERT_RESTART_POINT),
+    ("primal", 1, 100_000, 200, O.CERT_ANCHOR_MOVE),
+    ("dual", 1, 100_000, 200, O.CERT_ANCHOR_MOVE),
+    ("twin", 0, 100_000, 1000, O.CERT_ANCHOR_MOVE),
+])
+def test_each_certificate_candidate_certifies(case):
+    """Both candidates of Lemma sublinear-infeas (T(z) - z at restart points and checks, and the
+    anchor movement z^{n+1,0} - z^{n,0}) end a solve on some instance, and every returned
+    certificate passes the Farkas tests on the unscaled data."""
+    name, alg, C, cap, src = case
+    make = {"primal": lpgen.make_primal_infeasible, "dual": lpgen.make_dual_infeasible,
+            "twin": lpgen.make_dual_infeasible_twin}[name]
+    lp = make(3, m=500, n=1000)
+    r = O.solve(lp, O.OracleParams(algorithm=alg, max_iters=50_000, max_epoch_len=cap,
+                                   check_every=C))
+    assert r.cert_source == src
+    K = O.csr_matrix(lp)
+    if name == "primal":
+        assert r.status == O.PRIMAL_INFEASIBLE
+        by = lp.q @ r.cert_y
+        assert by > 0 and (K.T @ r.cert_y).max() / by <= 1e-8
+    else:
+        assert r.status == O.DUAL_INFEASIBLE
+        v, cd = O.dual_infeasibility_violation(lp, K, r.cert_x)
+        assert cd < 0 and v <= 1e-8
+        # independent restatement of the ray test for this instance's form
+        Kd = K @ r.cert_x
+        if lp.m_eq:
+            assert np.abs(Kd[:lp.m_eq]).max() <= 1e-8 * -cd
+        if lp.m_ineq:
+            assert (-Kd[lp.m_eq:]).max() <= 1e-8 * -cd
+
+
 def test_iteration_limit_status():
     lp = lpgen.make_c1(0)
     r = O.solve(lp, O.OracleParams(eps_rel_kkt=1e-12, max_iters=100))
