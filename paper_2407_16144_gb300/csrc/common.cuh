@@ -335,6 +335,87 @@ __device__ __forceinline__ void load_idx4(const int *p, int *j) {
   j[0] = t.x; j[1] = t.y; j[2] = t.z; j[3] = t.w;
 }
 
+// One long-row chunk (work item `item` < lay.n_chunks) of walk_tiles, by the whole warp.
+template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone>
+__device__ __forceinline__ void walk_chunk(const SideLayout &lay, const SideVals<VT> vals,
+                                           const Src &src, const WalkScratch ws, Epi &epi,
+                                           GroupDone &gdone, int item) {
+  const int lane = threadIdx.x & 31;
+  const int li = lay.chunk_row[item];
+  const int c0 = lay.chunk_ptr[li];
+  const int re = lay.end_l[li];
+  const int cb = lay.beg_l[li] + (item - c0) * kChunk;   // 4-aligned
+  const int ce = min(cb + kChunk, re);
+  // lane reads entries [p0, p0 + 8): two 16-byte index loads, 16 or 32 bytes of values
+  const int p0 = cb + 8 * lane;
+  PT s = PT(0);
+  if (p0 < ce) {
+    int j[8];
+    Vec4<VT> va, vb;
+    load_idx4(lay.idx_l + p0, j);
+    load_idx4(lay.idx_l + p0 + 4, j + 4);
+    va.load(vals.l + p0);
+    vb.load(vals.l + p0 + 4);
+    PT x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = (p0 + u < ce) ? PT(src(j[u])) : PT(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += PT(va.v[u]) * x[u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += PT(vb.v[u]) * x[4 + u];
+  }
+  s = warp_sum(s);
+  const int grp = li / kTileRows;
+  const int g0 = grp * kTileRows;
+  const int g1 = min(g0 + kTileRows, lay.n_long);
+  int fin = 0;
+  if (lane == 0) {
+    ws.chunk_part[item] = (double)s;
+    __threadfence();
+    const unsigned int need = (unsigned int)(lay.chunk_ptr[g1] - lay.chunk_ptr[g0]);
+    const unsigned int old = atomicAdd(ws.group_done + grp, 1u);
+    fin = (old == need - 1) ? 1 : 0;
+  }
+  fin = __shfl_sync(0xffffffffu, fin, 0);
+  if (fin) {
+    __threadfence();
+    const int lr = g0 + lane;
+    if (lr < g1) {
+      PT d = PT(0);
+      for (int c = lay.chunk_ptr[lr]; c < lay.chunk_ptr[lr + 1]; ++c)
+        d += PT(__ldcg(ws.chunk_part + c));
+      epi(lay.long_rows[lr], d, true);
+    }
+    // the finishing warp varies from run to run: the group's reduction contributions go to the
+    // group's own slots, which the last CTA adds in group order
+    gdone(grp);
+    if (lane == 0) ws.group_done[grp] = 0u;
+  }
+}
+
+// Lane r of a short tile sums row r's staged products smem[rb - seg_b, re - seg_b) with four
+// interleaved accumulators and runs its epilogue (rows marked long in lm are skipped).
+template <typename PT, typename Epi>
+__device__ __forceinline__ void tile_rows(const PT *smem, int row0, int nr, int rb, int re,
+                                          int seg_b, uint32_t lm, Epi &epi) {
+  const int lane = threadIdx.x & 31;
+  if (lane < nr && !((lm >> lane) & 1u)) {
+    PT s0 = PT(0), s1 = PT(0), s2 = PT(0), s3 = PT(0);
+    int p = rb - seg_b;
+    const int pe = re - seg_b;
+    for (; p + 4 <= pe; p += 4) {
+      s0 += smem[p];
+      s1 += smem[p + 1];
+      s2 += smem[p + 2];
+      s3 += smem[p + 3];
+    }
+    if (p < pe) s0 += smem[p];
+    if (p + 1 < pe) s1 += smem[p + 1];
+    if (p + 2 < pe) s2 += smem[p + 2];
+    epi(row0 + lane, (s0 + s1) + (s2 + s3), false);
+  }
+}
+
 template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone>
 __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals<VT> vals,
                                            const Src &src, PT *smem, const WalkScratch ws,
@@ -345,56 +426,7 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
   const int total = lay.total_items();
   for (int item = gwarp; item < total; item += nwarps) {
     if (item < lay.n_chunks) {
-      const int li = lay.chunk_row[item];
-      const int c0 = lay.chunk_ptr[li];
-      const int re = lay.end_l[li];
-      const int cb = lay.beg_l[li] + (item - c0) * kChunk;   // 4-aligned
-      const int ce = min(cb + kChunk, re);
-      // lane reads entries [p0, p0 + 8): two 16-byte index loads, 16 or 32 bytes of values
-      const int p0 = cb + 8 * lane;
-      PT s = PT(0);
-      if (p0 < ce) {
-        int j[8];
-        Vec4<VT> va, vb;
-        load_idx4(lay.idx_l + p0, j);
-        load_idx4(lay.idx_l + p0 + 4, j + 4);
-        va.load(vals.l + p0);
-        vb.load(vals.l + p0 + 4);
-        PT x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = (p0 + u < ce) ? PT(src(j[u])) : PT(0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) s += PT(va.v[u]) * x[u];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) s += PT(vb.v[u]) * x[4 + u];
-      }
-      s = warp_sum(s);
-      const int grp = li / kTileRows;
-      const int g0 = grp * kTileRows;
-      const int g1 = min(g0 + kTileRows, lay.n_long);
-      int fin = 0;
-      if (lane == 0) {
-        ws.chunk_part[item] = (double)s;
-        __threadfence();
-        const unsigned int need = (unsigned int)(lay.chunk_ptr[g1] - lay.chunk_ptr[g0]);
-        const unsigned int old = atomicAdd(ws.group_done + grp, 1u);
-        fin = (old == need - 1) ? 1 : 0;
-      }
-      fin = __shfl_sync(0xffffffffu, fin, 0);
-      if (fin) {
-        __threadfence();
-        const int lr = g0 + lane;
-        if (lr < g1) {
-          PT d = PT(0);
-          for (int c = lay.chunk_ptr[lr]; c < lay.chunk_ptr[lr + 1]; ++c)
-            d += PT(__ldcg(ws.chunk_part + c));
-          epi(lay.long_rows[lr], d, true);
-        }
-        // the finishing warp varies from run to run: the group's reduction contributions go
-        // to the group's own slots, which the last CTA adds in group order
-        gdone(grp);
-        if (lane == 0) ws.group_done[grp] = 0u;
-      }
+      walk_chunk<VT, PT>(lay, vals, src, ws, epi, gdone, item);
     } else {
       const int st = item - lay.n_chunks;
       const int row0 = st * kTileRows;
@@ -405,28 +437,29 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
       int re = __shfl_down_sync(0xffffffffu, rb, 1);
       if (lane >= nr - 1) re = seg_e;
       const int nvec = (seg_e - seg_b + 3) >> 2;             // groups of 4 entries
-      // stage: lane handles groups g = lane, lane + 32, ... (kStageUnroll at a time)
-      for (int g0 = 0; g0 < nvec; g0 += kWarp * kStageUnroll) {
-        int j[kStageUnroll][4];
-        Vec4<VT> vv[kStageUnroll];
+      // stage: lane handles groups g = lane, lane + 32, ... (kU at a time)
+      constexpr int kU = kStageUnroll;
+      for (int g0 = 0; g0 < nvec; g0 += kWarp * kU) {
+        int j[kU][4];
+        Vec4<VT> vv[kU];
 #pragma unroll
-        for (int u = 0; u < kStageUnroll; ++u) {
+        for (int u = 0; u < kU; ++u) {
           const int g = g0 + u * kWarp + lane;
           if (g < nvec) {
             load_idx4(lay.idx_s + seg_b + 4 * g, j[u]);
             vv[u].load(vals.s + seg_b + 4 * g);
           }
         }
-        PT x[kStageUnroll][4];
+        PT x[kU][4];
 #pragma unroll
-        for (int u = 0; u < kStageUnroll; ++u) {
+        for (int u = 0; u < kU; ++u) {
           const int g = g0 + u * kWarp + lane;
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             x[u][e] = (g < nvec && seg_b + 4 * g + e < seg_e) ? PT(src(j[u][e])) : PT(0);
         }
 #pragma unroll
-        for (int u = 0; u < kStageUnroll; ++u) {
+        for (int u = 0; u < kU; ++u) {
           const int g = g0 + u * kWarp + lane;
           if (g < nvec) {
 #pragma unroll
@@ -435,22 +468,7 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
         }
       }
       __syncwarp();
-      const uint32_t lm = lay.long_mask[st];
-      if (lane < nr && !((lm >> lane) & 1u)) {
-        PT s0 = PT(0), s1 = PT(0), s2 = PT(0), s3 = PT(0);
-        int p = rb - seg_b;
-        const int pe = re - seg_b;
-        for (; p + 4 <= pe; p += 4) {
-          s0 += smem[p];
-          s1 += smem[p + 1];
-          s2 += smem[p + 2];
-          s3 += smem[p + 3];
-        }
-        if (p < pe) s0 += smem[p];
-        if (p + 1 < pe) s1 += smem[p + 1];
-        if (p + 2 < pe) s2 += smem[p + 2];
-        epi(row0 + lane, (s0 + s1) + (s2 + s3), false);
-      }
+      tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lay.long_mask[st], epi);
       __syncwarp();
     }
   }
