@@ -4,7 +4,8 @@
         [--algorithm 0|1] [--max-iters N] [--scale S] [--repeat R]
 
 Workloads (all from lpgen, seeded): c1 = 200 x 500 planted standard form; c2 = 100k x 250k
-general form with power-law columns (--scale shrinks it); c4p = 50k x 100k primal-infeasible
+general form with power-law columns (--scale shrinks it); c3 = multicommodity flow, 20
+commodities on 250k nodes / 2M arcs (120M nonzeros; --scale shrinks the graph); c4p = 50k x 100k primal-infeasible
 LP with a planted Farkas vector; c4d = its dual twin (100k inequality rows over 50k free
 variables, unbounded along the planted vector); c4s = a 50k x 100k standard-form LP unbounded
 along a sparse planted ray.  Prints one JSON line per solve.
@@ -22,6 +23,9 @@ def make(workload: str, scale: float):
         return lpgen.make_c1(0)
     if workload == "c2":
         return lpgen.make_c2(1, scale=scale)
+    if workload == "c3":
+        return lpgen.make_multicommodity_flow(2, max(10, int(250_000 * scale)),
+                                              max(20, int(2_000_000 * scale)))
     if workload == "c4p":
         return lpgen.make_primal_infeasible(3, int(50_000 * scale), int(100_000 * scale))
     if workload == "c4d":
@@ -42,6 +46,7 @@ def main(argv=None):
     ap.add_argument("--max-epoch-len", type=int, default=1000)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--profile", type=int, default=0)
+    ap.add_argument("--time-limit", type=float, default=3600.0)
     a = ap.parse_args(argv)
     from . import rhpdhg
     rhpdhg.load()
@@ -50,7 +55,7 @@ def main(argv=None):
         t0 = time.perf_counter()
         with rhpdhg.Solver(lp, algorithm=a.algorithm, precision=a.precision, eps_rel_kkt=a.tol,
                            max_iters=a.max_iters, max_epoch_len=a.max_epoch_len,
-                           profile=a.profile) as s:
+                           profile=a.profile, time_limit_s=a.time_limit) as s:
             t1 = time.perf_counter()
             r = s.run()
             kt = s.kernel_times() if a.profile else None

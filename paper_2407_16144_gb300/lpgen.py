@@ -296,6 +296,75 @@ def make_c2(seed: int = 1, scale: float = 1.0) -> LP:
 
 
 # ---------------------------------------------------------------------------------------------
+# C3: multicommodity flow
+# ---------------------------------------------------------------------------------------------
+
+def make_multicommodity_flow(seed: int = 2, nodes: int = 250_000, arcs: int = 2_000_000,
+                             commodities: int = 20) -> LP:
+    """Multicommodity min-cost flow on a random digraph: a random Hamiltonian cycle (so the
+    graph is strongly connected) plus arcs - nodes uniform arcs u -> v, u != v.  Variables
+    f_{k,a} >= 0 (column k * arcs + a).  Rows: flow conservation N f_k = s_k for every commodity
+    and node (equality, row k * nodes + v, +1 on arcs leaving v and -1 on arcs entering it), then
+    one shared capacity row per arc, -sum_k f_{k,a} >= -cap_a.  Arc costs U[1, 100] are shared by
+    the commodities, capacities U[5, 50].  The supplies come from a planted flow
+    f*_{k,a} ~ U(0, cap_a / commodities), so the LP is feasible; its optimum is not planted.
+    Every coefficient is +-1 (exact in any floating type)."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(nodes)
+    tail = np.empty(arcs, dtype=np.int64)
+    head = np.empty(arcs, dtype=np.int64)
+    tail[:nodes] = perm
+    head[:nodes] = np.roll(perm, -1)
+    extra = arcs - nodes
+    u = rng.integers(0, nodes, size=extra)
+    v = rng.integers(0, nodes - 1, size=extra)
+    v = v + (v >= u)                                   # uniform over v != u
+    tail[nodes:] = u
+    head[nodes:] = v
+    cost = rng.uniform(1.0, 100.0, size=arcs)
+    cap = rng.uniform(5.0, 50.0, size=arcs)
+    # one commodity's node-arc incidence in CSR (rows = nodes, sorted columns)
+    rows1 = np.concatenate([tail, head])
+    cols1 = np.concatenate([np.arange(arcs), np.arange(arcs)])
+    vals1 = np.concatenate([np.ones(arcs), -np.ones(arcs)])
+    order = np.lexsort((cols1, rows1))
+    rows1, cols1, vals1 = rows1[order], cols1[order], vals1[order]
+    ptr1 = np.zeros(nodes + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows1, minlength=nodes), out=ptr1[1:])
+    del rows1, order
+    nnz1 = 2 * arcs
+    K = commodities
+    m_eq, m_ineq, n = K * nodes, arcs, K * arcs
+    nnz = K * nnz1 + K * arcs
+    row_ptr = np.empty(m_eq + m_ineq + 1, dtype=np.int64)
+    col_idx = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    for k in range(K):
+        row_ptr[k * nodes:(k + 1) * nodes] = ptr1[:-1] + k * nnz1
+        col_idx[k * nnz1:(k + 1) * nnz1] = cols1 + k * arcs
+        val[k * nnz1:(k + 1) * nnz1] = vals1
+    base = K * nnz1
+    row_ptr[m_eq:m_eq + m_ineq] = base + K * np.arange(arcs, dtype=np.int64)
+    row_ptr[-1] = nnz
+    cap_cols = (np.arange(K, dtype=np.int64)[None, :] * arcs + np.arange(arcs)[:, None])
+    col_idx[base:] = cap_cols.reshape(-1)
+    val[base:] = -1.0
+    del cap_cols
+    # planted feasible flow and the supplies it implies
+    f_star = rng.uniform(0.0, 1.0, size=(K, arcs)) * (cap / K)[None, :]
+    supply = np.zeros((K, nodes))
+    for k in range(K):
+        supply[k] = (np.bincount(tail, weights=f_star[k], minlength=nodes) -
+                     np.bincount(head, weights=f_star[k], minlength=nodes))
+    q = np.concatenate([supply.reshape(-1), -cap])
+    c = np.tile(cost, K)
+    return LP(m_eq=m_eq, m_ineq=m_ineq, n=n, row_ptr=row_ptr, col_idx=col_idx, val=val, c=c,
+              q=q, l=np.zeros(n), u=np.full(n, INF),
+              name=f"multicommodity_{commodities}x{nodes}n{arcs}a_s{seed}",
+              x_star=f_star.reshape(-1))
+
+
+# ---------------------------------------------------------------------------------------------
 # C4: infeasible LPs with planted certificates
 # ---------------------------------------------------------------------------------------------
 

@@ -121,6 +121,24 @@ def test_dual_infeasible_twin():
     assert (G @ y_bar - lp.q).min() > 0.0
 
 
+def test_multicommodity_flow_structure():
+    """Node-arc incidence per commodity plus shared capacity rows; the planted flow is feasible
+    and every column holds exactly +1 (tail), -1 (head) and -1 (capacity)."""
+    nodes, arcs, K = 300, 2000, 4
+    lp = lpgen.make_multicommodity_flow(5, nodes, arcs, K)
+    assert (lp.m_eq, lp.m_ineq, lp.n, lp.nnz) == (K * nodes, arcs, K * arcs, 3 * K * arcs)
+    A = _K(lp).tocsc()
+    cnt = np.diff(A.indptr)
+    assert (cnt == 3).all()
+    assert sorted(A.data.reshape(-1, 3)[:, :].sum(axis=1).tolist()) == [-1.0] * (K * arcs)
+    for r in range(lp.m):
+        seg = lp.col_idx[lp.row_ptr[r]:lp.row_ptr[r + 1]]
+        assert (np.diff(seg) > 0).all()
+    r = _K(lp) @ lp.x_star - lp.q
+    assert np.abs(r[:lp.m_eq]).max() < 1e-9 and r[lp.m_eq:].min() >= 0.0
+    assert (lp.x_star >= 0).all()
+
+
 def test_tiny_and_box_generators():
     for s in range(5):
         lp = lpgen.make_tiny_standard(s)
