@@ -302,7 +302,8 @@ def make_c2(seed: int = 1, scale: float = 1.0) -> LP:
 def make_multicommodity_flow(seed: int = 2, nodes: int = 250_000, arcs: int = 2_000_000,
                              commodities: int = 20) -> LP:
     """Multicommodity min-cost flow on a random digraph: a random Hamiltonian cycle (so the
-    graph is strongly connected) plus arcs - nodes uniform arcs u -> v, u != v.  Variables
+    graph is strongly connected) plus arcs - nodes uniform arcs u -> v, u != v, numbered in
+    forward-star order (sorted by tail node, then head node).  Variables
     f_{k,a} >= 0 (column k * arcs + a).  Rows: flow conservation N f_k = s_k for every commodity
     and node (equality, row k * nodes + v, +1 on arcs leaving v and -1 on arcs entering it), then
     one shared capacity row per arc, -sum_k f_{k,a} >= -cap_a.  Arc costs U[1, 100] are shared by
@@ -321,6 +322,9 @@ def make_multicommodity_flow(seed: int = 2, nodes: int = 250_000, arcs: int = 2_
     v = v + (v >= u)                                   # uniform over v != u
     tail[nodes:] = u
     head[nodes:] = v
+    # arcs numbered in forward-star order (by tail, then head), as a graph file lists them
+    order = np.lexsort((head, tail))
+    tail, head = tail[order], head[order]
     cost = rng.uniform(1.0, 100.0, size=arcs)
     cap = rng.uniform(5.0, 50.0, size=arcs)
     # one commodity's node-arc incidence in CSR (rows = nodes, sorted columns)
