@@ -47,11 +47,34 @@ def parse():
                     help="headline precision: 1 = FP32 iterates / FP64 restarts, 0 = FP64")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 120M-nonzero multicommodity-flow section")
     ap.add_argument("--serve-requests", type=int, default=40,
                     help="requests of the 50/s Poisson stream replayed through the serving loop "
                          "(0 = skip)")
     ap.add_argument("--serve-max-iters", type=int, default=10_000)
     return ap.parse_args()
+
+
+# DRAM bytes (read + write) per launch of the mixed-precision ordinary-iteration kernels on the
+# 100k x 250k LP, from one ncu capture (profiles/k_iter_mx_c2.md) of the kernel sources with
+# this digest.  Reported as roofline.traffic only while those sources are unchanged.
+KERNEL_SOURCES = ["paper_2407_16144_gb300/csrc/iterate_mx.cu", "paper_2407_16144_gb300/csrc/common.cuh",
+                  "paper_2407_16144_gb300/csrc/iter_common.cuh", "paper_2407_16144_gb300/csrc/internal.h"]
+PROFILED_TRAFFIC = {
+    "digest": "17ec2e71864b7d3a",
+    "column kernel (K^T y~ + primal step)": 27852288,
+    "row kernel (K x~ + dual step)": 23749632,
+}
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def load_peaks():
@@ -219,6 +242,40 @@ def run_serving(args, rhpdhg, lpgen):
                                  "p99_latency_s": float(np.percentile(lat_b, 99)),
                                  "sgm10_latency_s": sgm10(list(lat_b)), "solved": int(solved_b)},
     }
+
+
+def run_large(args, rhpdhg, lpgen, peak, peak_kind):
+    """The 120M-nonzero multicommodity-flow LP to 1e-4, both precisions, plus one profiled
+    mixed-precision solve for the per-kernel roofline."""
+    lp = lpgen.make_multicommodity_flow()
+    out = {"workload": "multicommodity flow: 20 commodities on 250k nodes / 2M arcs "
+                       "(7M rows, 40M columns, 120M nonzeros), arc costs U[1,100], "
+                       "capacities U[5,50], planted feasible flow (seed 2)",
+           "tol": 1e-4}
+    for prec, name in ((1, "fp32 iterates, fp64 restarts"), (0, "fp64")):
+        t0 = time.perf_counter()
+        s = rhpdhg.Solver(lp, algorithm=args.algorithm, precision=prec, eps_rel_kkt=1e-4,
+                          time_limit_s=300.0)
+        t1 = time.perf_counter()
+        r = s.run()
+        s.close()
+        out[name] = {"status": r.status_name, "iters": r.iters, "solve_s": r.solve_seconds,
+                     "create_s": t1 - t0, "iters_per_s": r.iters / r.solve_seconds,
+                     "rel_kkt": r.rel_kkt, "primal_obj": r.primal_obj}
+    s = rhpdhg.Solver(lp, algorithm=args.algorithm, precision=1, eps_rel_kkt=1e-4, profile=1)
+    s.run()
+    kt = s.kernel_times()
+    s.close()
+    ach_c = kt["bytes_col"] / (kt["ms_col"] / 1000.0) / 1e9
+    ach_r = kt["bytes_row"] / (kt["ms_row"] / 1000.0) / 1e9
+    out["roofline"] = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
+                       "column_kernel": {"achieved": ach_c, "frac": ach_c / peak,
+                                         "ms_per_launch": kt["ms_col"],
+                                         "bytes_per_launch": kt["bytes_col"]},
+                       "row_kernel": {"achieved": ach_r, "frac": ach_r / peak,
+                                      "ms_per_launch": kt["ms_row"],
+                                      "bytes_per_launch": kt["bytes_row"]}}
+    return out
 
 
 def run_reference(args):
@@ -401,7 +458,9 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * (lp.n + lp.m)},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (PROFILED_TRAFFIC.get(dom) if args.precision == 1 and
+                                 kernel_digest() == PROFILED_TRAFFIC["digest"] else None),
                      "ms_per_launch_row": kt["ms_row"], "ms_per_launch_col": kt["ms_col"],
                      "bytes_per_launch_row": kt["bytes_row"],
                      "bytes_per_launch_col": kt["bytes_col"],
@@ -410,6 +469,8 @@ def run_ours(args):
     }
     if world == 1 and args.serve_requests > 0:
         line["serving"] = run_serving(args, rhpdhg, lpgen)
+    if world == 1 and not args.no_large:
+        line["large_lp"] = run_large(args, rhpdhg, lpgen, peak, f"{peak_kind} hbm_gbs")
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_oracle_sample(lp, args.algorithm, args.tol, iters)
         line["cpu_baseline"] = {
