@@ -161,6 +161,11 @@ typedef struct {
   double  omega;                /* primal weight in force at iteration t                      */
   int32_t restart;              /* 1 if z^{n+1,0} = T(z^{n,k}) follows                         */
   int32_t pad;
+  int64_t active;               /* check iterations: columns with x~ on a bound (the active
+                                   set of Section 4's partition as the iterates see it); else -1 */
+  int64_t changed;              /* check iterations: columns whose on-bound status changed since
+                                   the previous recorded check; else -1 (also -1 for checks run
+                                   by the mixed-precision restart kernels)                     */
 } rhpdhg_trace_rec;
 
 /* Fills *p with the defaults listed above.  Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG if

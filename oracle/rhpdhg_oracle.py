@@ -288,6 +288,7 @@ class OracleResult:
     solve_seconds: float
     trace: list
     snapshots: dict
+    telemetry: list = dataclasses.field(default_factory=list)
 
 
 def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
@@ -341,6 +342,8 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
     kkt = None
     cert_x = cert_y = None
     cert_source = CERT_NONE
+    telemetry = []
+    at_prev = np.zeros(n, dtype=bool)
     t = 0
     while True:
         xt, yt = pdhg_T(Kh, KhT, c, q, l, u, m_eq, tau, sigma, x, y)
@@ -365,6 +368,13 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
             if st != RUNNING:
                 status, cert_x, cert_y = st, cx, cy
                 cert_source = CERT_RESTART_POINT if (k == 0 and n_ep >= 1) else CERT_CHECK
+        if is_check:
+            # active-set telemetry: columns whose PDHG point sits on a bound (the active set of
+            # the partition of Section 4 as the iterates see it), and how many changed since
+            # the previous check
+            at = (xt == l) | (xt == u)
+            telemetry.append((t, int(at.sum()), int((at != at_prev).sum())))
+            at_prev = at
         if status == RUNNING and is_check:
             kkt = rel_kkt(lp, K, E * xt, D * yt)
             if kkt["rel_kkt"] <= params.eps_rel_kkt:
@@ -424,6 +434,7 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
                         rel_d=kkt["rel_d"], rel_gap=kkt["rel_gap"],
                         primal_obj=kkt["primal_obj"], dual_obj=kkt["dual_obj"], x=E * xt,
                         y=D * yt, cert_x=cert_x, cert_y=cert_y, cert_source=cert_source,
+                        telemetry=telemetry,
                         eta=eta, omega=omega,
                         sigma_max=sigma_max, D=D, E=E,
                         solve_seconds=time.perf_counter() - t_start, trace=tr,

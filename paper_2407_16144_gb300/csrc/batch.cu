@@ -287,10 +287,12 @@ __device__ void batch_col_pass(const BatchDesc &d, const IterConsts &ic, int pha
   StepFlags fl{restart, ctl->w, ctl->tau, check, cert, rp, move, stash, ic.m_eq};
   ColAcc a;
   a.zero();
-  auto fn = [&](int j, double dot) { col_epilogue<RHO2>(j, dot, d.cv_, fl, a, a); };
+  Tel tl;
+  auto fn = [&](int j, double dot) { col_epilogue<RHO2>(j, dot, d.cv_, fl, a, a, tl); };
   const double *yt = d.rv_.yt;
   auto gs = [&](int i) { return yt[i]; };
   rows_apply(d.n, d.cp, d.ri, d.cv, d.gc, gs, fn);
+  if (check) tel_flush(ctl, tl);
   double r[19];
   block_reduce(a, r, sh, col_smask(check, cert, move), col_mmask(cert, move));
   if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, cert, rp, move, phase);
@@ -411,7 +413,7 @@ size_t slot_bytes(int m, int n, long long nnz) {
   b += align256((m + 1) * sizeof(int)) + align256(nnz * sizeof(int)) + align256(nnz * 8);
   b += align256((n + 1) * sizeof(int)) + align256(nnz * sizeof(int)) + align256(nnz * 8);
   b += 15 * align256((size_t)std::max(n, 1) * 8) + 13 * align256((size_t)std::max(m, 1) * 8);
-  b += align256(sizeof(rh::IterConsts)) + align256(16);
+  b += align256(sizeof(rh::IterConsts)) + align256(16) + align256((size_t)std::max(n, 1));
   return b;
 }
 
@@ -584,6 +586,7 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
          *certx = (double *)take(nb), *c = (double *)take(nb), *l = (double *)take(nb),
          *u = (double *)take(nb), *E = (double *)take(nb), *Einv = (double *)take(nb),
          *tmp_n = (double *)take(nb), *certx2 = (double *)take(nb);
+  unsigned char *act = (unsigned char *)take((size_t)std::max(n, 1));
   double *y = (double *)take(mb), *yt = (double *)take(mb), *y0 = (double *)take(mb),
          *kx = (double *)take(mb), *kxt = (double *)take(mb), *kx0 = (double *)take(mb),
          *certy = (double *)take(mb), *q = (double *)take(mb), *D = (double *)take(mb),
@@ -594,7 +597,7 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   d.tmp_m = tmp_m;
   d.tmp_n = tmp_n;
   d.rv_ = rh::RowVecs{y, yt, y0, kx, kxt, kx0, certy, q, D, Dinv, certy2};
-  d.cv_ = rh::ColVecs{x, xt, x0, kty, kty0, xout, certx, c, l, u, E, Einv, certx2};
+  d.cv_ = rh::ColVecs{x, xt, x0, kty, kty0, xout, certx, c, l, u, E, Einv, certx2, act};
   d.ctl = ctl;
   d.ic = ic;
   d.setup_out = setup_out;
@@ -614,6 +617,7 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   cudaMemsetAsync(certx, 0, nb, st);
   cudaMemsetAsync(certy, 0, mb, st);
   cudaMemsetAsync(certx2, 0, nb, st);
+  cudaMemsetAsync(act, 0, (size_t)std::max(n, 1), st);
   cudaMemsetAsync(certy2, 0, mb, st);
   rh::Ctl c0{};
   c0.status = rh::kRunning;

@@ -50,6 +50,7 @@ struct rhpdhg_handle {
   double *y = nullptr, *yt = nullptr, *y0 = nullptr, *kx = nullptr, *kxt = nullptr,
          *kx0 = nullptr, *certy = nullptr, *certy2 = nullptr;
   double *x_init = nullptr, *y_init = nullptr, *xres = nullptr, *yres = nullptr;
+  unsigned char *act = nullptr;   // on-bound flags of the previous check (telemetry)
   // mixed precision: FP32 offsets and anchor images
   bool mixed = false;
   float *dxt = nullptr, *dx = nullptr, *ktdy = nullptr, *s0 = nullptr, *xlo = nullptr,
@@ -126,6 +127,7 @@ void destroy(rhpdhg_handle *h) {
   float *fbufs[] = {h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi,
                     h->dyt, h->kdxt, h->dy, h->kdx, h->r0, h->ylo};
   for (float *b : fbufs) cudaFree(b);
+  cudaFree(h->act);
   cudaFree(h->ctl);
   cudaFree(h->trace);
   if (h->h_mirror) cudaFreeHost(h->h_mirror);
@@ -209,6 +211,7 @@ int reset_state(rhpdhg_handle *h) {
   c.sigma = h->eta * h->omega0;
   c.eta = h->eta;
   CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemsetAsync(h->act, 0, (size_t)std::max(h->n, 1), h->st));
   if (h->mixed) {
     // anchors z^{0,0}, zero offsets; the set-up column kernel runs in restart mode and forms
     // K^T y0, the anchor images and dxt_0; the first row kernel forms K x0 likewise
@@ -689,6 +692,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     CKC(dalloc(&h->dxt64, n));
     CKC(dalloc(&h->dyt64, m));
   }
+  CKC(dalloc(&h->act, n));
   CKC(cudaMemsetAsync(h->certx, 0, n * sizeof(double), st));
   CKC(cudaMemsetAsync(h->certx2, 0, n * sizeof(double), st));
   if (m) CKC(cudaMemsetAsync(h->certy, 0, m * sizeof(double), st));
@@ -740,11 +744,11 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv,
                   h->certy2};
   h->cv = ColVecs{h->x, h->xt, h->x0, h->kty, h->kty0, h->xout, h->certx, h->c, h->l, h->u,
-                  h->E, h->Einv, h->certx2};
+                  h->E, h->Einv, h->certx2, h->act};
   h->rvm = RowVecsMx{h->dyt, h->kdxt, h->dy, h->kdx, h->r0, h->ylo, h->y0, h->kx0, h->certy,
                      h->dyt64, h->q, h->D, h->Dinv, h->certy2};
   h->cvm = ColVecsMx{h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi, h->x0, h->kty0, h->xout,
-                     h->certx, h->dxt64, h->c, h->l, h->u, h->E, h->Einv, h->certx2};
+                     h->certx, h->dxt64, h->c, h->l, h->u, h->E, h->Einv, h->certx2, h->act};
   algorithmic_bytes(h);
   h->launches = launches_so_far() - launches0;
   CKC(cudaStreamSynchronize(st));

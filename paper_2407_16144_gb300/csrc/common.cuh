@@ -111,6 +111,10 @@ struct Ctl {
   double mv_cd, mv_u, mv_l, mv_dlb, mv_dub, mv_au, mv_al;
   int mv_ready;
   int cert_src;          // candidate that certified infeasibility (kCert*)
+  // active-set telemetry of check iterations: columns with x~ on a bound, and columns whose
+  // on-bound status changed since the previous check (integer atomics, reset by col_finalize)
+  unsigned long long tel_act, tel_chg;
+  long long act_last, chg_last;
   unsigned int cnt_row, cnt_col;   // last-CTA tickets
   int stage;             // 0: the row stage of iteration t is next; 1: the column stage is next
                          // (each finalisation advances it, so of two kernels launched for the
@@ -121,6 +125,7 @@ struct TraceRec {      // mirrors rhpdhg_trace_rec
   long long t, epoch, k;
   double fpr_sq, omega;
   int restart, pad;
+  long long active, changed;   // check iterations: active-set telemetry, else -1
 };
 
 // Per-solve constants passed by value to the iteration kernels.

@@ -40,6 +40,7 @@ struct ColVecs {      // n-vectors used by the column kernel (K^T y~ and the pri
   double *x, *xt, *x0, *kty, *kty0, *xout, *certx;
   const double *c, *l, *u, *e, *einv;
   double *certx2;     // x-part of the anchor-movement candidate
+  unsigned char *act; // 1 where x~ was on a bound at the previous check
 };
 
 struct RowVecsMx {    // mixed precision, m-vectors (offsets from the FP64 anchor y0)
@@ -54,6 +55,7 @@ struct ColVecsMx {    // mixed precision, n-vectors (offsets from the FP64 ancho
   double *x0, *kty0, *xout, *certx, *dxt64;
   const double *c, *l, *u, *e, *einv;
   double *certx2;
+  unsigned char *act;
 };
 
 // Message for rhpdhg_last_error(NULL) (calls without a handle).

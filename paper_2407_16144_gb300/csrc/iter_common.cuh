@@ -88,6 +88,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
     TraceRec tr;
     tr.t = t; tr.epoch = n_ep; tr.k = k; tr.fpr_sq = fpr2; tr.omega = omega;
     tr.restart = rs ? 1 : 0; tr.pad = 0;
+    tr.active = -1; tr.changed = -1;
     ic.trace[t] = tr;
   }
   ctl->fpr0_sq = fpr0;
@@ -128,7 +129,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
 // of the anchor-movement candidate are staged for the next row kernel.
 __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, const double *r,
                                              long long t, bool check, bool cert, bool rp,
-                                             bool move, int phase) {
+                                             bool move, int phase, bool tel = true) {
   ctl->dx_sq = r[0];
   ctl->xa_sq = r[1];
   int st = kRunning;
@@ -155,6 +156,19 @@ __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, con
     ctl->mv_au = r[17];
     ctl->mv_al = r[18];
     ctl->mv_ready = 1;
+  }
+  if (check) {
+    // active-set telemetry (the partition of Section 4 as the iterates see it)
+    const unsigned long long ua = atomicExch(&ctl->tel_act, 0ull);
+    const unsigned long long uc = atomicExch(&ctl->tel_chg, 0ull);
+    const long long na = tel ? (long long)ua : -1;
+    const long long nc = tel ? (long long)uc : -1;
+    ctl->act_last = na;
+    ctl->chg_last = nc;
+    if (ic.trace && t < ic.trace_cap) {
+      ic.trace[t].active = na;
+      ic.trace[t].changed = nc;
+    }
   }
   if (st == kRunning && check) {
     const double rel_p = sqrt(ctl->rp_sq) / ic.qn1;
@@ -288,13 +302,42 @@ __device__ __forceinline__ void col_cert_parts(int j, double d, double kv, const
 // (z_t is the anchor at a restart point, else the stored x_t, K^T y_t), then the blend to
 // x_{t+1} (at a restart with move set, first the anchor-movement parts against the old
 // anchor) and the primal step x~_{t+1} = proj_X(x_{t+1} - tau (c - K^T y_{t+1})).
+// Per-thread active-set counts of a check iteration (see tel_flush).
+struct Tel {
+  int act = 0, chg = 0;
+};
+
+// Column j's on-bound status at a check: counts it and records it for the next check.
+__device__ __forceinline__ void tel_column(int j, bool at, unsigned char *act, Tel &tl) {
+  const unsigned char prev = act[j];
+  tl.act += at ? 1 : 0;
+  tl.chg += (at ? 1 : 0) != prev ? 1 : 0;
+  act[j] = at ? 1 : 0;
+}
+
+// Adds the CTA's telemetry counts to the control block (integer atomics: exact and
+// order-independent); called by every thread before the CTA's reduction and ticket.
+__device__ __forceinline__ void tel_flush(Ctl *ctl, const Tel &tl) {
+  int a = tl.act, c = tl.chg;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (a | c)) {
+    atomicAdd(&ctl->tel_act, (unsigned long long)a);
+    atomicAdd(&ctl->tel_chg, (unsigned long long)c);
+  }
+}
+
 template <int RHO2, class AS, class AM>
 __device__ __forceinline__ void col_epilogue(int j, double dot, const ColVecs &v,
-                                             const StepFlags &f, AS &S, AM &M) {
+                                             const StepFlags &f, AS &S, AM &M, Tel &tl) {
   const double xtj = v.xt[j];
   const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
   const double w = f.w, tau = f.step;
   if (f.check) {
+    tel_column(j, xtj == lj || xtj == uj, v.act, tl);
     const double g = cj - dot;
     const double lam = proj_lambda(g, lj, uj);
     const double rd = (g - lam) * v.einv[j];

@@ -84,15 +84,17 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   double *my = smem + (threadIdx.x >> 5) * lay.seg;
 
   StepFlags fl{restart, w, tau, check, cert, rp, move, stash, ic.m_eq};
+  Tel tl;
   auto epi = [&](int j, double dot, bool lg) {
-    if (lg) col_epilogue<RHO2>(j, dot, v, fl, al, a);
-    else col_epilogue<RHO2>(j, dot, v, fl, a, a);
+    if (lg) col_epilogue<RHO2>(j, dot, v, fl, al, a, tl);
+    else col_epilogue<RHO2>(j, dot, v, fl, a, a, tl);
   };
   const unsigned smask = col_smask(check, cert, move);
   const unsigned mmask = col_mmask(cert, move);
   auto gdone = [&](int grp) { store_group(al, smask, ws.group_part, grp); };
   auto gather = [&](int j) { return ytv[j]; };
   walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
+  if (check) tel_flush(ctl, tl);
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[19];

@@ -224,6 +224,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   a.zero();
   al.zero();
   F3 fa, fl;
+  Tel tl;         // active-set telemetry (ordinary check iterations)
   const unsigned smask = col_smask(check, rp, move);
   const unsigned mmask = col_mmask(rp, move);
 
@@ -320,6 +321,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     auto body = [&](int j, float ktdyt, auto &A, F3 &F) {
       const float dxtj = v.dxt[j];
       if (check) {
+        tel_column(j, dxtj == v.xlo[j] || dxtj == v.xhi[j], v.act, tl);
         const double x0j = v.x0[j];
         checks(j, x0j, (double)dxtj, v.kty0[j] + (double)ktdyt, (double)ktdyt, A);
       }
@@ -345,6 +347,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     };
     auto gB = [&](int i) { return dyt[i]; };
     walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone);
+    if (check) tel_flush(ctl, tl);
   }
   unsigned prewarp = 0u;
   if (!restart) {       // MODE 0, and the restart-point iterations of MODE 1, sum in FP32
@@ -357,7 +360,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   if (cta_reduce_and_ticket(a, smask, mmask, prewarp, part, &ctl->cnt_col)) {
     double r[19];
     grid_finish<11, 8>(part, r, smask, mmask, (restart ? wa : wb).group_part, lay.n_long_tiles);
-    if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, rp, move, phase);
+    if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, rp, move, phase, MODE == 0);
   }
 }
 

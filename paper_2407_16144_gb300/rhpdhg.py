@@ -67,7 +67,7 @@ class rhpdhg_result(C.Structure):
 class rhpdhg_trace_rec(C.Structure):
     _fields_ = [("t", C.c_int64), ("epoch", C.c_int64), ("k", C.c_int64),
                 ("fpr_sq", C.c_double), ("omega", C.c_double), ("restart", C.c_int32),
-                ("pad", C.c_int32)]
+                ("pad", C.c_int32), ("active", C.c_int64), ("changed", C.c_int64)]
 
 
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
@@ -645,7 +645,8 @@ class Solver:
     def trace(self, capacity: int = 1 << 16):
         rc, recs = rhpdhg_get_trace(self.h, capacity)
         _check(rc, self.h, "rhpdhg_get_trace")
-        return [(r.t, r.epoch, r.k, r.fpr_sq, bool(r.restart), r.omega) for r in recs]
+        return [(r.t, r.epoch, r.k, r.fpr_sq, bool(r.restart), r.omega, r.active, r.changed)
+                for r in recs]
 
     def kernel_times(self):
         rc, d = rhpdhg_kernel_times(self.h)

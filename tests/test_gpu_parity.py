@@ -44,7 +44,8 @@ def rel(a, b):
 def first_tie(trace, beta=math.exp(-1.0)):
     """Index of the first iteration whose restart test is within TIE of its threshold."""
     fpr0 = None
-    for idx, (t, n, k, f, rs, om) in enumerate(trace):
+    for idx, rec in enumerate(trace):
+        t, n, k, f = rec[:4]
         if k == 0:
             fpr0 = f
         if n >= 1 and fpr0 and abs(f / fpr0 - beta * beta) < TIE:
@@ -96,6 +97,13 @@ def test_iterates_match_oracle_first_200(rh, case, alg, pw):
             assert a[4] == b[4], f"restart flag differs at t={a[0]}"
             assert abs(a[3] - b[3]) <= 1e-10 * max(abs(b[3]), 1e-300)
             assert abs(a[5] - b[5]) <= 1e-10 * b[5]                  # omega
+        # active-set telemetry at the check iterations (on-bound columns, changes)
+        tel = {t: (na, nc) for (t, na, nc) in o.telemetry}
+        for a in tr[:stop]:
+            if a[0] in tel:
+                assert (a[6], a[7]) == tel[a[0]], (a[0], a[6:], tel[a[0]])
+            else:
+                assert (a[6], a[7]) == (-1, -1)
     # PDHG points at the snapshot iterations: rerun with max_iters = t + 1
     for t in SNAP:
         if t >= stop:
@@ -402,6 +410,23 @@ def test_mixed_precision_certificates(rh, alg):
         assert np.array_equal(r2.cert_x, r.cert_x) and np.array_equal(r2.cert_y, r.cert_y)
         _check_certificate(rh, lp, r, kind)
         print(f"mixed {name} alg={alg}: detected at {r.iters} iterations")
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_active_set_identification_on_device(rh, precision):
+    """The device telemetry shows finite-time identification on C1 (Section 4, Stage I): the
+    on-bound count settles on the planted zeros of x* and stops changing."""
+    lp = lpgen.make_c1(0)
+    with rh.Solver(lp, algorithm=1, precision=precision, eps_rel_kkt=1e-8, trace=1,
+                   trace_capacity=1 << 14) as s:
+        r = s.run()
+        tr = s.trace(1 << 14)
+    assert r.status == rh.STATUS_OPTIMAL
+    checks = [(a[6], a[7]) for a in tr if a[6] >= 0]
+    planted = int((lp.x_star == 0).sum())
+    assert checks[-1] == (planted, 0)
+    tol = 0.0 if precision == 0 else 1e-9      # FP32 offsets from an FP64 anchor
+    assert np.array_equal(np.abs(r.x) <= tol, lp.x_star == 0.0)
 
 
 def test_mixed_first_iterations_close_to_fp64(rh):

@@ -402,6 +402,24 @@ def test_each_certificate_candidate_certifies(case):
             assert (-Kd[lp.m_eq:]).max() <= 1e-8 * -cd
 
 
+@pytest.mark.parametrize("case", ["c1", "c2_small"])
+def test_active_set_identification(case):
+    """Stage I of Section 4 (finite-time identification): on these planted LPs with strict
+    complementarity, the set of PDHG-point coordinates on a bound settles on the planted active
+    set and stops changing.  C1: exactly the planted zeros of x*."""
+    lp = lpgen.make_c1(0) if case == "c1" else lpgen.make_c2(1, scale=0.01)
+    r = O.solve(lp, O.OracleParams(algorithm=1, eps_rel_kkt=1e-10, max_iters=200_000))
+    assert r.status == O.OPTIMAL
+    tel = r.telemetry
+    assert tel[0][1] == tel[0][2]                      # first check: all on-bound columns new
+    planted = int(((lp.x_star == lp.l) | (lp.x_star == lp.u)).sum())
+    assert tel[-1][1] == planted
+    half = tel[len(tel) // 2:]
+    assert all(c == 0 for (_, _, c) in half) and all(a == planted for (_, a, _) in half)
+    if case == "c1":
+        assert np.array_equal(r.x == 0.0, lp.x_star == 0.0)
+
+
 def test_iteration_limit_status():
     lp = lpgen.make_c1(0)
     r = O.solve(lp, O.OracleParams(eps_rel_kkt=1e-12, max_iters=100))
