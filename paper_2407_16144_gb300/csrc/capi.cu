@@ -643,29 +643,41 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   }
 
   // ---- power iteration for sigma_max(K^) ----
+  // v <- K^T K^ v / ||K^T K^ v|| from v = 1/sqrt(n); each step is two fused products (the
+  // normalisation rides on the next product's input scale), then sigma = ||K^ v||.
   {
-    double *v = nullptr, *w = nullptr, *um = nullptr;
+    double *v = nullptr, *w = nullptr, *um = nullptr, *pp = nullptr, *ss = nullptr;
+    unsigned int *tk = nullptr;
+    const bool f32 = false;              // FP64 values (the FP32 copy measured no faster)
+    const int gr = side_spmv_pw_grid(h->rows, f32, h->sm_count);
+    const int gc = side_spmv_pw_grid(h->cols, f32, h->sm_count);
+    const int gmax = std::max(gr, gc);
     CKT(dalloc(&v, n));
     CKT(dalloc(&w, n));
     CKT(dalloc(&um, m));
-    CKT(dalloc(&tmp, 1024));
+    CKT(dalloc(&pp, (size_t)gmax * kMaxPartials));
+    CKT(dalloc(&ss, 8));
+    CKT(dalloc(&tk, 1));
+    CKT(cudaMemsetAsync(tk, 0, sizeof(unsigned int), st));
     fill(st, n, 1.0 / std::sqrt((double)n), v);
+    const double *scale = nullptr;       // v is already normalised
     for (int it = 0; it < P.power_iters; ++it) {
-      side_spmv(st, h->rows, v, um, h->grid_row);
-      side_spmv(st, h->cols, um, w, h->grid_col);
-      sumsq(st, n, w, dn + 4, tmp);
-      normalize(st, n, w, dn + 4, v);
+      side_spmv_pw(st, h->rows, f32, v, scale, um, pp, tk, ss + 2, gr);
+      side_spmv_pw(st, h->cols, f32, um, nullptr, w, pp, tk, ss + 4, gc);
+      std::swap(v, w);
+      scale = ss + 5;                    // 1 / ||K^T K^ v||
     }
-    side_spmv(st, h->rows, v, um, h->grid_row);
-    sumsq(st, m, um, dn + 5, tmp);
+    side_spmv_pw(st, h->rows, f32, v, scale, um, pp, tk, ss + 6, gr);
     double s2 = 0;
-    CKT(cudaMemcpyAsync(&s2, dn + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKT(cudaMemcpyAsync(&s2, ss + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     CKT(cudaStreamSynchronize(st));
+    CKT(cudaGetLastError());
     cudaFree(v);
     cudaFree(w);
     cudaFree(um);
-    cudaFree(tmp);
-    tmp = nullptr;
+    cudaFree(pp);
+    cudaFree(ss);
+    cudaFree(tk);
     h->sigma_max = (m > 0 && h->nnz > 0) ? std::sqrt(s2) : 0.0;
   }
   cudaFree(dn);

@@ -84,20 +84,33 @@ __global__ void k_gather_csc(int nnz, const int *perm, const int *rows_of, const
   cval[s] = val[p];
 }
 
-// per row r of a CSR side: OP 0 -> max_p |v_p| rs_r cs_{idx_p};  OP 1 -> sum_p (..)^alpha
-template <int OP>
+// per row r of a CSR side: OP 0 -> max_p |v_p| rs_r cs_{idx_p};  OP 1 -> sum_p (..)^alpha.
+// G consecutive lanes share a row (strided over its entries, then a fixed shuffle tree), so a
+// long power-law row is spread over a lane group instead of running on one thread.
+template <int OP, int G>
 __global__ void k_side_stat(int nrows, const int *ptr, const int *idx, const double *val,
                             const double *rs, const double *cs, double alpha, double *out) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
+  const long long gid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const int sub = threadIdx.x % G;
+  const bool in = gid < nrows;
+  const int r = in ? (int)gid : 0;
   double acc = 0.0;
-  const double sr = rs[r];
-  for (int p = ptr[r]; p < ptr[r + 1]; ++p) {
-    double a = fabs(val[p]) * sr * cs[idx[p]];
-    if (OP == 0) acc = fmax(acc, a);
-    else acc += (alpha == 1.0) ? a : pow(a, alpha);
+  if (in) {
+    const double sr = rs[r];
+    const int pe = ptr[r + 1];
+#pragma unroll 4
+    for (int p = ptr[r] + sub; p < pe; p += G) {
+      const double a = fabs(val[p]) * sr * cs[idx[p]];
+      if (OP == 0) acc = fmax(acc, a);
+      else acc += (alpha == 1.0) ? a : pow(a, alpha);
+    }
   }
-  out[r] = acc;
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, acc, o, G);
+    acc = (OP == 0) ? fmax(acc, t) : acc + t;
+  }
+  if (in && sub == 0) out[r] = acc;
 }
 
 __global__ void k_scale_update(int n, const double *stat, double *scale) {
@@ -195,6 +208,40 @@ k_side_spmv(SideLayout lay, SideVals<double> vals, WalkScratch ws,
   walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
 }
 
+// One product of the power iteration on K^T K^: out = side * (src * in_scale[0]) (in_scale NULL:
+// 1), plus ss[0] = ||out||^2 and ss[1] = 1 / ||out|| (0 for a zero vector) from the grid's
+// deterministic ticket reduction.  The next product reads ss + 1 as its input scale, so the
+// normalisation v = w / ||w|| costs no launch of its own.
+template <typename VT>
+__global__ void __launch_bounds__(kBlockThreads)
+k_side_spmv_pw(SideLayout lay, SideVals<VT> vals, WalkScratch ws,
+               const double *__restrict__ src, const double *in_scale, double *out, double *part,
+               unsigned int *ticket, double *ss) {
+  extern __shared__ double smem[];
+  double *my = smem + (threadIdx.x >> 5) * lay.seg;
+  const double sc = in_scale ? *in_scale : 1.0;
+  Acc<1, 0> a, al;
+  a.zero();
+  al.zero();
+  auto epi = [&](int row, double dot, bool lg) {
+    out[row] = dot;
+    if (lg) al.s[0] += dot * dot;
+    else a.s[0] += dot * dot;
+  };
+  auto gather = [&](int j) { return src[j] * sc; };
+  auto gdone = [&](int grp) { store_group(al, 0x1u, ws.group_part, grp); };
+  walk_tiles<VT, double>(lay, vals, gather, my, ws, epi, gdone);
+  if (cta_reduce_and_ticket(a, 0x1u, 0u, 0u, part, ticket)) {
+    double r[1];
+    grid_finish<1, 0>(part, r, 0x1u, 0u, ws.group_part, lay.n_long_tiles);
+    if (threadIdx.x == 0) {
+      ss[0] = r[0];
+      ss[1] = r[0] > 0.0 ? 1.0 / sqrt(r[0]) : 0.0;
+      *ticket = 0u;
+    }
+  }
+}
+
 }  // namespace
 
 static std::atomic<long long> g_launches{0};
@@ -263,23 +310,55 @@ done:
   return err;
 }
 
+// lanes per row for a side with `nnz` entries over `nrows` rows (the mean row length, rounded
+// up to a power of two, 4 to 32)
+static int stat_group(long long nnz, int nrows) {
+  const double mean = nrows > 0 ? (double)nnz / nrows : 0.0;
+  int g = 4;
+  while (g < 32 && g < mean) g *= 2;
+  return g;
+}
+
+template <int OP>
+static void side_stat(cudaStream_t st, int nrows, long long nnz, const int *ptr, const int *idx,
+                      const double *val, const double *rs, const double *cs, double alpha,
+                      double *out) {
+  const int g = stat_group(nnz, nrows);
+  const long long threads = (long long)nrows * g;
+  const int nb = (int)((threads + 255) / 256);
+  if (nb <= 0) return;
+  switch (g) {
+    case 4: k_side_stat<OP, 4><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rs, cs, alpha, out); break;
+    case 8: k_side_stat<OP, 8><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rs, cs, alpha, out); break;
+    case 16: k_side_stat<OP, 16><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rs, cs, alpha, out); break;
+    default: k_side_stat<OP, 32><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rs, cs, alpha, out); break;
+  }
+}
+
 void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *col,
                      const double *val, const int *cp, const int *ridx, const double *cval,
                      int ruiz_iters, double alpha, double *D, double *E, double *tmp_m,
                      double *tmp_n) {
+  long long nnz = 0;
+  {
+    int last = 0;
+    if (m > 0) cudaMemcpyAsync(&last, rp + m, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    nnz = last;
+  }
   k_fill<<<nblocks(m, 256), 256, 0, st>>>(m, 1.0, D);
   k_fill<<<nblocks(n, 256), 256, 0, st>>>(n, 1.0, E);
   count_launches(2 + 4LL * ruiz_iters + (alpha >= 0.0 ? 4 : 0));
   for (int it = 0; it < ruiz_iters; ++it) {
     // both norms from the same current matrix, then both updates
-    k_side_stat<0><<<nblocks(m, 256), 256, 0, st>>>(m, rp, col, val, D, E, 1.0, tmp_m);
-    k_side_stat<0><<<nblocks(n, 256), 256, 0, st>>>(n, cp, ridx, cval, E, D, 1.0, tmp_n);
+    side_stat<0>(st, m, nnz, rp, col, val, D, E, 1.0, tmp_m);
+    side_stat<0>(st, n, nnz, cp, ridx, cval, E, D, 1.0, tmp_n);
     k_scale_update<<<nblocks(m, 256), 256, 0, st>>>(m, tmp_m, D);
     k_scale_update<<<nblocks(n, 256), 256, 0, st>>>(n, tmp_n, E);
   }
   if (alpha >= 0.0) {
-    k_side_stat<1><<<nblocks(m, 256), 256, 0, st>>>(m, rp, col, val, D, E, alpha, tmp_m);
-    k_side_stat<1><<<nblocks(n, 256), 256, 0, st>>>(n, cp, ridx, cval, E, D, 2.0 - alpha, tmp_n);
+    side_stat<1>(st, m, nnz, rp, col, val, D, E, alpha, tmp_m);
+    side_stat<1>(st, n, nnz, cp, ridx, cval, E, D, 2.0 - alpha, tmp_n);
     k_scale_update<<<nblocks(m, 256), 256, 0, st>>>(m, tmp_m, D);
     k_scale_update<<<nblocks(n, 256), 256, 0, st>>>(n, tmp_n, E);
   }
@@ -463,6 +542,32 @@ int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm) {
 
 void allow_large_smem_setup(int bytes) {
   cudaFuncSetAttribute(k_side_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_side_spmv_pw<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_side_spmv_pw<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void side_spmv_pw(cudaStream_t st, const SideStore &side, bool fp32, const double *src,
+                  const double *in_scale, double *out, double *part, unsigned int *ticket,
+                  double *ss, int grid) {
+  int smem = kBlockWarps * side.lay.seg * (int)sizeof(double);
+  if (fp32)
+    k_side_spmv_pw<float><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v32, side.wa, src,
+                                                             in_scale, out, part, ticket, ss);
+  else
+    k_side_spmv_pw<double><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, src,
+                                                              in_scale, out, part, ticket, ss);
+  count_launches(1);
+}
+
+// grid of the power-iteration product on `side`: whole resident waves, at most the work items
+int side_spmv_pw_grid(const SideStore &side, bool fp32, int sm_count) {
+  int smem = kBlockWarps * side.lay.seg * (int)sizeof(double);
+  int b = 0;
+  if (fp32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_side_spmv_pw<float>, kBlockThreads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_side_spmv_pw<double>, kBlockThreads, smem);
+  return tile_grid(side.lay, sm_count, b);
 }
 
 void side_spmv(cudaStream_t st, const SideStore &side, const double *src, double *out, int grid) {
