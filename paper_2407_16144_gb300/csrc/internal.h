@@ -105,7 +105,6 @@ int side_spmv_pw_grid(const SideStore &side, bool fp32, int sm_count);
 // deterministic sum of squares -> *out (device scalar); tmp holds >= 1024 doubles
 void sumsq(cudaStream_t st, int n, const double *x, double *out, double *tmp);
 // v = w / sqrt(*ss)
-void normalize(cudaStream_t st, int n, const double *w, const double *ss, double *v);
 void fill(cudaStream_t st, int n, double v, double *x);
 // y = a .* x (elementwise), optionally y = x ./ a when div = 1
 void vmul(cudaStream_t st, int n, const double *a, const double *x, double *y, int div);

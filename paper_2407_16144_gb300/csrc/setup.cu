@@ -175,13 +175,6 @@ __global__ void k_sum_final(int nparts, const double *part, double *out) {
   if (threadIdx.x == 0) *out = sh[0];
 }
 
-__global__ void k_normalize(int n, const double *w, const double *ss, double *v) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = sqrt(*ss);
-  v[i] = s > 0.0 ? w[i] / s : 0.0;
-}
-
 __global__ void k_fill(int n, double v, double *x) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = v;
@@ -580,11 +573,6 @@ void sumsq(cudaStream_t st, int n, const double *x, double *out, double *tmp) {
   k_sumsq_part<<<256, 256, 0, st>>>(n, x, tmp);
   k_sum_final<<<1, 256, 0, st>>>(256, tmp, out);
   count_launches(2);
-}
-
-void normalize(cudaStream_t st, int n, const double *w, const double *ss, double *v) {
-  k_normalize<<<nblocks(n, 256), 256, 0, st>>>(n, w, ss, v);
-  count_launches(1);
 }
 
 void fill(cudaStream_t st, int n, double v, double *x) {
