@@ -132,6 +132,12 @@ typedef struct {
   const double *x0;             /* optional warm start, host memory, unscaled (n)  (Algorithm 1
                                    input z^{0,0}); NULL = projection of 0 onto [l, u]          */
   const double *y0;             /* optional warm start, host memory (m); NULL = 0              */
+  int32_t adaptive_step;        /* 1 = the adaptive step rule (Section 7 adopts cuPDLP's): a step
+                                   eta is accepted while eta <= ||dz||_w^2 / (2 |dy^T K dx|), the
+                                   next one is min((1 - j^-0.3) eta_bar, (1 + j^-0.6) eta) with
+                                   j = iteration + 2, and a rejected step is redone with it.
+                                   precision 0 only; not in batched slots.       default 0    */
+  int32_t reserved;
 } rhpdhg_params;
 
 /* Result of a finished solve, filled by rhpdhg_poll. */
@@ -145,7 +151,8 @@ typedef struct {
   double  rel_p, rel_d, rel_gap;/* relative KKT parts at the returned point (last check)       */
   double  primal_obj, dual_obj;
   double  solve_seconds;        /* host wall clock from solve() to the final status           */
-  double  eta, omega, sigma_max;/* step size, final primal weight, power-iteration estimate    */
+  double  eta, omega, sigma_max;/* step size (the last one with the adaptive rule), final
+                                   primal weight, power-iteration estimate                    */
   double *x;                    /* caller-owned, n entries, or NULL: primal point (unscaled)   */
   double *y;                    /* caller-owned, m entries, or NULL: dual point (unscaled)     */
   double *cert_x;               /* caller-owned, n, or NULL: unbounded ray d (DUAL_INFEASIBLE) */
@@ -160,7 +167,7 @@ typedef struct {
   double  fpr_sq;               /* ||z^{n,k} - T(z^{n,k})||_P^2                                */
   double  omega;                /* primal weight in force at iteration t                      */
   int32_t restart;              /* 1 if z^{n+1,0} = T(z^{n,k}) follows                         */
-  int32_t pad;
+  int32_t retries;              /* adaptive step: rejected steps before this iteration's      */
   int64_t active;               /* check iterations: columns with x~ on a bound (the active
                                    set of Section 4's partition as the iterates see it); else -1 */
   int64_t changed;              /* check iterations: columns whose on-bound status changed since

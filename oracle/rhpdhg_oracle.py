@@ -77,6 +77,7 @@ class OracleParams:
     restart_scheme: int = 0       # 0 = adaptive (eq. adaptive-restart), 1 = fixed (eq. fixed-restart)
     restart_beta: float = math.exp(-1.0)
     check_every: int = 64
+    adaptive_step: int = 0        # 1 = the adaptive step rule (Section 7, "as cuPDLP")
     x0: Optional[np.ndarray] = None
     y0: Optional[np.ndarray] = None
 
@@ -289,6 +290,7 @@ class OracleResult:
     trace: list
     snapshots: dict
     telemetry: list = dataclasses.field(default_factory=list)
+    steps: list = dataclasses.field(default_factory=list)
 
 
 def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
@@ -345,9 +347,32 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
     telemetry = []
     at_prev = np.zeros(n, dtype=bool)
     t = 0
+    retries = 0
+    eta_next = eta
+    steps = []          # adaptive step: (t, eta tried, eta_bar, retries before it) per attempt
     while True:
         xt, yt = pdhg_T(Kh, KhT, c, q, l, u, m_eq, tau, sigma, x, y)
         dx, dy = x - xt, y - yt
+        if params.adaptive_step:
+            # the step is admissible while eta <= eta_bar = ||dz||_w^2 / (2 |dy^T K^ dx|) with
+            # ||dz||_w^2 = omega ||dx||^2 + ||dy||^2 / omega; the next step is
+            # min((1 - j^-0.3) eta_bar, (1 + j^-0.6) eta), j = t + 2; an inadmissible step is
+            # retried with it (reading R22)
+            cross = abs(float(dy @ (Kh @ dx)))
+            num = omega * float(dx @ dx) + float(dy @ dy) / omega
+            eta_bar = num / (2.0 * cross) if cross > 0.0 else math.inf
+            j = t + 2.0
+            eta_next = min((1.0 - j ** -0.3) * eta_bar, (1.0 + j ** -0.6) * eta)
+            steps.append((t, eta, eta_bar, retries))
+            if eta > eta_bar:
+                retries += 1
+                if retries > 64 or not np.isfinite(eta_next) or eta_next <= 0.0:
+                    status = NUMERICAL_ERROR
+                    break
+                eta = eta_next
+                tau, sigma = eta / omega, eta * omega
+                continue
+            retries = 0
         fpr2 = p_norm_sq(Kh, dx, dy, tau, sigma)
         if not np.isfinite(fpr2):
             status = NUMERICAL_ERROR
@@ -395,6 +420,9 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
         t += 1
         if status != RUNNING:
             break
+        if params.adaptive_step:
+            eta = eta_next
+            tau, sigma = eta / omega, eta * omega
         if restart:
             # z^{n+1,0} <- T(z^{n,k}).  Second candidate: the anchor movement
             # z^{n+1,0} - z^{n,0}, the restarted form of the normalised iterate
@@ -434,7 +462,7 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
                         rel_d=kkt["rel_d"], rel_gap=kkt["rel_gap"],
                         primal_obj=kkt["primal_obj"], dual_obj=kkt["dual_obj"], x=E * xt,
                         y=D * yt, cert_x=cert_x, cert_y=cert_y, cert_source=cert_source,
-                        telemetry=telemetry,
+                        telemetry=telemetry, steps=steps,
                         eta=eta, omega=omega,
                         sigma_max=sigma_max, D=D, E=E,
                         solve_seconds=time.perf_counter() - t_start, trace=tr,

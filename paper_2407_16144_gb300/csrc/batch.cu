@@ -512,6 +512,8 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   else rhpdhg_params_default(&P);
   if (P.precision != 0)
     return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: the batched kernel computes in FP64");
+  if (P.adaptive_step)
+    return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: batched slots use the constant step");
   // host validation and transpose (the batched path serves small LPs)
   const int64_t *rp = lp->row_ptr;
   if (rp[0] != 0 || rp[m] != nnz) return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: malformed row_ptr");

@@ -432,6 +432,7 @@ int rhpdhg_params_default(rhpdhg_params *p) {
   p->trace = 0;
   p->profile = 0;
   p->trace_capacity = 4096;
+  p->adaptive_step = 0;
   p->x0 = nullptr;
   p->y0 = nullptr;
   return RHPDHG_OK;
@@ -464,8 +465,11 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
       P.first_epoch_len < 0 || P.max_epoch_len < 0 || P.restart_scheme < 0 ||
       P.restart_scheme > 1 || (P.restart_scheme == 1 && P.max_epoch_len < 1) ||
       !(P.restart_beta > 0 && P.restart_beta < 1) || P.trace_capacity < 0 ||
-      P.pock_chambolle_alpha > 2.0)
+      P.pock_chambolle_alpha > 2.0 || P.adaptive_step < 0 || P.adaptive_step > 1)
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "invalid parameter");
+  if (P.adaptive_step && P.precision == 1)
+    return set_err(nullptr, RHPDHG_ERR_INVALID_ARG,
+                   "the adaptive step rule runs with precision 0 (FP64) only");
 
   h = new rhpdhg_handle();
   h->p = P;
@@ -753,6 +757,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   ic.trace_cap = h->trace ? P.trace_capacity : 0;
   ic.trace = h->trace;
   ic.mixed = h->mixed ? 1 : 0;
+  ic.adaptive = P.adaptive_step ? 1 : 0;
   h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv,
                   h->certy2};
   h->cv = ColVecs{h->x, h->xt, h->x0, h->kty, h->kty0, h->xout, h->certx, h->c, h->l, h->u,
@@ -803,7 +808,7 @@ int rhpdhg_poll(rhpdhg_handle *h, rhpdhg_result *r) {
   r->primal_obj = c.pobj;
   r->dual_obj = c.dobj;
   r->solve_seconds = h->solve_seconds;
-  r->eta = h->eta;
+  r->eta = h->p.adaptive_step ? c.eta : h->eta;
   r->omega = c.omega;
   r->sigma_max = h->sigma_max;
   const cudaMemcpyKind kind =

@@ -111,6 +111,10 @@ struct Ctl {
   double mv_cd, mv_u, mv_l, mv_dlb, mv_dub, mv_au, mv_al;
   int mv_ready;
   int cert_src;          // candidate that certified infeasibility (kCert*)
+  // adaptive step rule: redo = 1 while iteration t is being recomputed with a smaller step
+  // (the kernels then take z_t from the stored x, K^T y, y, K x); retries counts the attempts
+  int redo, retries;
+  double eta_next;
   // active-set telemetry of check iterations: columns with x~ on a bound, and columns whose
   // on-bound status changed since the previous check (integer atomics, reset by col_finalize)
   unsigned long long tel_act, tel_chg;
@@ -124,7 +128,7 @@ struct Ctl {
 struct TraceRec {      // mirrors rhpdhg_trace_rec
   long long t, epoch, k;
   double fpr_sq, omega;
-  int restart, pad;
+  int restart, retries;        // retries: rejected step sizes before this iteration's step
   long long active, changed;   // check iterations: active-set telemetry, else -1
 };
 
@@ -146,6 +150,7 @@ struct IterConsts {
   long long trace_cap;
   TraceRec *trace;
   int mixed;                  // 1 = FP32-offset iterates (certificates escalate to FP64)
+  int adaptive;               // 1 = adaptive step rule (inadmissible steps are redone)
 };
 
 // ---------------------------------------------------------------------------------------------

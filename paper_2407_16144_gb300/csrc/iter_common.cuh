@@ -75,6 +75,29 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
     }
   }
   const double tau = ctl->tau, omega = ctl->omega;
+  if (ic.adaptive) {
+    // the step eta is admissible while eta <= eta_bar = ||dz||_w^2 / (2 |dy^T K dx|),
+    // ||dz||_w^2 = omega ||dx||^2 + ||dy||^2 / omega; the next step is
+    // min((1 - j^-0.3) eta_bar, (1 + j^-0.6) eta), j = t + 2; an inadmissible step is redone
+    const double eta = ctl->eta;
+    const double cross = fabs(r[1]);
+    const double num = omega * ctl->dx_sq + r[0] / omega;
+    const double eta_bar = cross > 0.0 ? num / (2.0 * cross) : INFINITY;
+    const double j = (double)t + 2.0;
+    const double nxt = fmin((1.0 - pow(j, -0.3)) * eta_bar, (1.0 + pow(j, -0.6)) * eta);
+    if (eta > eta_bar) {
+      ctl->retries += 1;
+      if (ctl->retries > 64 || !(nxt > 0.0) || !isfinite(nxt)) ctl->status = kNumericalError;
+      ctl->eta = nxt;
+      ctl->tau = nxt / omega;
+      ctl->sigma = nxt * omega;
+      ctl->redo = 1;
+      ctl->cnt_row = 0;
+      ctl->stage = 1;
+      return;
+    }
+    ctl->eta_next = nxt;
+  }
   const double fpr2 = ctl->dx_sq / tau + r[0] / sigma + 2.0 * r[1];
   const double fpr0 = (k == 0) ? fpr2 : ctl->fpr0_sq;
   bool rs;
@@ -87,7 +110,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
   if (ic.trace && t < ic.trace_cap) {
     TraceRec tr;
     tr.t = t; tr.epoch = n_ep; tr.k = k; tr.fpr_sq = fpr2; tr.omega = omega;
-    tr.restart = rs ? 1 : 0; tr.pad = 0;
+    tr.restart = rs ? 1 : 0; tr.retries = ctl->retries;
     tr.active = -1; tr.changed = -1;
     ic.trace[t] = tr;
   }
@@ -100,6 +123,15 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
   ctl->inf_kd_eq = r[8];
   ctl->inf_kd_in = r[9];
   if (!isfinite(fpr2)) ctl->status = kNumericalError;
+  // the accepted step's successor takes effect from the next PDHG evaluation
+  const double eta_now = ic.adaptive ? ctl->eta_next : ic.eta;
+  if (ic.adaptive) {
+    ctl->eta = eta_now;
+    ctl->tau = eta_now / omega;
+    ctl->sigma = eta_now * omega;
+    ctl->redo = 0;
+    ctl->retries = 0;
+  }
   if (rs) {
     if (ic.pw_update) {
       const double dxa = sqrt(ctl->xa_sq), dya = sqrt(r[2]);
@@ -107,8 +139,8 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
       if (dxa > 1e-10 && dya > 1e-10 && ratio > 0.0 && isfinite(ratio)) {
         const double om = exp(0.5 * log(ratio) + 0.5 * log(omega));
         ctl->omega = om;
-        ctl->tau = ic.eta / om;
-        ctl->sigma = ic.eta * om;
+        ctl->tau = eta_now / om;
+        ctl->sigma = eta_now * om;
       }
     }
     ctl->k_next = 0;
@@ -130,6 +162,13 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
 __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, const double *r,
                                              long long t, bool check, bool cert, bool rp,
                                              bool move, int phase, bool tel = true) {
+  if (ctl->redo) {          // x~_t recomputed with the smaller step; the row stage follows
+    ctl->dx_sq = r[0];
+    ctl->xa_sq = r[1];
+    ctl->cnt_col = 0;
+    ctl->stage = 0;
+    return;
+  }
   ctl->dx_sq = r[0];
   ctl->xa_sq = r[1];
   int st = kRunning;
@@ -211,8 +250,10 @@ struct StepFlags {
   bool cert;        // certificate test of T(z) - z at this iteration (restart point or check)
   bool rp;          // restart point (k == 0, n >= 1): z_t is the anchor
   bool move;        // this restart's anchor movement z^{n+1,0} - z^{n,0} is tested
-  bool stash;       // rHPDHG: keep x_{t+1}, K^T y_{t+1} (the next iteration is a check)
+  bool stash;       // rHPDHG: keep x_{t+1}, K^T y_{t+1} (next iteration a check, or adaptive)
   int m_eq;
+  bool redo = false;   // adaptive step: recompute T(z_t) from the stored z_t
+  bool keep = false;   // adaptive step, rHPDHG: keep y_t, K x_t for a redo
 };
 
 // Row i of K^ x~_t = dot: forms y_t and K x_t by the pending blend (eq. hpdhg / eq. hrpdhg, or
@@ -226,7 +267,9 @@ __device__ __forceinline__ void row_epilogue(int i, double dot, const RowVecs &v
   const double w = f.w, sigma = f.step;
   const double qi = v.q[i];
   double yi, kxi, y0i;
-  if (f.restart) {
+  if (f.redo) {
+    yi = v.y[i]; kxi = v.kx[i]; y0i = v.y0[i];
+  } else if (f.restart) {
     if (f.move) {
       const double dyb = ytp - v.y0[i];                  // y^{n+1,0} - y^{n,0} (scaled)
       const double kdb = (kxtp - v.kx0[i]) * v.dinv[i];  // K (x^{n+1,0} - x^{n,0}) (unscaled)
@@ -239,7 +282,7 @@ __device__ __forceinline__ void row_epilogue(int i, double dot, const RowVecs &v
     }
     yi = ytp; kxi = kxtp; y0i = yi;
     v.y0[i] = yi; v.kx0[i] = kxi;
-    if (RHO2) { v.y[i] = yi; v.kx[i] = kxi; }
+    if (RHO2 || f.keep) { v.y[i] = yi; v.kx[i] = kxi; }
   } else {
     y0i = v.y0[i];
     const double kx0i = v.kx0[i];
@@ -250,6 +293,7 @@ __device__ __forceinline__ void row_epilogue(int i, double dot, const RowVecs &v
     } else {
       yi = w * ytp + (1.0 - w) * y0i;
       kxi = w * kxtp + (1.0 - w) * kx0i;
+      if (f.keep) { v.y[i] = yi; v.kx[i] = kxi; }
     }
   }
   double yn = yi + sigma * (qi - 2.0 * dot + kxi);

@@ -45,6 +45,8 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   double *my = smem + (threadIdx.x >> 5) * lay.seg;
 
   StepFlags fl{restart, w, sigma, check, cert, rp, (bool)move, false, ic.m_eq};
+  fl.redo = ic.adaptive && ctl->redo;
+  fl.keep = ic.adaptive && !RHO2;
   auto epi = [&](int i, double dot, bool lg) {
     if (lg) row_epilogue<RHO2>(i, dot, v, fl, al, a);
     else row_epilogue<RHO2>(i, dot, v, fl, a, a);
@@ -76,7 +78,28 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   const bool cert = rp || check;
   const bool move = phase == 0 && restart;
   const long long tn = phase == 0 ? t + 1 : t;     // the iteration this kernel's x_{t+1} opens
-  const bool stash = ((tn + 1) % ic.check_every == 0) || (tn + 1 >= ic.max_iters);
+  const bool stash = ic.adaptive || ((tn + 1) % ic.check_every == 0) || (tn + 1 >= ic.max_iters);
+  if (ic.adaptive && ctl->redo) {
+    // adaptive step: x~_t = proj_X(x_t - tau (c - K^T y_t)) again, from the stored x_t and
+    // K^T y_t, with the smaller step; no product is needed
+    Acc<2, 0> a;
+    a.zero();
+    const double tau = ctl->tau;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < lay.nrows; j += gridDim.x * blockDim.x) {
+      const double xj = v.x[j];
+      const double xtn = fmin(fmax(xj - tau * (v.c[j] - v.kty[j]), v.l[j]), v.u[j]);
+      v.xt[j] = xtn;
+      const double dx = xj - xtn, xa = xtn - v.x0[j];
+      a.s[0] += dx * dx;
+      a.s[1] += xa * xa;
+    }
+    if (cta_reduce_and_ticket(a, 0x3u, 0u, 0u, part, &ctl->cnt_col)) {
+      double r[19] = {0.0};
+      grid_finish<2, 0>(part, r, 0x3u, 0u);
+      if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, false, false, false, false, phase);
+    }
+    return;
+  }
   ColAcc a;
   ColAccL al;
   a.zero();

@@ -51,7 +51,8 @@ class rhpdhg_params(C.Structure):
                 ("max_epoch_len", C.c_int64), ("restart_scheme", C.c_int32),
                 ("restart_beta", C.c_double), ("check_every", C.c_int32),
                 ("use_graphs", C.c_int32), ("trace", C.c_int32), ("profile", C.c_int32),
-                ("trace_capacity", C.c_int64), ("x0", C.c_void_p), ("y0", C.c_void_p)]
+                ("trace_capacity", C.c_int64), ("x0", C.c_void_p), ("y0", C.c_void_p),
+                ("adaptive_step", C.c_int32), ("reserved", C.c_int32)]
 
 
 class rhpdhg_result(C.Structure):
@@ -67,7 +68,7 @@ class rhpdhg_result(C.Structure):
 class rhpdhg_trace_rec(C.Structure):
     _fields_ = [("t", C.c_int64), ("epoch", C.c_int64), ("k", C.c_int64),
                 ("fpr_sq", C.c_double), ("omega", C.c_double), ("restart", C.c_int32),
-                ("pad", C.c_int32), ("active", C.c_int64), ("changed", C.c_int64)]
+                ("retries", C.c_int32), ("active", C.c_int64), ("changed", C.c_int64)]
 
 
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
@@ -645,8 +646,8 @@ class Solver:
     def trace(self, capacity: int = 1 << 16):
         rc, recs = rhpdhg_get_trace(self.h, capacity)
         _check(rc, self.h, "rhpdhg_get_trace")
-        return [(r.t, r.epoch, r.k, r.fpr_sq, bool(r.restart), r.omega, r.active, r.changed)
-                for r in recs]
+        return [(r.t, r.epoch, r.k, r.fpr_sq, bool(r.restart), r.omega, r.active, r.changed,
+                 r.retries) for r in recs]
 
     def kernel_times(self):
         rc, d = rhpdhg_kernel_times(self.h)

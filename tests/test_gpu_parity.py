@@ -429,6 +429,54 @@ def test_active_set_identification_on_device(rh, precision):
     assert np.array_equal(np.abs(r.x) <= tol, lp.x_star == 0.0)
 
 
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("case", ["c1", "c2_small"])
+def test_adaptive_step_matches_oracle(rh, case, alg):
+    """Adaptive step rule (FP64): the same accepted steps, retries, restarts and FPR as the
+    oracle over the first 100 iterations; then both solves reach 1e-8 at the planted optimum.
+    Steps above 1/||K|| make the map locally expansive, so the two trajectories separate
+    slowly after that and iteration counts to tolerance are compared only loosely."""
+    lp = CASES[case]()
+    T = 100
+    common = dict(algorithm=alg, adaptive_step=1, eps_rel_kkt=1e-14, first_epoch_len=20,
+                  check_every=16)
+    o = O.solve(lp, O.OracleParams(max_iters=T, **common), trace=True)
+    with rh.Solver(lp, max_iters=T, trace=1, trace_capacity=256, **common) as s:
+        r = s.run()
+        tr = s.trace()
+    assert r.iters == T and len(tr) == T
+    retries = {}
+    for (t, eta, eb, rt) in o.steps:
+        retries[t] = rt
+    stop = min(first_tie(o.trace), first_tie(tr))
+    for (a, b) in zip(tr[:stop], o.trace[:stop]):
+        assert a[:3] == b[:3] and a[4] == b[4]
+        assert abs(a[3] - b[3]) <= 1e-6 * max(abs(b[3]), 1e-300), (a[0], a[3], b[3])
+        assert abs(a[5] - b[5]) <= 1e-9 * b[5]
+        assert a[8] == retries[a[0]], (a[0], a[8], retries[a[0]])
+    oo = O.solve(lp, O.OracleParams(algorithm=alg, adaptive_step=1, eps_rel_kkt=1e-8,
+                                    max_iters=100_000))
+    with rh.Solver(lp, algorithm=alg, adaptive_step=1, eps_rel_kkt=1e-8,
+                   max_iters=100_000) as s:
+        rr = s.run()
+    assert rr.status == rh.STATUS_OPTIMAL == oo.status
+    k = O.rel_kkt(lp, O.csr_matrix(lp), rr.x, rr.y)
+    assert k["rel_kkt"] <= 1.05e-8
+    ref = lp.planted_objective()
+    assert abs(rr.primal_obj - ref) <= 1e-6 * (1 + abs(ref))
+    print(f"adaptive {case} alg={alg}: {rr.iters} iterations (oracle {oo.iters}), "
+          f"final eta {rr.eta:.4f}")
+
+
+def test_adaptive_step_parameter_checks(rh):
+    lp = lpgen.make_c1(0)
+    with pytest.raises(rh.RHPDHGError, match="precision 0"):
+        rh.Solver(lp, adaptive_step=1, precision=1)
+    with rh.Batch(2, 64 << 20) as b:
+        with pytest.raises(rh.RHPDHGError, match="constant step"):
+            b.add(lp, adaptive_step=1)
+
+
 def test_mixed_first_iterations_close_to_fp64(rh):
     """Before any restart the mixed path follows the FP64 trajectory to FP32 accuracy."""
     lp = CASES["c2_small"]()

@@ -420,6 +420,26 @@ def test_active_set_identification(case):
         assert np.array_equal(r.x == 0.0, lp.x_star == 0.0)
 
 
+@pytest.mark.parametrize("alg", [0, 1])
+def test_adaptive_step_bound(alg):
+    """Adaptive step rule: |dy^T K dx| <= ||K|| ||dx|| ||dy|| <= ||K|| ||dz||_w^2 / 2, so the
+    admissibility bound eta_bar is never below 1 / ||K^|| (SVD); every accepted step satisfies
+    eta <= eta_bar; and the solve still reaches the planted optimum."""
+    lp = lpgen.make_c2(1, scale=0.01)
+    r = O.solve(lp, O.OracleParams(algorithm=alg, eps_rel_kkt=1e-8, max_iters=100_000,
+                                   adaptive_step=1))
+    Kh, _, _ = O.scale_problem(O.csr_matrix(lp), 10, 1.0)
+    smax = np.linalg.svd(Kh.toarray(), compute_uv=False)[0]
+    assert r.status == O.OPTIMAL
+    assert r.steps and min(eb for (_, _, eb, _) in r.steps) >= (1.0 - 1e-12) / smax
+    accepted = {}
+    for (t, eta, eb, _) in r.steps:
+        accepted[t] = (eta, eb)                        # the last attempt of t is the accepted one
+    assert all(eta <= eb for (eta, eb) in accepted.values())
+    ref = lp.planted_objective()
+    assert abs(r.primal_obj - ref) <= 1e-6 * (1 + abs(ref))
+
+
 def test_iteration_limit_status():
     lp = lpgen.make_c1(0)
     r = O.solve(lp, O.OracleParams(eps_rel_kkt=1e-12, max_iters=100))
