@@ -146,6 +146,22 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_max(dist, values, device):
+    """Max over ranks of each timed total (replicas: the slowest rank bounds the job)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_throughput(world, units_per_rank, max_ms):
+    """Whole-job rate of `world` independent replicas that each ran `units_per_rank` units in
+    at most `max_ms` milliseconds (weak scaling)."""
+    return world * units_per_rank / (max_ms / 1000.0)
+
+
 def problem_bytes(lp):
     return (8 * (lp.m + 1) + 12 * lp.nnz + 8 * (3 * lp.n) + 8 * lp.m)
 
@@ -417,17 +433,12 @@ def run_ours(args):
     rp = s.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
     kt = s.kernel_times()
     s.close()
-    if dist is not None:
-        t = torch.tensor([total_ms, sum(e2e_ms)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_total = float(t[0]), float(t[1])
-    else:
-        e2e_total = sum(e2e_ms)
+    total_ms, e2e_total = replica_max(dist, [total_ms, sum(e2e_ms)], "cuda")
     if rank != 0:
         return 0
     ms_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
-    e2e_value = world * len(e2e_ms) / (e2e_total / 1000.0)
+    value = replica_throughput(world, args.steps, total_ms)
+    e2e_value = replica_throughput(world, len(e2e_ms), e2e_total)
     peak, peak_kind = load_peaks()
     # dominant kernel by total time
     if kt["ms_col"] >= kt["ms_row"]:
