@@ -256,7 +256,18 @@ __device__ __forceinline__ void store_group(Acc<NS, 0> &al, unsigned smask, doub
 // In the last CTA: reduce the grid's partials in block order, then the long-row groups'
 // partials in group order, for the slots in the masks (others return 0).  out[i] valid in all
 // threads.
-template <int NS, int NM>
+//
+// Thread t sums blocks t, t + blockDim, ... of each slot in that order, then groups t,
+// t + blockDim, ...; each warp reduces its lanes with a fixed shuffle tree and the warps' results
+// are added in warp order, so the result does not depend on how the loads are scheduled.  The
+// reads are latency-bound (a few values per thread from L2, possibly on the other die) and the
+// last CTA's time is set by the number of dependent round trips.  Two schedules: block by block
+// with all active slots of a block in flight (ceil(nb / blockDim) rounds), or slot by slot with
+// kGridBatch blocks in flight (about one round per active slot); the one with fewer rounds runs.
+// BATCH = false keeps only the first (the FP64 kernels: ALU-bound, with fewer CTAs, where the
+// second gains nothing and its registers cost).
+constexpr int kGridBatch = 10;
+template <int NS, int NM, bool BATCH = true>
 __device__ void grid_finish(const double *part, double *out, unsigned smask, unsigned mmask,
                             const double *gpart = nullptr, int ngroups = 0) {
   __shared__ double red[kBlockWarps][kMaxPartials];
@@ -266,16 +277,32 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) v[i] = 0.0;
   const unsigned all = smask | (mmask << NS);
-  // thread t sums blocks t, t + blockDim, ... then groups t, t + blockDim, ... (fixed order);
-  // unrolled so that several blocks' loads are in flight at once
+  const int rounds_by_block = (nb + (int)blockDim.x - 1) / (int)blockDim.x;
+  if (!BATCH || rounds_by_block <= __popc(all)) {
 #pragma unroll 4
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    const double *src = part + (size_t)b * kMaxPartials;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const double *src = part + (size_t)b * kMaxPartials;
 #pragma unroll
-    for (int i = 0; i < NS + NM; ++i) {
-      if (!((all >> i) & 1u)) continue;
-      const double p = __ldcg(src + i);
-      v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
+      for (int i = 0; i < NS + NM; ++i) {
+        if (!((all >> i) & 1u)) continue;
+        const double p = __ldcg(src + i);
+        v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
+      }
+    }
+  } else {
+    for (int b0 = threadIdx.x; b0 < nb; b0 += kGridBatch * blockDim.x) {
+#pragma unroll
+      for (int i = 0; i < NS + NM; ++i) {
+        if (!((all >> i) & 1u)) continue;
+        double p[kGridBatch];
+#pragma unroll
+        for (int j = 0; j < kGridBatch; ++j) {
+          const int b = b0 + j * blockDim.x;
+          p[j] = b < nb ? __ldcg(part + (size_t)b * kMaxPartials + i) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < kGridBatch; ++j) v[i] = (i < NS) ? v[i] + p[j] : fmax(v[i], p[j]);
+      }
     }
   }
   // groups hold sums only (long-row maxima go straight to the finishing warp's CTA partials)

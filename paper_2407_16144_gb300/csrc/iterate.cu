@@ -59,7 +59,7 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
     double r[13];
-    grid_finish<7, 6>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
+    grid_finish<7, 6, false>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
   }
 }
@@ -95,7 +95,7 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
     }
     if (cta_reduce_and_ticket(a, 0x3u, 0u, 0u, part, &ctl->cnt_col)) {
       double r[19] = {0.0};
-      grid_finish<2, 0>(part, r, 0x3u, 0u);
+      grid_finish<2, 0, false>(part, r, 0x3u, 0u);
       if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, false, false, false, false, phase);
     }
     return;
@@ -121,7 +121,7 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[19];
-    grid_finish<11, 8>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
+    grid_finish<11, 8, false>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, cert, rp, move, phase);
   }
 }
