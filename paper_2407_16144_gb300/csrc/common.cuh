@@ -453,10 +453,24 @@ __device__ __forceinline__ void tile_rows(const PT *smem, int row0, int nr, int 
   }
 }
 
-template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone>
+// Prefetch of the line holding *p into L1 (no register is held while it is in flight).
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Default per-row prefetch hook of walk_tiles: none.
+struct NoPrefetch {
+  __device__ __forceinline__ void operator()(int) const {}
+};
+
+// pre(row) is called by the lane of each short-tile row before the tile's entries are staged,
+// so that what the row's epilogue will read can be requested while the staging round trips run.
+template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone,
+          typename Pre = NoPrefetch>
 __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals<VT> vals,
                                            const Src &src, PT *smem, const WalkScratch ws,
-                                           Epi &epi, GroupDone &gdone) {
+                                           Epi &epi, GroupDone &gdone,
+                                           const Pre &pre = Pre()) {
   const int lane = threadIdx.x & 31;
   const int gwarp = blockIdx.x * kBlockWarps + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kBlockWarps;
@@ -468,6 +482,7 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
       const int st = item - lay.n_chunks;
       const int row0 = st * kTileRows;
       const int nr = min(kTileRows, lay.nrows - row0);
+      if (lane < nr) pre(row0 + lane);
       const int rb = lay.ptr_s[row0 + min(lane, nr - 1)];
       const int seg_e = lay.tile_end[st];
       const int seg_b = __shfl_sync(0xffffffffu, rb, 0);     // 4-aligned

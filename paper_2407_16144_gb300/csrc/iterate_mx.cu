@@ -179,7 +179,17 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       store_group(al, smask, wb.group_part, grp);
     };
     auto gB = [&](int j) { return dxt[j]; };
-    walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone);
+    auto pre = [&](int i) {
+      prefetch_l1(v.dyt + i);
+      prefetch_l1(v.kdxt + i);
+      if (RHO2) {
+        prefetch_l1(v.dy + i);
+        prefetch_l1(v.kdx + i);
+      }
+      prefetch_l1(v.r0 + i);
+      if (i >= m_eq) prefetch_l1(v.ylo + i);
+    };
+    walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone, pre);
   }
   // the FP32 sums (zero in restart mode) are reduced over the warp in FP32, then widened
   unsigned prewarp = 0u;
@@ -346,7 +356,17 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       else body(j, ktdyt, a, fa);
     };
     auto gB = [&](int i) { return dyt[i]; };
-    walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone);
+    auto pre = [&](int j) {
+      prefetch_l1(v.dxt + j);
+      if (RHO2) {
+        prefetch_l1(v.dx + j);
+        prefetch_l1(v.ktdy + j);
+      }
+      prefetch_l1(v.s0 + j);
+      prefetch_l1(v.xlo + j);
+      prefetch_l1(v.xhi + j);
+    };
+    walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone, pre);
     if (check) tel_flush(ctl, tl);
   }
   unsigned prewarp = 0u;
