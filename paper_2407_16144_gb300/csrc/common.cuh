@@ -32,6 +32,7 @@ constexpr int kSegBudget = 1024;       // entries of one tile's short segment (s
 constexpr int kMaxTileSmem = kBlockWarps * (kSegBudget + 8) * 8;   // bytes, FP64 staging
 constexpr int kChunk = 256;            // entries per long-row chunk (8 per lane)
 constexpr int kStageUnroll = 2;        // 4-entry groups staged per lane per round
+constexpr int kMaxTileMult = 4;        // most short tiles walked as one work item
 
 // Infeasibility certificate candidates (rhpdhg_result.cert_source).
 enum CertSource : int { kCertNone = 0, kCertRestartPoint = 1, kCertCheck = 2, kCertAnchorMove = 3 };
@@ -49,8 +50,8 @@ enum Status : int {
 // rows are further cut into chunks of at most kChunk entries; a chunk is one warp task.
 struct SideLayout {
   int nrows = 0;
-  int seg = 8;               // per-warp staging stride (entries): longest tile segment,
-                             // rounded up to 4, plus 4
+  int seg = 8;               // per-warp staging stride (entries): longest segment of a work
+                             // item's tile group, rounded up to 4, plus 4
   int n_short_tiles = 0;     // ceil(nrows / 32)
   int n_long = 0;            // number of long rows
   int n_long_tiles = 0;      // ceil(n_long / 32): groups of 32 long rows sharing an epilogue
@@ -65,7 +66,9 @@ struct SideLayout {
   const int *idx_l = nullptr;       // long entries (padded, plus kChunk slack at the end)
   const int *chunk_ptr = nullptr;   // n_long + 1: chunks of long row i are [chunk_ptr[i], ..[i+1])
   const int *chunk_row = nullptr;   // n_chunks: long-row index of each chunk
-  __host__ __device__ int total_items() const { return n_chunks + n_short_tiles; }
+  int tile_mult = 1;         // consecutive short tiles per work item (1 .. kMaxTileMult)
+  int n_tile_groups = 0;     // ceil(n_short_tiles / tile_mult)
+  __host__ __device__ int total_items() const { return n_chunks + n_tile_groups; }
 };
 
 // Values of one side in one precision.
@@ -453,6 +456,7 @@ __device__ __forceinline__ void tile_rows(const PT *smem, int row0, int nr, int 
   }
 }
 
+
 // Prefetch of the line holding *p into L1 (no register is held while it is in flight).
 __device__ __forceinline__ void prefetch_l1(const void *p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
@@ -463,10 +467,71 @@ struct NoPrefetch {
   __device__ __forceinline__ void operator()(int) const {}
 };
 
+// Stage the products of the segment [seg_b, seg_e) (seg_b 4-aligned) in smem[0, ...): lane
+// handles 4-entry groups g = lane, lane + 32, ..., kStageUnroll at a time.
+template <typename VT, typename PT, typename Src>
+__device__ __forceinline__ void stage_segment(const SideLayout &lay, const SideVals<VT> vals,
+                                              const Src &src, PT *smem, int seg_b, int seg_e) {
+  const int lane = threadIdx.x & 31;
+  const int nvec = (seg_e - seg_b + 3) >> 2;             // groups of 4 entries
+  constexpr int kU = kStageUnroll;
+  for (int g0 = 0; g0 < nvec; g0 += kWarp * kU) {
+    int j[kU][4];
+    Vec4<VT> vv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int g = g0 + u * kWarp + lane;
+      if (g < nvec) {
+        load_idx4(lay.idx_s + seg_b + 4 * g, j[u]);
+        vv[u].load(vals.s + seg_b + 4 * g);
+      }
+    }
+    PT x[kU][4];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int g = g0 + u * kWarp + lane;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        x[u][e] = (g < nvec && seg_b + 4 * g + e < seg_e) ? PT(src(j[u][e])) : PT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int g = g0 + u * kWarp + lane;
+      if (g < nvec) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) smem[4 * g + e] = PT(vv[u].v[e]) * x[u][e];
+      }
+    }
+  }
+}
+
+// One short tile st of walk_tiles (tile_mult == 1): stage its segment, then lane r sums row r
+// and runs its epilogue.
+template <typename VT, typename PT, typename Src, typename Epi, typename Pre>
+__device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<VT> vals,
+                                          const Src &src, PT *smem, Epi &epi, const Pre &pre,
+                                          int st) {
+  const int lane = threadIdx.x & 31;
+  const int row0 = st * kTileRows;
+  const int nr = min(kTileRows, lay.nrows - row0);
+  if (lane < nr) pre(row0 + lane);
+  const int rb = lay.ptr_s[row0 + min(lane, nr - 1)];
+  const int seg_e = lay.tile_end[st];
+  const int seg_b = __shfl_sync(0xffffffffu, rb, 0);     // 4-aligned
+  int re = __shfl_down_sync(0xffffffffu, rb, 1);
+  if (lane >= nr - 1) re = seg_e;
+  stage_segment<VT, PT>(lay, vals, src, smem, seg_b, seg_e);
+  __syncwarp();
+  tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lay.long_mask[st], epi);
+  __syncwarp();
+}
+
+// GROUPED = false is the walk of layouts with tile_mult == 1 only (one tile per item, fewer
+// registers); GROUPED = true walks any layout.
 // pre(row) is called by the lane of each short-tile row before the tile's entries are staged,
 // so that what the row's epilogue will read can be requested while the staging round trips run.
-template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone,
-          typename Pre = NoPrefetch>
+template <typename VT, typename PT, bool GROUPED = true, typename Src, typename Epi,
+          typename GroupDone, typename Pre = NoPrefetch>
 __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals<VT> vals,
                                            const Src &src, PT *smem, const WalkScratch ws,
                                            Epi &epi, GroupDone &gdone,
@@ -478,49 +543,41 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
   for (int item = gwarp; item < total; item += nwarps) {
     if (item < lay.n_chunks) {
       walk_chunk<VT, PT>(lay, vals, src, ws, epi, gdone, item);
+    } else if constexpr (!GROUPED) {
+      walk_tile<VT, PT>(lay, vals, src, smem, epi, pre, item - lay.n_chunks);
     } else {
-      const int st = item - lay.n_chunks;
-      const int row0 = st * kTileRows;
-      const int nr = min(kTileRows, lay.nrows - row0);
-      if (lane < nr) pre(row0 + lane);
-      const int rb = lay.ptr_s[row0 + min(lane, nr - 1)];
-      const int seg_e = lay.tile_end[st];
-      const int seg_b = __shfl_sync(0xffffffffu, rb, 0);     // 4-aligned
-      int re = __shfl_down_sync(0xffffffffu, rb, 1);
-      if (lane >= nr - 1) re = seg_e;
-      const int nvec = (seg_e - seg_b + 3) >> 2;             // groups of 4 entries
-      // stage: lane handles groups g = lane, lane + 32, ... (kU at a time)
-      constexpr int kU = kStageUnroll;
-      for (int g0 = 0; g0 < nvec; g0 += kWarp * kU) {
-        int j[kU][4];
-        Vec4<VT> vv[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int g = g0 + u * kWarp + lane;
-          if (g < nvec) {
-            load_idx4(lay.idx_s + seg_b + 4 * g, j[u]);
-            vv[u].load(vals.s + seg_b + 4 * g);
-          }
-        }
-        PT x[kU][4];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int g = g0 + u * kWarp + lane;
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            x[u][e] = (g < nvec && seg_b + 4 * g + e < seg_e) ? PT(src(j[u][e])) : PT(0);
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int g = g0 + u * kWarp + lane;
-          if (g < nvec) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) smem[4 * g + e] = PT(vv[u].v[e]) * x[u][e];
-          }
-        }
+      // a group of nt <= tile_mult consecutive short tiles, staged as one segment
+      const int t0 = (item - lay.n_chunks) * lay.tile_mult;
+      const int nt = min(lay.tile_mult, lay.n_short_tiles - t0);
+      for (int r = t0 * kTileRows + lane; r < min((t0 + nt) * kTileRows, lay.nrows); r += kWarp)
+        pre(r);
+      // the tiles' row starts (requested into L1 for the row sums), ends and long-row masks
+      for (int m = 1; m < nt; ++m) {
+        const int row0 = (t0 + m) * kTileRows;
+        prefetch_l1(lay.ptr_s + row0 + min(lane, lay.nrows - 1 - row0));
       }
+      int te = 0;
+      uint32_t lmk = 0u;
+      if (lane < nt) {
+        te = lay.tile_end[t0 + lane];
+        lmk = lay.long_mask[t0 + lane];
+      }
+      const int rb0 = lay.ptr_s[t0 * kTileRows + min(lane, lay.nrows - 1 - t0 * kTileRows)];
+      const int seg_b = __shfl_sync(0xffffffffu, rb0, 0);     // 4-aligned
+      const int seg_e = __shfl_sync(0xffffffffu, te, nt - 1);
+      stage_segment<VT, PT>(lay, vals, src, smem, seg_b, seg_e);
       __syncwarp();
-      tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lay.long_mask[st], epi);
+#pragma unroll 1
+      for (int m = 0; m < nt; ++m) {
+        const int row0 = (t0 + m) * kTileRows;
+        const int nr = min(kTileRows, lay.nrows - row0);
+        const int rb = m == 0 ? rb0 : lay.ptr_s[row0 + min(lane, nr - 1)];
+        const int te_m = __shfl_sync(0xffffffffu, te, m);
+        const uint32_t lm_m = __shfl_sync(0xffffffffu, lmk, m);
+        int re = __shfl_down_sync(0xffffffffu, rb, 1);
+        if (lane >= nr - 1) re = te_m;
+        tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lm_m, epi);
+      }
       __syncwarp();
     }
   }

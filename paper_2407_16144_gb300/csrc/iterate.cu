@@ -25,8 +25,12 @@ namespace rh {
 
 namespace {
 
-template <int RHO2>
-__global__ void __launch_bounds__(kBlockThreads)
+// The FP64 iteration kernels are bound by the FP64 pipe; four resident CTAs per SM (128
+// registers a thread) keep it busy, and the register cap keeps the grid at that size.
+constexpr int kFp64BlocksPerSm = 4;
+
+template <int RHO2, bool GRP>
+__global__ void __launch_bounds__(kBlockThreads, kFp64BlocksPerSm)
 k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ xt,
            RowVecs v, Ctl *ctl, double *part, IterConsts ic) {
   extern __shared__ double smem[];
@@ -55,7 +59,7 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   const unsigned mmask = row_mmask(cert, move);
   auto gdone = [&](int grp) { store_group(al, smask, ws.group_part, grp); };
   auto gather = [&](int j) { return xt[j]; };
-  walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
+  walk_tiles<double, double, GRP>(lay, vals, gather, my, ws, epi, gdone);
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
     double r[13];
@@ -64,8 +68,8 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   }
 }
 
-template <int RHO2>
-__global__ void __launch_bounds__(kBlockThreads)
+template <int RHO2, bool GRP>
+__global__ void __launch_bounds__(kBlockThreads, kFp64BlocksPerSm)
 k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ ytv,
            ColVecs v, Ctl *ctl, double *part, IterConsts ic, int phase) {
   extern __shared__ double smem[];
@@ -116,7 +120,7 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   const unsigned mmask = col_mmask(cert, move);
   auto gdone = [&](int grp) { store_group(al, smask, ws.group_part, grp); };
   auto gather = [&](int j) { return ytv[j]; };
-  walk_tiles<double, double>(lay, vals, gather, my, ws, epi, gdone);
+  walk_tiles<double, double, GRP>(lay, vals, gather, my, ws, epi, gdone);
   if (check) tel_flush(ctl, tl);
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
@@ -135,25 +139,27 @@ __global__ void k_unscale(int n, int m, const double *e, const double *xs, const
 
 }  // namespace
 
+// GRP: the grouped walk for sides whose short tiles are walked several at a time.
 void launch_row_iter(cudaStream_t st, const SideStore &side, const double *xt, const RowVecs &v,
                      Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem) {
-  if (ic.rho2)
-    k_row_iter<1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl,
-                                                      part, ic);
-  else
-    k_row_iter<0><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl,
-                                                      part, ic);
+  auto go = [&](auto kern) {
+    kern<<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl, part, ic);
+  };
+  const bool grp = side.lay.tile_mult > 1;
+  if (ic.rho2) grp ? go(k_row_iter<1, true>) : go(k_row_iter<1, false>);
+  else grp ? go(k_row_iter<0, true>) : go(k_row_iter<0, false>);
 }
 
 void launch_col_iter(cudaStream_t st, const SideStore &side, const double *yt, const ColVecs &v,
                      Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem,
                      int phase) {
-  if (ic.rho2)
-    k_col_iter<1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, yt, v, ctl,
-                                                      part, ic, phase);
-  else
-    k_col_iter<0><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, yt, v, ctl,
-                                                      part, ic, phase);
+  auto go = [&](auto kern) {
+    kern<<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, yt, v, ctl, part, ic,
+                                            phase);
+  };
+  const bool grp = side.lay.tile_mult > 1;
+  if (ic.rho2) grp ? go(k_col_iter<1, true>) : go(k_col_iter<1, false>);
+  else grp ? go(k_col_iter<0, true>) : go(k_col_iter<0, false>);
 }
 
 void launch_unscale(cudaStream_t st, int n, int m, const double *e, const double *xs,
@@ -163,26 +169,34 @@ void launch_unscale(cudaStream_t st, int n, int m, const double *e, const double
 }
 
 void allow_large_smem(int bytes) {
-  cudaFuncSetAttribute(k_row_iter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_row_iter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void *k[] = {(const void *)k_row_iter<0, false>, (const void *)k_row_iter<1, false>,
+                     (const void *)k_col_iter<0, false>, (const void *)k_col_iter<1, false>,
+                     (const void *)k_row_iter<0, true>,  (const void *)k_row_iter<1, true>,
+                     (const void *)k_col_iter<0, true>,  (const void *)k_col_iter<1, true>};
+  for (const void *f : k) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// Resident CTAs per SM of the FP64 iteration kernels of one side (all instantiations).
+static int fp64_blocks_per_sm(const void *const *k, int nk, int smem) {
+  int mn = 1 << 30;
+  for (int i = 0; i < nk; ++i) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k[i], kBlockThreads, smem);
+    mn = b < mn ? b : mn;
+  }
+  return mn;
 }
 
 int row_iter_blocks_per_sm(int smem) {
-  int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_row_iter<0>, kBlockThreads, smem);
-  int b2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_row_iter<1>, kBlockThreads, smem);
-  return b < b2 ? b : b2;
+  const void *k[] = {(const void *)k_row_iter<0, false>, (const void *)k_row_iter<1, false>,
+                     (const void *)k_row_iter<0, true>, (const void *)k_row_iter<1, true>};
+  return fp64_blocks_per_sm(k, 4, smem);
 }
 
 int col_iter_blocks_per_sm(int smem) {
-  int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_col_iter<0>, kBlockThreads, smem);
-  int b2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_col_iter<1>, kBlockThreads, smem);
-  return b < b2 ? b : b2;
+  const void *k[] = {(const void *)k_col_iter<0, false>, (const void *)k_col_iter<1, false>,
+                     (const void *)k_col_iter<0, true>, (const void *)k_col_iter<1, true>};
+  return fp64_blocks_per_sm(k, 4, smem);
 }
 
 }  // namespace rh

@@ -42,7 +42,7 @@ struct F3 {
 // MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
 // MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
 // launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
-template <int RHO2, int MODE>
+template <int RHO2, int MODE, bool GRP>
 __global__ void __launch_bounds__(kBlockThreads)
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
@@ -189,7 +189,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       prefetch_l1(v.r0 + i);
       if (i >= m_eq) prefetch_l1(v.ylo + i);
     };
-    walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone, pre);
+    walk_tiles<float, float, GRP>(lay, v32, gB, my32, wb, epi, gdone, pre);
   }
   // the FP32 sums (zero in restart mode) are reduced over the warp in FP32, then widened
   unsigned prewarp = 0u;
@@ -209,7 +209,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
 }
 
 // MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
-template <int RHO2, int MODE>
+template <int RHO2, int MODE, bool GRP>
 __global__ void __launch_bounds__(kBlockThreads)
 k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
@@ -366,7 +366,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       prefetch_l1(v.xlo + j);
       prefetch_l1(v.xhi + j);
     };
-    walk_tiles<float, float>(lay, v32, gB, my32, wb, epi, gdone, pre);
+    walk_tiles<float, float, GRP>(lay, v32, gB, my32, wb, epi, gdone, pre);
     if (check) tel_flush(ctl, tl);
   }
   unsigned prewarp = 0u;
@@ -404,43 +404,40 @@ __global__ void k_zero_f32(int n, float *x) {
 
 }  // namespace
 
+// The restart-mode kernel (MODE 1) of each stage is launched first and returns at entry unless
+// the stage needs it; the ordinary kernel (MODE 0) follows, in the ungrouped instantiation when
+// the side walks one short tile per item.
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int smem) {
+  auto go = [&](auto kern, int sm) {
+    kern<<<grid, kBlockThreads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dxt,
+                                          dxt64, x0, ctl, part, ic);
+  };
+  const bool grp = side.lay.tile_mult > 1;
   if (ic.rho2) {
-    k_row_iter_mx<1, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dxt, dxt64, x0, ctl,
-                                                            part, ic);
-    k_row_iter_mx<1, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dxt, dxt64, x0, ctl,
-                                                            part, ic);
+    go(k_row_iter_mx<1, 1, true>, smem);
+    grp ? go(k_row_iter_mx<1, 0, true>, smem / 2) : go(k_row_iter_mx<1, 0, false>, smem / 2);
   } else {
-    k_row_iter_mx<0, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dxt, dxt64, x0, ctl,
-                                                            part, ic);
-    k_row_iter_mx<0, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dxt, dxt64, x0, ctl,
-                                                            part, ic);
+    go(k_row_iter_mx<0, 1, true>, smem);
+    grp ? go(k_row_iter_mx<0, 0, true>, smem / 2) : go(k_row_iter_mx<0, 0, false>, smem / 2);
   }
 }
 
 void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx &v,
                         const float *dyt, const double *dyt64, const double *y0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int smem, int phase) {
+  auto go = [&](auto kern, int sm) {
+    kern<<<grid, kBlockThreads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dyt,
+                                          dyt64, y0, ctl, part, ic, phase);
+  };
+  const bool grp = side.lay.tile_mult > 1;
   if (ic.rho2) {
-    k_col_iter_mx<1, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dyt, dyt64, y0, ctl,
-                                                            part, ic, phase);
-    k_col_iter_mx<1, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dyt, dyt64, y0, ctl,
-                                                            part, ic, phase);
+    go(k_col_iter_mx<1, 1, true>, smem);
+    grp ? go(k_col_iter_mx<1, 0, true>, smem / 2) : go(k_col_iter_mx<1, 0, false>, smem / 2);
   } else {
-    k_col_iter_mx<0, 1><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dyt, dyt64, y0, ctl,
-                                                            part, ic, phase);
-    k_col_iter_mx<0, 0><<<grid, kBlockThreads, smem / 2, st>>>(side.lay, side.v64, side.v32, side.wa,
-                                                            side.wb, v, dyt, dyt64, y0, ctl,
-                                                            part, ic, phase);
+    go(k_col_iter_mx<0, 1, true>, smem);
+    grp ? go(k_col_iter_mx<0, 0, true>, smem / 2) : go(k_col_iter_mx<0, 0, false>, smem / 2);
   }
 }
 
@@ -457,26 +454,28 @@ void zero_f32(cudaStream_t st, int n, float *x) {
 }
 
 void allow_large_smem_mx(int bytes) {
-  cudaFuncSetAttribute(k_row_iter_mx<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_row_iter_mx<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_row_iter_mx<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_row_iter_mx<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter_mx<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter_mx<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter_mx<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_col_iter_mx<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void *k[] = {
+      (const void *)k_row_iter_mx<0, 0, false>, (const void *)k_row_iter_mx<1, 0, false>,
+      (const void *)k_row_iter_mx<0, 0, true>,  (const void *)k_row_iter_mx<1, 0, true>,
+      (const void *)k_row_iter_mx<0, 1, true>,  (const void *)k_row_iter_mx<1, 1, true>,
+      (const void *)k_col_iter_mx<0, 0, false>, (const void *)k_col_iter_mx<1, 0, false>,
+      (const void *)k_col_iter_mx<0, 0, true>,  (const void *)k_col_iter_mx<1, 0, true>,
+      (const void *)k_col_iter_mx<0, 1, true>,  (const void *)k_col_iter_mx<1, 1, true>};
+  for (const void *f : k) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// Blocks per SM of the ordinary-iteration kernels (the restart kernels run with the same grid;
-// they are resident-limited too but run rarely).
 int iter_mx_blocks_per_sm(int smem) {
-  int b[4] = {0, 0, 0, 0};
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], k_row_iter_mx<0, 0>, kBlockThreads, smem / 2);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], k_row_iter_mx<1, 0>, kBlockThreads, smem / 2);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], k_col_iter_mx<0, 0>, kBlockThreads, smem / 2);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[3], k_col_iter_mx<1, 0>, kBlockThreads, smem / 2);
-  int mn = b[0];
-  for (int i = 1; i < 4; ++i) mn = b[i] < mn ? b[i] : mn;
+  const void *k[] = {
+      (const void *)k_row_iter_mx<0, 0, false>, (const void *)k_row_iter_mx<1, 0, false>,
+      (const void *)k_row_iter_mx<0, 0, true>,  (const void *)k_row_iter_mx<1, 0, true>,
+      (const void *)k_col_iter_mx<0, 0, false>, (const void *)k_col_iter_mx<1, 0, false>,
+      (const void *)k_col_iter_mx<0, 0, true>,  (const void *)k_col_iter_mx<1, 0, true>};
+  int mn = 1 << 30;
+  for (const void *f : k) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlockThreads, smem / 2);
+    mn = b < mn ? b : mn;
+  }
   return mn;
 }
 

@@ -419,9 +419,29 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   const long long nnz_s = align4(cur) + 4, nnz_l = align4(cl) + kChunk;
   if (nnz_s > INT_MAX || nnz_l > INT_MAX) return cudaErrorInvalidValue;
   const int nlong = (int)long_rows.size(), nch = (int)chunk_row.size();
+  // Tiles per work item: where tiles are short (a few entries per row), M consecutive tiles are
+  // staged as one segment, so that each warp's chain of dependent loads carries M tiles' bytes.
+  // M is the largest of kMaxTileMult, ..., 2 whose mean group segment fits one staging round
+  // (128 * kStageUnroll entries) and whose longest fits the staging budget; else 1.
+  int mult = 1;
+  for (int cand = kMaxTileMult; cand >= 2 && mult == 1; cand /= 2) {
+    if (ntiles < 2 * cand) continue;
+    if (align4(cur) * cand > (long long)ntiles * kWarp * kStageUnroll * 4) continue;
+    long long mx = 0;
+    for (int t0 = 0; t0 < ntiles; t0 += cand) {
+      const int t1 = std::min(ntiles, t0 + cand) - 1;
+      mx = std::max(mx, (long long)tile_end[t1] - ptr_s[(size_t)t0 * kTileRows]);
+    }
+    if (mx <= kSegBudget) {
+      mult = cand;
+      maxseg = mx;
+    }
+  }
   s.lay.nrows = nrows;
   s.lay.seg = (int)align4(maxseg) + 4;
   s.lay.n_short_tiles = ntiles;
+  s.lay.tile_mult = mult;
+  s.lay.n_tile_groups = (ntiles + mult - 1) / mult;
   s.lay.n_long = nlong;
   s.lay.n_long_tiles = (nlong + kTileRows - 1) / kTileRows;
   s.lay.n_chunks = nch;
