@@ -639,8 +639,9 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   allow_large_smem_setup(kMaxTileSmem);
   allow_large_smem_mx(kMaxTileSmem);
   if (h->mixed) {
-    h->grid_row = tile_grid(h->rows.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_row));
-    h->grid_col = tile_grid(h->cols.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_col));
+    const bool gr = h->rows.lay.tile_mult > 1, gc = h->cols.lay.tile_mult > 1;
+    h->grid_row = tile_grid(h->rows.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_row, gr, gc));
+    h->grid_col = tile_grid(h->cols.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_col, gr, gc));
   } else {
     h->grid_row = tile_grid(h->rows.lay, h->sm_count, row_iter_blocks_per_sm(h->smem_row));
     h->grid_col = tile_grid(h->cols.lay, h->sm_count, col_iter_blocks_per_sm(h->smem_col));

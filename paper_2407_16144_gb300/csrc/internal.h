@@ -143,7 +143,9 @@ void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const dou
                        double *yo, double *yt64);
 void zero_f32(cudaStream_t st, int n, float *x);
 void allow_large_smem_mx(int bytes);
-int iter_mx_blocks_per_sm(int smem);
+// Resident CTAs per SM of the ordinary mixed kernels that a handle launches (grp_*: the grouped
+// walk instantiation of that side).
+int iter_mx_blocks_per_sm(int smem, bool grp_row, bool grp_col);
 // opt in to dynamic shared memory above 48 KB for the tile kernels
 void allow_large_smem(int bytes);
 void allow_large_smem_setup(int bytes);

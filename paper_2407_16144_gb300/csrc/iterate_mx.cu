@@ -464,12 +464,13 @@ void allow_large_smem_mx(int bytes) {
   for (const void *f : k) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-int iter_mx_blocks_per_sm(int smem) {
+int iter_mx_blocks_per_sm(int smem, bool grp_row, bool grp_col) {
+  // the ordinary kernels that will be launched (both reflection settings)
   const void *k[] = {
-      (const void *)k_row_iter_mx<0, 0, false>, (const void *)k_row_iter_mx<1, 0, false>,
-      (const void *)k_row_iter_mx<0, 0, true>,  (const void *)k_row_iter_mx<1, 0, true>,
-      (const void *)k_col_iter_mx<0, 0, false>, (const void *)k_col_iter_mx<1, 0, false>,
-      (const void *)k_col_iter_mx<0, 0, true>,  (const void *)k_col_iter_mx<1, 0, true>};
+      grp_row ? (const void *)k_row_iter_mx<0, 0, true> : (const void *)k_row_iter_mx<0, 0, false>,
+      grp_row ? (const void *)k_row_iter_mx<1, 0, true> : (const void *)k_row_iter_mx<1, 0, false>,
+      grp_col ? (const void *)k_col_iter_mx<0, 0, true> : (const void *)k_col_iter_mx<0, 0, false>,
+      grp_col ? (const void *)k_col_iter_mx<1, 0, true> : (const void *)k_col_iter_mx<1, 0, false>};
   int mn = 1 << 30;
   for (const void *f : k) {
     int b = 0;
