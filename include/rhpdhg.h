@@ -230,6 +230,15 @@ int rhpdhg_get_scaling(const rhpdhg_handle *h, double *D, double *E, double *eta
 int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t capacity,
                      int64_t *count);
 
+/* Launch geometry and walk layout chosen at create (for inspection and tests); out receives
+ * RHPDHG_LAYOUT_FIELDS values: CTAs of the row kernels and of the column kernels; short tiles
+ * walked per work item on K^ and on K^T (1, 2 or 4); long rows of K^ and of K^T; their chunks on
+ * K^ and on K^T; the staging stride (entries per warp) of K^ and of K^T.
+ * capacity: entries available at out.  Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG for a NULL
+ * handle or out, or capacity < RHPDHG_LAYOUT_FIELDS. */
+#define RHPDHG_LAYOUT_FIELDS 10
+int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity);
+
 /* With params.profile = 1: average device time (ms) per launch of the row-side kernel
  * (K x~ product + dual step) and of the column-side kernel (K^T y~ product + primal step) over
  * the last solve, their launch counts, and the algorithmic bytes one launch of each moves. */

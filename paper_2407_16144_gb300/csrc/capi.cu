@@ -867,6 +867,16 @@ int rhpdhg_get_scaling(const rhpdhg_handle *hc, double *D, double *E, double *et
   return RHPDHG_OK;
 }
 
+int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity) {
+  if (!h || !out || capacity < RHPDHG_LAYOUT_FIELDS) return RHPDHG_ERR_INVALID_ARG;
+  const SideLayout &r = h->rows.lay, &c = h->cols.lay;
+  const int64_t v[RHPDHG_LAYOUT_FIELDS] = {h->grid_row,  h->grid_col,  r.tile_mult, c.tile_mult,
+                                           r.n_long,     c.n_long,     r.n_chunks,  c.n_chunks,
+                                           r.seg,        c.seg};
+  for (int i = 0; i < RHPDHG_LAYOUT_FIELDS; ++i) out[i] = v[i];
+  return RHPDHG_OK;
+}
+
 int rhpdhg_get_trace(const rhpdhg_handle *hc, rhpdhg_trace_rec *recs, int64_t capacity,
                      int64_t *count) {
   rhpdhg_handle *h = const_cast<rhpdhg_handle *>(hc);

@@ -73,7 +73,7 @@ class rhpdhg_trace_rec(C.Structure):
 
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
             "rhpdhg_cancel", "rhpdhg_free", "rhpdhg_last_error", "rhpdhg_get_state",
-            "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_kernel_times",
+            "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_get_layout", "rhpdhg_kernel_times",
             "rhpdhg_launch_count", "rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc",
             "rhpdhg_batch_create", "rhpdhg_batch_add", "rhpdhg_batch_step", "rhpdhg_batch_poll",
             "rhpdhg_batch_remove", "rhpdhg_batch_slot_status", "rhpdhg_batch_free_bytes",
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "rhpdhg_get_scaling": (C.c_int, [H, _dp, _dp, _dp, _dp, _dp]),
         "rhpdhg_get_trace": (C.c_int, [H, C.POINTER(rhpdhg_trace_rec), C.c_int64,
                                        C.POINTER(C.c_int64)]),
+        "rhpdhg_get_layout": (C.c_int, [H, C.POINTER(C.c_int64), C.c_int32]),
         "rhpdhg_kernel_times": (C.c_int, [H, _dp, _dp, C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int64), _dp, _dp]),
         "rhpdhg_launch_count": (C.c_int64, [H]),
@@ -191,6 +192,16 @@ def rhpdhg_get_trace(h, capacity: int):
     cnt = C.c_int64()
     rc = load().rhpdhg_get_trace(h, recs, capacity, C.byref(cnt))
     return rc, [recs[i] for i in range(min(cnt.value, capacity))]
+
+
+LAYOUT_FIELDS = ("grid_row", "grid_col", "tile_mult_row", "tile_mult_col", "long_rows_row",
+                 "long_rows_col", "chunks_row", "chunks_col", "seg_row", "seg_col")
+
+
+def rhpdhg_get_layout(h):
+    out = (C.c_int64 * len(LAYOUT_FIELDS))()
+    rc = load().rhpdhg_get_layout(h, out, len(LAYOUT_FIELDS))
+    return rc, dict(zip(LAYOUT_FIELDS, list(out)))
 
 
 def rhpdhg_kernel_times(h):
@@ -648,6 +659,12 @@ class Solver:
         _check(rc, self.h, "rhpdhg_get_trace")
         return [(r.t, r.epoch, r.k, r.fpr_sq, bool(r.restart), r.omega, r.active, r.changed,
                  r.retries) for r in recs]
+
+    def layout(self):
+        """Launch geometry and walk layout chosen at create (see LAYOUT_FIELDS)."""
+        rc, d = rhpdhg_get_layout(self.h)
+        _check(rc, self.h, "rhpdhg_get_layout")
+        return d
 
     def kernel_times(self):
         rc, d = rhpdhg_kernel_times(self.h)
