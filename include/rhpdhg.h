@@ -233,10 +233,13 @@ int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t cap
 /* Launch geometry and walk layout chosen at create (for inspection and tests); out receives
  * RHPDHG_LAYOUT_FIELDS values: CTAs of the row kernels and of the column kernels; short tiles
  * walked per work item on K^ and on K^T (1, 2 or 4); long rows of K^ and of K^T; their chunks on
- * K^ and on K^T; the staging stride (entries per warp) of K^ and of K^T.
+ * K^ and on K^T; the staging stride (entries per warp) of K^ and of K^T; the walk of the
+ * ordinary mixed-precision kernels on K^ and on K^T (0 = one tile per item, 1 = one tile per
+ * item with twice the loads in flight per staging round, 2 = groups of tiles per item; 0 for
+ * FP64 handles).
  * capacity: entries available at out.  Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG for a NULL
  * handle or out, or capacity < RHPDHG_LAYOUT_FIELDS. */
-#define RHPDHG_LAYOUT_FIELDS 10
+#define RHPDHG_LAYOUT_FIELDS 12
 int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity);
 
 /* With params.profile = 1: average device time (ms) per launch of the row-side kernel

@@ -639,9 +639,20 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   allow_large_smem_setup(kMaxTileSmem);
   allow_large_smem_mx(kMaxTileSmem);
   if (h->mixed) {
-    const bool gr = h->rows.lay.tile_mult > 1, gc = h->cols.lay.tile_mult > 1;
-    h->grid_row = tile_grid(h->rows.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_row, gr, gc));
-    h->grid_col = tile_grid(h->cols.lay, h->sm_count, iter_mx_blocks_per_sm(h->smem_col, gr, gc));
+    SideLayout &lr = h->rows.lay, &lc = h->cols.lay;
+    lr.walk = lr.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
+    lc.walk = lc.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
+    // The row kernels stage twice as many groups per round (fewer dependent rounds, more
+    // registers) when their tiles are long and the grid stays set by the tile count at the
+    // wider kernel's residency, so that the registers cost no CTAs.
+    if (lr.walk == kWalkPlain && lr.n_short_tiles > 0 &&
+        h->rows.nnz_short > (long long)lr.n_short_tiles * kWarp * kStageUnroll * 4) {
+      const int bw = iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide);
+      const long long need = ((long long)lr.total_items() + kBlockWarps - 1) / kBlockWarps;
+      if (bw > 0 && need <= (long long)bw * h->sm_count) lr.walk = kWalkWide;
+    }
+    h->grid_row = tile_grid(lr, h->sm_count, iter_mx_blocks_per_sm(h->smem_row, true, lr.walk));
+    h->grid_col = tile_grid(lc, h->sm_count, iter_mx_blocks_per_sm(h->smem_col, false, lc.walk));
   } else {
     h->grid_row = tile_grid(h->rows.lay, h->sm_count, row_iter_blocks_per_sm(h->smem_row));
     h->grid_col = tile_grid(h->cols.lay, h->sm_count, col_iter_blocks_per_sm(h->smem_col));
@@ -872,7 +883,7 @@ int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity) {
   const SideLayout &r = h->rows.lay, &c = h->cols.lay;
   const int64_t v[RHPDHG_LAYOUT_FIELDS] = {h->grid_row,  h->grid_col,  r.tile_mult, c.tile_mult,
                                            r.n_long,     c.n_long,     r.n_chunks,  c.n_chunks,
-                                           r.seg,        c.seg};
+                                           r.seg,        c.seg,        r.walk,      c.walk};
   for (int i = 0; i < RHPDHG_LAYOUT_FIELDS; ++i) out[i] = v[i];
   return RHPDHG_OK;
 }

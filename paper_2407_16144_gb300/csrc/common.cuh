@@ -34,6 +34,14 @@ constexpr int kChunk = 256;            // entries per long-row chunk (8 per lane
 constexpr int kStageUnroll = 2;        // 4-entry groups staged per lane per round
 constexpr int kMaxTileMult = 4;        // most short tiles walked as one work item
 
+// Walk instantiations of the ordinary mixed kernels: one tile per item; one tile per item with
+// twice the staging unroll (row side only: long tiles, grid set by the tile count); groups of
+// tiles per item (any layout).
+enum WalkKind : int { kWalkPlain = 0, kWalkWide = 1, kWalkGrouped = 2 };
+__host__ __device__ constexpr int walk_unroll(int walk) {
+  return walk == kWalkWide ? 2 * kStageUnroll : kStageUnroll;
+}
+
 // Infeasibility certificate candidates (rhpdhg_result.cert_source).
 enum CertSource : int { kCertNone = 0, kCertRestartPoint = 1, kCertCheck = 2, kCertAnchorMove = 3 };
 
@@ -67,6 +75,7 @@ struct SideLayout {
   const int *chunk_ptr = nullptr;   // n_long + 1: chunks of long row i are [chunk_ptr[i], ..[i+1])
   const int *chunk_row = nullptr;   // n_chunks: long-row index of each chunk
   int tile_mult = 1;         // consecutive short tiles per work item (1 .. kMaxTileMult)
+  int walk = 0;              // instantiation of the ordinary mixed kernels' walk (kWalk*)
   int n_tile_groups = 0;     // ceil(n_short_tiles / tile_mult)
   __host__ __device__ int total_items() const { return n_chunks + n_tile_groups; }
 };
@@ -468,13 +477,14 @@ struct NoPrefetch {
 };
 
 // Stage the products of the segment [seg_b, seg_e) (seg_b 4-aligned) in smem[0, ...): lane
-// handles 4-entry groups g = lane, lane + 32, ..., kStageUnroll at a time.
-template <typename VT, typename PT, typename Src>
+// handles 4-entry groups g = lane, lane + 32, ..., U at a time (more loads in flight per round,
+// more registers).
+template <typename VT, typename PT, int U, typename Src>
 __device__ __forceinline__ void stage_segment(const SideLayout &lay, const SideVals<VT> vals,
                                               const Src &src, PT *smem, int seg_b, int seg_e) {
   const int lane = threadIdx.x & 31;
   const int nvec = (seg_e - seg_b + 3) >> 2;             // groups of 4 entries
-  constexpr int kU = kStageUnroll;
+  constexpr int kU = U;
   for (int g0 = 0; g0 < nvec; g0 += kWarp * kU) {
     int j[kU][4];
     Vec4<VT> vv[kU];
@@ -507,7 +517,7 @@ __device__ __forceinline__ void stage_segment(const SideLayout &lay, const SideV
 
 // One short tile st of walk_tiles (tile_mult == 1): stage its segment, then lane r sums row r
 // and runs its epilogue.
-template <typename VT, typename PT, typename Src, typename Epi, typename Pre>
+template <typename VT, typename PT, int U, typename Src, typename Epi, typename Pre>
 __device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<VT> vals,
                                           const Src &src, PT *smem, Epi &epi, const Pre &pre,
                                           int st) {
@@ -520,7 +530,7 @@ __device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<
   const int seg_b = __shfl_sync(0xffffffffu, rb, 0);     // 4-aligned
   int re = __shfl_down_sync(0xffffffffu, rb, 1);
   if (lane >= nr - 1) re = seg_e;
-  stage_segment<VT, PT>(lay, vals, src, smem, seg_b, seg_e);
+  stage_segment<VT, PT, U>(lay, vals, src, smem, seg_b, seg_e);
   __syncwarp();
   tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lay.long_mask[st], epi);
   __syncwarp();
@@ -530,8 +540,8 @@ __device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<
 // registers); GROUPED = true walks any layout.
 // pre(row) is called by the lane of each short-tile row before the tile's entries are staged,
 // so that what the row's epilogue will read can be requested while the staging round trips run.
-template <typename VT, typename PT, bool GROUPED = true, typename Src, typename Epi,
-          typename GroupDone, typename Pre = NoPrefetch>
+template <typename VT, typename PT, bool GROUPED = true, int U = kStageUnroll, typename Src,
+          typename Epi, typename GroupDone, typename Pre = NoPrefetch>
 __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals<VT> vals,
                                            const Src &src, PT *smem, const WalkScratch ws,
                                            Epi &epi, GroupDone &gdone,
@@ -544,7 +554,7 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
     if (item < lay.n_chunks) {
       walk_chunk<VT, PT>(lay, vals, src, ws, epi, gdone, item);
     } else if constexpr (!GROUPED) {
-      walk_tile<VT, PT>(lay, vals, src, smem, epi, pre, item - lay.n_chunks);
+      walk_tile<VT, PT, U>(lay, vals, src, smem, epi, pre, item - lay.n_chunks);
     } else {
       // a group of nt <= tile_mult consecutive short tiles, staged as one segment
       const int t0 = (item - lay.n_chunks) * lay.tile_mult;
@@ -565,7 +575,7 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
       const int rb0 = lay.ptr_s[t0 * kTileRows + min(lane, lay.nrows - 1 - t0 * kTileRows)];
       const int seg_b = __shfl_sync(0xffffffffu, rb0, 0);     // 4-aligned
       const int seg_e = __shfl_sync(0xffffffffu, te, nt - 1);
-      stage_segment<VT, PT>(lay, vals, src, smem, seg_b, seg_e);
+      stage_segment<VT, PT, U>(lay, vals, src, smem, seg_b, seg_e);
       __syncwarp();
 #pragma unroll 1
       for (int m = 0; m < nt; ++m) {

@@ -143,9 +143,9 @@ void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const dou
                        double *yo, double *yt64);
 void zero_f32(cudaStream_t st, int n, float *x);
 void allow_large_smem_mx(int bytes);
-// Resident CTAs per SM of the ordinary mixed kernels that a handle launches (grp_*: the grouped
-// walk instantiation of that side).
-int iter_mx_blocks_per_sm(int smem, bool grp_row, bool grp_col);
+// Resident CTAs per SM of the ordinary mixed kernels of one side (row: K^, else K^T) in one
+// walk instantiation (kWalk*).
+int iter_mx_blocks_per_sm(int smem, bool row, int walk);
 // opt in to dynamic shared memory above 48 KB for the tile kernels
 void allow_large_smem(int bytes);
 void allow_large_smem_setup(int bytes);

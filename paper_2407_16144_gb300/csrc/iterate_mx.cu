@@ -42,7 +42,7 @@ struct F3 {
 // MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
 // MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
 // launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
-template <int RHO2, int MODE, bool GRP>
+template <int RHO2, int MODE, int WALK>
 __global__ void __launch_bounds__(kBlockThreads)
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
@@ -189,7 +189,8 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       prefetch_l1(v.r0 + i);
       if (i >= m_eq) prefetch_l1(v.ylo + i);
     };
-    walk_tiles<float, float, GRP>(lay, v32, gB, my32, wb, epi, gdone, pre);
+    walk_tiles<float, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
+                                                                       epi, gdone, pre);
   }
   // the FP32 sums (zero in restart mode) are reduced over the warp in FP32, then widened
   unsigned prewarp = 0u;
@@ -209,7 +210,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
 }
 
 // MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
-template <int RHO2, int MODE, bool GRP>
+template <int RHO2, int MODE, int WALK>
 __global__ void __launch_bounds__(kBlockThreads)
 k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
@@ -366,7 +367,8 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       prefetch_l1(v.xlo + j);
       prefetch_l1(v.xhi + j);
     };
-    walk_tiles<float, float, GRP>(lay, v32, gB, my32, wb, epi, gdone, pre);
+    walk_tiles<float, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
+                                                                       epi, gdone, pre);
     if (check) tel_flush(ctl, tl);
   }
   unsigned prewarp = 0u;
@@ -405,8 +407,8 @@ __global__ void k_zero_f32(int n, float *x) {
 }  // namespace
 
 // The restart-mode kernel (MODE 1) of each stage is launched first and returns at entry unless
-// the stage needs it; the ordinary kernel (MODE 0) follows, in the ungrouped instantiation when
-// the side walks one short tile per item.
+// the stage needs it; the ordinary kernel (MODE 0) follows, in the instantiation of the side's
+// walk (SideLayout::walk).
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int smem) {
@@ -414,13 +416,17 @@ void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx 
     kern<<<grid, kBlockThreads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dxt,
                                           dxt64, x0, ctl, part, ic);
   };
-  const bool grp = side.lay.tile_mult > 1;
+  const int w = side.lay.walk;
   if (ic.rho2) {
-    go(k_row_iter_mx<1, 1, true>, smem);
-    grp ? go(k_row_iter_mx<1, 0, true>, smem / 2) : go(k_row_iter_mx<1, 0, false>, smem / 2);
+    go(k_row_iter_mx<1, 1, kWalkGrouped>, smem);
+    if (w == kWalkGrouped) go(k_row_iter_mx<1, 0, kWalkGrouped>, smem / 2);
+    else if (w == kWalkWide) go(k_row_iter_mx<1, 0, kWalkWide>, smem / 2);
+    else go(k_row_iter_mx<1, 0, kWalkPlain>, smem / 2);
   } else {
-    go(k_row_iter_mx<0, 1, true>, smem);
-    grp ? go(k_row_iter_mx<0, 0, true>, smem / 2) : go(k_row_iter_mx<0, 0, false>, smem / 2);
+    go(k_row_iter_mx<0, 1, kWalkGrouped>, smem);
+    if (w == kWalkGrouped) go(k_row_iter_mx<0, 0, kWalkGrouped>, smem / 2);
+    else if (w == kWalkWide) go(k_row_iter_mx<0, 0, kWalkWide>, smem / 2);
+    else go(k_row_iter_mx<0, 0, kWalkPlain>, smem / 2);
   }
 }
 
@@ -431,13 +437,13 @@ void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx 
     kern<<<grid, kBlockThreads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dyt,
                                           dyt64, y0, ctl, part, ic, phase);
   };
-  const bool grp = side.lay.tile_mult > 1;
+  const bool grp = side.lay.walk == kWalkGrouped;
   if (ic.rho2) {
-    go(k_col_iter_mx<1, 1, true>, smem);
-    grp ? go(k_col_iter_mx<1, 0, true>, smem / 2) : go(k_col_iter_mx<1, 0, false>, smem / 2);
+    go(k_col_iter_mx<1, 1, kWalkGrouped>, smem);
+    grp ? go(k_col_iter_mx<1, 0, kWalkGrouped>, smem / 2) : go(k_col_iter_mx<1, 0, kWalkPlain>, smem / 2);
   } else {
-    go(k_col_iter_mx<0, 1, true>, smem);
-    grp ? go(k_col_iter_mx<0, 0, true>, smem / 2) : go(k_col_iter_mx<0, 0, false>, smem / 2);
+    go(k_col_iter_mx<0, 1, kWalkGrouped>, smem);
+    grp ? go(k_col_iter_mx<0, 0, kWalkGrouped>, smem / 2) : go(k_col_iter_mx<0, 0, kWalkPlain>, smem / 2);
   }
 }
 
@@ -455,22 +461,32 @@ void zero_f32(cudaStream_t st, int n, float *x) {
 
 void allow_large_smem_mx(int bytes) {
   const void *k[] = {
-      (const void *)k_row_iter_mx<0, 0, false>, (const void *)k_row_iter_mx<1, 0, false>,
-      (const void *)k_row_iter_mx<0, 0, true>,  (const void *)k_row_iter_mx<1, 0, true>,
-      (const void *)k_row_iter_mx<0, 1, true>,  (const void *)k_row_iter_mx<1, 1, true>,
-      (const void *)k_col_iter_mx<0, 0, false>, (const void *)k_col_iter_mx<1, 0, false>,
-      (const void *)k_col_iter_mx<0, 0, true>,  (const void *)k_col_iter_mx<1, 0, true>,
-      (const void *)k_col_iter_mx<0, 1, true>,  (const void *)k_col_iter_mx<1, 1, true>};
+      (const void *)k_row_iter_mx<0, 0, kWalkPlain>,   (const void *)k_row_iter_mx<1, 0, kWalkPlain>,
+      (const void *)k_row_iter_mx<0, 0, kWalkWide>,    (const void *)k_row_iter_mx<1, 0, kWalkWide>,
+      (const void *)k_row_iter_mx<0, 0, kWalkGrouped>, (const void *)k_row_iter_mx<1, 0, kWalkGrouped>,
+      (const void *)k_row_iter_mx<0, 1, kWalkGrouped>, (const void *)k_row_iter_mx<1, 1, kWalkGrouped>,
+      (const void *)k_col_iter_mx<0, 0, kWalkPlain>,   (const void *)k_col_iter_mx<1, 0, kWalkPlain>,
+      (const void *)k_col_iter_mx<0, 0, kWalkGrouped>, (const void *)k_col_iter_mx<1, 0, kWalkGrouped>,
+      (const void *)k_col_iter_mx<0, 1, kWalkGrouped>, (const void *)k_col_iter_mx<1, 1, kWalkGrouped>};
   for (const void *f : k) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-int iter_mx_blocks_per_sm(int smem, bool grp_row, bool grp_col) {
-  // the ordinary kernels that will be launched (both reflection settings)
-  const void *k[] = {
-      grp_row ? (const void *)k_row_iter_mx<0, 0, true> : (const void *)k_row_iter_mx<0, 0, false>,
-      grp_row ? (const void *)k_row_iter_mx<1, 0, true> : (const void *)k_row_iter_mx<1, 0, false>,
-      grp_col ? (const void *)k_col_iter_mx<0, 0, true> : (const void *)k_col_iter_mx<0, 0, false>,
-      grp_col ? (const void *)k_col_iter_mx<1, 0, true> : (const void *)k_col_iter_mx<1, 0, false>};
+int iter_mx_blocks_per_sm(int smem, bool row, int walk) {
+  // the ordinary kernels of one side in one walk instantiation (both reflection settings)
+  const void *k[2];
+  if (row) {
+    k[0] = walk == kWalkGrouped ? (const void *)k_row_iter_mx<0, 0, kWalkGrouped>
+           : walk == kWalkWide  ? (const void *)k_row_iter_mx<0, 0, kWalkWide>
+                                : (const void *)k_row_iter_mx<0, 0, kWalkPlain>;
+    k[1] = walk == kWalkGrouped ? (const void *)k_row_iter_mx<1, 0, kWalkGrouped>
+           : walk == kWalkWide  ? (const void *)k_row_iter_mx<1, 0, kWalkWide>
+                                : (const void *)k_row_iter_mx<1, 0, kWalkPlain>;
+  } else {
+    k[0] = walk == kWalkGrouped ? (const void *)k_col_iter_mx<0, 0, kWalkGrouped>
+                                : (const void *)k_col_iter_mx<0, 0, kWalkPlain>;
+    k[1] = walk == kWalkGrouped ? (const void *)k_col_iter_mx<1, 0, kWalkGrouped>
+                                : (const void *)k_col_iter_mx<1, 0, kWalkPlain>;
+  }
   int mn = 1 << 30;
   for (const void *f : k) {
     int b = 0;

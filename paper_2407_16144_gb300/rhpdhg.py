@@ -195,7 +195,8 @@ def rhpdhg_get_trace(h, capacity: int):
 
 
 LAYOUT_FIELDS = ("grid_row", "grid_col", "tile_mult_row", "tile_mult_col", "long_rows_row",
-                 "long_rows_col", "chunks_row", "chunks_col", "seg_row", "seg_col")
+                 "long_rows_col", "chunks_row", "chunks_col", "seg_row", "seg_col", "walk_row",
+                 "walk_col")
 
 
 def rhpdhg_get_layout(h):

@@ -106,6 +106,17 @@ def test_walk_layout(rh, case):
     if case == "c3_small":
         assert lay["tile_mult_col"] == 2
     assert lay["grid_row"] >= 1 and lay["grid_col"] >= 1
+    assert lay["walk_row"] == 0 and lay["walk_col"] == 0          # FP64 handle
+    with rh.Solver(lp, precision=1) as s:
+        mx = s.layout()
+    # mixed: grouped walks where tiles are grouped; the row side takes the wide staging round
+    # only with long tiles and a grid set by the tile count
+    assert (mx["walk_col"] == 2) == (mx["tile_mult_col"] > 1)
+    assert (mx["walk_row"] == 2) == (mx["tile_mult_row"] > 1)
+    if mx["walk_row"] == 1:
+        assert A.nnz > 256 * ((A.shape[0] + 31) // 32)
+    if case == "c2_small":
+        assert mx["walk_row"] == 1
 
 
 @pytest.mark.parametrize("case", list(CASES))
