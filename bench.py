@@ -58,22 +58,32 @@ def parse():
 
 # DRAM bytes (read + write) per launch of the mixed-precision ordinary-iteration kernels on the
 # 100k x 250k LP, from one ncu capture (profiles/k_iter_mx_c2.md) of the kernel sources with
-# this digest.  Reported as roofline.traffic only while those sources are unchanged.
+# this digest (their code with comments and whitespace removed).  Reported as roofline.traffic
+# only while that code is unchanged.
 KERNEL_SOURCES = ["paper_2407_16144_gb300/csrc/iterate_mx.cu", "paper_2407_16144_gb300/csrc/common.cuh",
                   "paper_2407_16144_gb300/csrc/iter_common.cuh", "paper_2407_16144_gb300/csrc/internal.h"]
 PROFILED_TRAFFIC = {
-    "digest": "544b4017a54998ab",
+    "digest": "d00bfb682069c2b7",
     "column kernel (K^T y~ + primal step)": 27863296,
     "row kernel (K x~ + dual step)": 23753088,
 }
+
+
+def code_text(src: str) -> str:
+    """C/C++/CUDA source with comments removed and whitespace runs collapsed (string literals
+    kept as they are), so that a digest follows the code only."""
+    import re
+    tok = re.compile(r'"(?:\\.|[^"\\])*"|/\*.*?\*/|//[^\n]*', re.S)
+    out = tok.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", src)
+    return " ".join(out.split())
 
 
 def kernel_digest():
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f)) as fh:
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

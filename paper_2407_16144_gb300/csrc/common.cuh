@@ -346,15 +346,15 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 // ---------------------------------------------------------------------------------------------
 // The tile walker: computes dot = (row of the side operator) . src for every row and calls
 // epi(row, dot, is_long) once per row, from one lane, 32 rows per warp at a time.  Work items are
-// the chunks of the long rows followed by the short-row tiles, distributed over all warps of the
-// grid in a fixed order (so two walks over the same structure give every row to the same warp
-// and lane).
+// the chunks of the long rows followed by the short-row tiles (or groups of tile_mult consecutive
+// tiles), distributed over all warps of the grid round robin (so two walks over the same
+// structure give every row to the same warp and lane).
 //   * A chunk's warp reads its (<= 256) entries as 32 contiguous bytes of indices and values per
 //     lane, sums them (fixed shuffle tree) into chunk_part and takes a ticket; the warp that
 //     completes the last chunk of a group of 32 long rows (no waiting) adds each row's chunk
 //     partials in chunk order, runs the 32 epilogues lane-parallel and calls gdone(group).
 //   * A short tile stages the products of its 16-byte-aligned entry segment in shared memory
-//     (128-bit index / value loads, kStageUnroll gathers per lane in flight), then lane r sums
+//     (128-bit index / value loads, 4 U gathers per lane in flight), then lane r sums
 //     row r's products with four interleaved accumulators.
 // VT is the value type, PT the product/accumulator type; src(j) returns the gathered vector
 // entry; smem is this warp's staging area of 32 * L + 4 PTs.
