@@ -12,8 +12,8 @@ the problem and the device->host copy of (x, y) inside the timed region.
 Multi-GPU: the LPs are independent, so each rank solves its own copy (weak scaling, no data-path
 collective; a barrier and a max-over-ranks of the timings only).
 
-``--impl reference`` times the FP64 CPU oracle (the reference for this build) on the host
-cores instead, on bounded samples of the same workload.
+``--impl reference`` times the FP64 CPU oracle (written from the paper; the only reference
+implementation there is) on the host cores instead, on bounded samples of the same workload.
 """
 from __future__ import annotations
 
