@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/rhpdhg.h"
+#include "bufcache.h"
 #include "internal.h"
 
 using namespace rh;
@@ -107,14 +108,17 @@ int set_err(rhpdhg_handle *h, int code, const std::string &msg) {
     }                                                                                     \
   } while (0)
 
+// Device buffers of a handle come from the buffer cache (buf_alloc); each is released only after
+// the handle's stream has been synchronised.
 template <typename T>
 cudaError_t dalloc(T **p, size_t count) {
-  return cudaMalloc((void **)p, (count > 0 ? count : 1) * sizeof(T));
+  return buf_alloc((void **)p, (count > 0 ? count : 1) * sizeof(T));
 }
 
 void destroy(rhpdhg_handle *h) {
   if (!h) return;
   if (h->th.joinable()) h->th.join();
+  if (h->st) cudaStreamSynchronize(h->st);
   for (auto &g : h->gexec)
     if (g) cudaGraphExecDestroy(g);
   free_side(&h->rows);
@@ -123,13 +127,13 @@ void destroy(rhpdhg_handle *h) {
                     h->kty, h->kty0, h->xout, h->certx, h->y, h->yt, h->y0, h->kx, h->kxt,
                     h->kx0, h->certy, h->x_init, h->y_init, h->xres, h->yres, h->part_row,
                     h->part_col, h->dxt64, h->dyt64, h->certx2, h->certy2};
-  for (double *b : bufs) cudaFree(b);
+  for (double *b : bufs) buf_release(b);
   float *fbufs[] = {h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi,
                     h->dyt, h->kdxt, h->dy, h->kdx, h->r0, h->ylo};
-  for (float *b : fbufs) cudaFree(b);
-  cudaFree(h->act);
-  cudaFree(h->ctl);
-  cudaFree(h->trace);
+  for (float *b : fbufs) buf_release(b);
+  buf_release(h->act);
+  buf_release(h->ctl);
+  buf_release(h->trace);
   if (h->h_mirror) cudaFreeHost(h->h_mirror);
   if (h->own_stream && h->st) cudaStreamDestroy(h->st);
   delete h;
@@ -523,9 +527,11 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
          *u_in = nullptr, *tmp = nullptr;
   unsigned int *flags = nullptr;
   auto free_tmp = [&]() {
-    cudaFree(rp64); cudaFree(rp); cudaFree(col); cudaFree(cp); cudaFree(ridx); cudaFree(val);
-    cudaFree(cval); cudaFree(c_in); cudaFree(q_in); cudaFree(l_in); cudaFree(u_in); cudaFree(tmp);
-    cudaFree(flags);
+    cudaStreamSynchronize(st);
+    for (void *b : {(void *)rp64, (void *)rp, (void *)col, (void *)cp, (void *)ridx, (void *)val,
+                    (void *)cval, (void *)c_in, (void *)q_in, (void *)l_in, (void *)u_in,
+                    (void *)tmp, (void *)flags})
+      buf_release(b);
     rp64 = nullptr; rp = col = cp = ridx = nullptr; val = cval = c_in = q_in = l_in = u_in = tmp = nullptr;
     flags = nullptr;
   };
@@ -591,8 +597,8 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     compute_scaling(st, m, n, rp, col, val, cp, ridx, cval, P.ruiz_iters, P.pock_chambolle_alpha,
                     h->D, h->E, tm, tn);
     cudaError_t e = cudaStreamSynchronize(st);
-    cudaFree(tm);
-    cudaFree(tn);
+    buf_release(tm);
+    buf_release(tn);
     CKT(e);
     CKT(cudaGetLastError());
   }
@@ -688,15 +694,15 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     CKT(cudaMemcpyAsync(&s2, ss + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     CKT(cudaStreamSynchronize(st));
     CKT(cudaGetLastError());
-    cudaFree(v);
-    cudaFree(w);
-    cudaFree(um);
-    cudaFree(pp);
-    cudaFree(ss);
-    cudaFree(tk);
+    buf_release(v);
+    buf_release(w);
+    buf_release(um);
+    buf_release(pp);
+    buf_release(ss);
+    buf_release(tk);
     h->sigma_max = (m > 0 && h->nnz > 0) ? std::sqrt(s2) : 0.0;
   }
-  cudaFree(dn);
+  buf_release(dn);
   if (P.step_size > 0) h->eta = P.step_size;
   else if (h->sigma_max > 1e-12) h->eta = P.step_safety / h->sigma_max;
   else h->eta = 1.0;

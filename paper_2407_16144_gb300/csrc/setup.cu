@@ -6,8 +6,12 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
+#include "bufcache.h"
 #include "internal.h"
 
 namespace rh {
@@ -357,6 +361,66 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
   }
 }
 
+namespace {
+std::mutex g_buf_mu;
+std::unordered_map<void *, size_t> g_buf_size;   // every buffer from buf_alloc, live or cached
+std::multimap<size_t, void *> g_buf_free;         // cached buffers by size
+size_t g_buf_free_bytes = 0;
+
+void buf_drop_cache() {
+  std::lock_guard<std::mutex> lk(g_buf_mu);
+  for (auto &kv : g_buf_free) {
+    g_buf_size.erase(kv.second);
+    cudaFree(kv.second);
+  }
+  g_buf_free.clear();
+  g_buf_free_bytes = 0;
+}
+}  // namespace
+
+cudaError_t buf_alloc(void **p, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 1);
+  {
+    std::lock_guard<std::mutex> lk(g_buf_mu);
+    auto it = g_buf_free.find(bytes);
+    if (it != g_buf_free.end()) {
+      *p = it->second;
+      g_buf_free.erase(it);
+      g_buf_free_bytes -= bytes;
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    buf_drop_cache();
+    e = cudaMalloc(p, bytes);
+  }
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_buf_mu);
+    g_buf_size[*p] = bytes;
+  }
+  return e;
+}
+
+void buf_release(void *p) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(g_buf_mu);
+    auto it = g_buf_size.find(p);
+    if (it != g_buf_size.end()) {
+      const size_t bytes = it->second;
+      if (g_buf_free_bytes + bytes <= kBufferCacheBytes) {
+        g_buf_free.emplace(bytes, p);
+        g_buf_free_bytes += bytes;
+        return;
+      }
+      g_buf_size.erase(it);
+    }
+  }
+  cudaFree(p);
+}
+
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
                        const double *val, const double *rscale, const double *cscale,
                        bool with32, SideStore *out) {
@@ -450,7 +514,7 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   const size_t ng = (size_t)std::max(s.lay.n_long_tiles, 1);
   int *d_dst = nullptr;
   auto up = [&](int **d, const std::vector<int> &h) -> cudaError_t {
-    cudaError_t e = cudaMalloc(d, std::max<size_t>(h.size(), 1) * sizeof(int));
+    cudaError_t e = buf_alloc((void **)d, std::max<size_t>(h.size(), 1) * sizeof(int));
     if (e == cudaSuccess && !h.empty())
       e = cudaMemcpy(*d, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice);
     return e;
@@ -467,20 +531,20 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   TRY(up(&s.chunk_ptr, chunk_ptr));
   TRY(up(&s.chunk_row, chunk_row));
   TRY(up(&d_dst, dst));
-  TRY(cudaMalloc(&s.long_mask, mask.size() * sizeof(uint32_t)));
+  TRY(buf_alloc((void **)&s.long_mask, mask.size() * sizeof(uint32_t)));
   TRY(cudaMemcpy(s.long_mask, mask.data(), mask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   // ---- entries (zero padding), scaled on the device ------------------------------------------
-  TRY(cudaMalloc(&s.idx_s, nnz_s * sizeof(int)));
-  TRY(cudaMalloc(&s.val64_s, nnz_s * sizeof(double)));
-  TRY(cudaMalloc(&s.idx_l, nnz_l * sizeof(int)));
-  TRY(cudaMalloc(&s.val64_l, nnz_l * sizeof(double)));
+  TRY(buf_alloc((void **)&s.idx_s, nnz_s * sizeof(int)));
+  TRY(buf_alloc((void **)&s.val64_s, nnz_s * sizeof(double)));
+  TRY(buf_alloc((void **)&s.idx_l, nnz_l * sizeof(int)));
+  TRY(buf_alloc((void **)&s.val64_l, nnz_l * sizeof(double)));
   TRY(cudaMemsetAsync(s.idx_s, 0, nnz_s * sizeof(int), st));
   TRY(cudaMemsetAsync(s.val64_s, 0, nnz_s * sizeof(double), st));
   TRY(cudaMemsetAsync(s.idx_l, 0, nnz_l * sizeof(int), st));
   TRY(cudaMemsetAsync(s.val64_l, 0, nnz_l * sizeof(double), st));
   if (with32) {
-    TRY(cudaMalloc(&s.val32_s, nnz_s * sizeof(float)));
-    TRY(cudaMalloc(&s.val32_l, nnz_l * sizeof(float)));
+    TRY(buf_alloc((void **)&s.val32_s, nnz_s * sizeof(float)));
+    TRY(buf_alloc((void **)&s.val32_l, nnz_l * sizeof(float)));
     TRY(cudaMemsetAsync(s.val32_s, 0, nnz_s * sizeof(float), st));
     TRY(cudaMemsetAsync(s.val32_l, 0, nnz_l * sizeof(float), st));
   }
@@ -497,18 +561,18 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
     count_launches(1);
   }
   // ---- walk scratch ------------------------------------------------------------------------
-  TRY(cudaMalloc(&s.part_a, (size_t)std::max(nch, 1) * sizeof(double)));
-  TRY(cudaMalloc(&s.part_b, (size_t)std::max(nch, 1) * sizeof(double)));
-  TRY(cudaMalloc(&s.done_a, ng * sizeof(unsigned int)));
-  TRY(cudaMalloc(&s.done_b, ng * sizeof(unsigned int)));
-  TRY(cudaMalloc(&s.gpart_a, ng * kMaxPartials * sizeof(double)));
-  TRY(cudaMalloc(&s.gpart_b, ng * kMaxPartials * sizeof(double)));
+  TRY(buf_alloc((void **)&s.part_a, (size_t)std::max(nch, 1) * sizeof(double)));
+  TRY(buf_alloc((void **)&s.part_b, (size_t)std::max(nch, 1) * sizeof(double)));
+  TRY(buf_alloc((void **)&s.done_a, ng * sizeof(unsigned int)));
+  TRY(buf_alloc((void **)&s.done_b, ng * sizeof(unsigned int)));
+  TRY(buf_alloc((void **)&s.gpart_a, ng * kMaxPartials * sizeof(double)));
+  TRY(buf_alloc((void **)&s.gpart_b, ng * kMaxPartials * sizeof(double)));
   TRY(cudaMemsetAsync(s.done_a, 0, ng * sizeof(unsigned int), st));
   TRY(cudaMemsetAsync(s.done_b, 0, ng * sizeof(unsigned int), st));
   TRY(cudaStreamSynchronize(st));
   TRY(cudaGetLastError());
 #undef TRY
-  cudaFree(d_dst);
+  buf_release(d_dst);
   s.lay.ptr_s = s.ptr_s;
   s.lay.tile_end = s.tile_end;
   s.lay.idx_s = s.idx_s;
@@ -532,7 +596,8 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   *out = s;
   return cudaSuccess;
 fail:
-  cudaFree(d_dst);
+  cudaStreamSynchronize(st);
+  buf_release(d_dst);
   free_side(&s);
   return err;
 }
@@ -542,7 +607,7 @@ void free_side(SideStore *s) {
                   s->end_l, s->idx_l,
                   s->chunk_ptr, s->chunk_row, s->val64_s, s->val64_l, s->val32_s, s->val32_l,
                   s->part_a, s->part_b, s->done_a, s->done_b, s->gpart_a, s->gpart_b};
-  for (void *b : bufs) cudaFree(b);
+  for (void *b : bufs) buf_release(b);
   *s = SideStore();
 }
 
