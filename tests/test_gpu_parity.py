@@ -590,3 +590,21 @@ def test_kkt_eval_matches_oracle_checker(rh, case):
             assert abs(got - ref[key]) <= 1e-12 * max(1.0, abs(ref[key])), (key, got, ref[key])
     # solver's own report agrees with the independent evaluation of its returned point
     assert abs(out[0] - r.rel_p) <= 1e-9 * max(r.rel_p, 1e-12) + 1e-15
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_repeated_handles_bit_identical(rh, precision):
+    """Handles created after others were freed run on reused (dirty) device buffers: every solve
+    of the same LP gives bit-identical results, so nothing relies on freshly zeroed memory."""
+    lp = CASES["c3_small"]()
+    outs = []
+    for _ in range(3):
+        with rh.Solver(lp, precision=precision, eps_rel_kkt=1e-6, max_iters=3000) as s:
+            r = s.run()
+        outs.append((r.status, r.iters, r.x.copy(), r.y.copy()))
+        # a handle of another size in between, so the cache holds buffers of both
+        with rh.Solver(CASES["c1"](), precision=precision, max_iters=50) as s2:
+            s2.run()
+    for st, it, x, y in outs[1:]:
+        assert (st, it) == outs[0][:2]
+        assert np.array_equal(x, outs[0][2]) and np.array_equal(y, outs[0][3])
