@@ -242,6 +242,16 @@ int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t cap
 #define RHPDHG_LAYOUT_FIELDS 12
 int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity);
 
+/* Plan of the tiled split-CSR layout that rhpdhg_create builds for an operator side (K^ or K^T)
+ * with nrows rows and row pointers row_ptr (host memory, nrows + 1 entries, row_ptr[0] = 0); no
+ * device is used.  out receives RHPDHG_PLAN_FIELDS values: 32-row tiles; short tiles per work
+ * item (1, 2 or 4); long rows; long-row chunks; staging stride (entries per warp); padded
+ * short-array entries; padded long-array entries.  capacity: entries available at out.
+ * Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG for a NULL pointer, nrows < 0, row pointers that
+ * do not start at 0 or decrease, offsets beyond int32, or capacity < RHPDHG_PLAN_FIELDS. */
+#define RHPDHG_PLAN_FIELDS 7
+int rhpdhg_plan_layout(const int64_t *row_ptr, int32_t nrows, int64_t *out, int32_t capacity);
+
 /* With params.profile = 1: average device time (ms) per launch of the row-side kernel
  * (K x~ product + dual step) and of the column-side kernel (K^T y~ product + primal step) over
  * the last solve, their launch counts, and the algorithmic bytes one launch of each moves. */

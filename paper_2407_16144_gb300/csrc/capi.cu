@@ -11,6 +11,7 @@
 
 #include "../../include/rhpdhg.h"
 #include "bufcache.h"
+#include "plan.h"
 #include "internal.h"
 
 using namespace rh;
@@ -891,6 +892,28 @@ int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity) {
                                            r.n_long,     c.n_long,     r.n_chunks,  c.n_chunks,
                                            r.seg,        c.seg,        r.walk,      c.walk};
   for (int i = 0; i < RHPDHG_LAYOUT_FIELDS; ++i) out[i] = v[i];
+  return RHPDHG_OK;
+}
+
+int rhpdhg_plan_layout(const int64_t *row_ptr, int32_t nrows, int64_t *out, int32_t capacity) {
+  if (!row_ptr || !out || nrows < 0 || capacity < RHPDHG_PLAN_FIELDS || row_ptr[0] != 0)
+    return RHPDHG_ERR_INVALID_ARG;
+  std::vector<int> hp((size_t)nrows + 1);
+  for (int32_t i = 0; i <= nrows; ++i) {
+    if (row_ptr[i] > INT_MAX || (i > 0 && row_ptr[i] < row_ptr[i - 1]))
+      return RHPDHG_ERR_INVALID_ARG;
+    hp[i] = (int)row_ptr[i];
+  }
+  SidePlan P;
+  if (!plan_side(hp.data(), nrows, &P)) return RHPDHG_ERR_INVALID_ARG;
+  const int64_t v[RHPDHG_PLAN_FIELDS] = {P.ntiles,
+                                         P.mult,
+                                         (int64_t)P.long_rows.size(),
+                                         (int64_t)P.chunk_row.size(),
+                                         ((P.maxseg + 3) & ~3LL) + 4,
+                                         P.nnz_s,
+                                         P.nnz_l};
+  for (int i = 0; i < RHPDHG_PLAN_FIELDS; ++i) out[i] = v[i];
   return RHPDHG_OK;
 }
 

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "bufcache.h"
+#include "plan.h"
 #include "internal.h"
 
 namespace rh {
@@ -421,20 +422,17 @@ void buf_release(void *p) {
   cudaFree(p);
 }
 
-cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
-                       const double *val, const double *rscale, const double *cscale,
-                       bool with32, SideStore *out) {
-  (void)nnz;
-  SideStore s;
-  cudaError_t err = cudaSuccess;
+bool plan_side(const int *hp, int nrows, SidePlan *p) {
+  SidePlan &P = *p;
   const int ntiles = (nrows + kTileRows - 1) / kTileRows;
-  // ---- structure, on the host -------------------------------------------------------------
-  std::vector<int> hp(nrows + 1);
-  if ((err = cudaMemcpy(hp.data(), ptr, (nrows + 1) * sizeof(int), cudaMemcpyDeviceToHost)))
-    return err;
-  std::vector<int> ptr_s(std::max(nrows, 1)), tile_end(std::max(ntiles, 1)), dst(std::max(nrows, 1));
-  std::vector<uint32_t> mask(std::max(ntiles, 1), 0u);
-  std::vector<int> long_rows, beg_l, end_l, chunk_ptr(1, 0), chunk_row;
+  P = SidePlan();
+  P.nrows = nrows;
+  P.ntiles = ntiles;
+  P.ptr_s.assign(std::max(nrows, 1), 0);
+  P.tile_end.assign(std::max(ntiles, 1), 0);
+  P.dst.assign(std::max(nrows, 1), 0);
+  P.mask.assign(std::max(ntiles, 1), 0u);
+  P.chunk_ptr.assign(1, 0);
   long long cur = 0, cl = 0, maxseg = 0;
   auto align4 = [](long long v) { return (v + 3) & ~3LL; };
   for (int t = 0; t < ntiles; ++t) {
@@ -444,45 +442,46 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
     long long sum = 0;
     for (int r = r0; r < r1; ++r) {
       const int len = hp[r + 1] - hp[r];
-      if (len > kShortMax) mask[t] |= 1u << (r - r0);
+      if (len > kShortMax) P.mask[t] |= 1u << (r - r0);
       else sum += len;
     }
     while (sum > kSegBudget) {
       int best = -1, blen = -1;
       for (int r = r0; r < r1; ++r) {
         const int len = hp[r + 1] - hp[r];
-        if (!((mask[t] >> (r - r0)) & 1u) && len > blen) { best = r; blen = len; }
+        if (!((P.mask[t] >> (r - r0)) & 1u) && len > blen) { best = r; blen = len; }
       }
-      mask[t] |= 1u << (best - r0);
+      P.mask[t] |= 1u << (best - r0);
       sum -= blen;
     }
     cur = align4(cur);
     const long long seg_b = cur;
     for (int r = r0; r < r1; ++r) {
       const int len = hp[r + 1] - hp[r];
-      ptr_s[r] = (int)cur;
-      if (!((mask[t] >> (r - r0)) & 1u)) {
-        dst[r] = (int)cur;
+      P.ptr_s[r] = (int)cur;
+      if (!((P.mask[t] >> (r - r0)) & 1u)) {
+        P.dst[r] = (int)cur;
         cur += len;
       } else {
         cl = align4(cl);
-        const int li = (int)long_rows.size();
-        long_rows.push_back(r);
-        beg_l.push_back((int)cl);
-        end_l.push_back((int)(cl + len));
-        dst[r] = (int)cl;
+        const int li = (int)P.long_rows.size();
+        P.long_rows.push_back(r);
+        P.beg_l.push_back((int)cl);
+        P.end_l.push_back((int)(cl + len));
+        P.dst[r] = (int)cl;
         cl += len;
         const int nc = (len + kChunk - 1) / kChunk;
-        for (int c = 0; c < nc; ++c) chunk_row.push_back(li);
-        chunk_ptr.push_back(chunk_ptr.back() + nc);
+        for (int c = 0; c < nc; ++c) P.chunk_row.push_back(li);
+        P.chunk_ptr.push_back(P.chunk_ptr.back() + nc);
       }
+      if (cur > INT_MAX - 8 || cl > INT_MAX - 2 * kChunk) return false;   // casts stay in range
     }
-    tile_end[t] = (int)cur;
+    P.tile_end[t] = (int)cur;
     maxseg = std::max(maxseg, cur - seg_b);
   }
-  const long long nnz_s = align4(cur) + 4, nnz_l = align4(cl) + kChunk;
-  if (nnz_s > INT_MAX || nnz_l > INT_MAX) return cudaErrorInvalidValue;
-  const int nlong = (int)long_rows.size(), nch = (int)chunk_row.size();
+  P.nnz_s = align4(cur) + 4;
+  P.nnz_l = align4(cl) + kChunk;
+  if (P.nnz_s > INT_MAX || P.nnz_l > INT_MAX) return false;
   // Tiles per work item: where tiles are short (a few entries per row), M consecutive tiles are
   // staged as one segment, so that each warp's chain of dependent loads carries M tiles' bytes.
   // M is the largest of kMaxTileMult, ..., 2 whose mean group segment fits one staging round
@@ -494,13 +493,38 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
     long long mx = 0;
     for (int t0 = 0; t0 < ntiles; t0 += cand) {
       const int t1 = std::min(ntiles, t0 + cand) - 1;
-      mx = std::max(mx, (long long)tile_end[t1] - ptr_s[(size_t)t0 * kTileRows]);
+      mx = std::max(mx, (long long)P.tile_end[t1] - P.ptr_s[(size_t)t0 * kTileRows]);
     }
     if (mx <= kSegBudget) {
       mult = cand;
       maxseg = mx;
     }
   }
+  P.mult = mult;
+  P.maxseg = maxseg;
+  return true;
+}
+
+cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
+                       const double *val, const double *rscale, const double *cscale,
+                       bool with32, SideStore *out) {
+  (void)nnz;
+  SideStore s;
+  cudaError_t err = cudaSuccess;
+  // ---- structure, on the host -------------------------------------------------------------
+  std::vector<int> hp(nrows + 1);
+  if ((err = cudaMemcpy(hp.data(), ptr, (nrows + 1) * sizeof(int), cudaMemcpyDeviceToHost)))
+    return err;
+  SidePlan P;
+  if (!plan_side(hp.data(), nrows, &P)) return cudaErrorInvalidValue;
+  const int ntiles = P.ntiles, mult = P.mult;
+  const long long nnz_s = P.nnz_s, nnz_l = P.nnz_l, maxseg = P.maxseg;
+  const std::vector<int> &ptr_s = P.ptr_s, &tile_end = P.tile_end, &dst = P.dst,
+                         &long_rows = P.long_rows, &beg_l = P.beg_l, &end_l = P.end_l,
+                         &chunk_ptr = P.chunk_ptr, &chunk_row = P.chunk_row;
+  const std::vector<uint32_t> &mask = P.mask;
+  auto align4 = [](long long v) { return (v + 3) & ~3LL; };
+  const int nlong = (int)long_rows.size(), nch = (int)chunk_row.size();
   s.lay.nrows = nrows;
   s.lay.seg = (int)align4(maxseg) + 4;
   s.lay.n_short_tiles = ntiles;

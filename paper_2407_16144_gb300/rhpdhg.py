@@ -73,7 +73,8 @@ class rhpdhg_trace_rec(C.Structure):
 
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
             "rhpdhg_cancel", "rhpdhg_free", "rhpdhg_last_error", "rhpdhg_get_state",
-            "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_get_layout", "rhpdhg_kernel_times",
+            "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_get_layout", "rhpdhg_plan_layout",
+            "rhpdhg_kernel_times",
             "rhpdhg_launch_count", "rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc",
             "rhpdhg_batch_create", "rhpdhg_batch_add", "rhpdhg_batch_step", "rhpdhg_batch_poll",
             "rhpdhg_batch_remove", "rhpdhg_batch_slot_status", "rhpdhg_batch_free_bytes",
@@ -108,6 +109,8 @@ def load(path: str = LIB_PATH):
         "rhpdhg_get_trace": (C.c_int, [H, C.POINTER(rhpdhg_trace_rec), C.c_int64,
                                        C.POINTER(C.c_int64)]),
         "rhpdhg_get_layout": (C.c_int, [H, C.POINTER(C.c_int64), C.c_int32]),
+        "rhpdhg_plan_layout": (C.c_int, [C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_int64),
+                                         C.c_int32]),
         "rhpdhg_kernel_times": (C.c_int, [H, _dp, _dp, C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int64), _dp, _dp]),
         "rhpdhg_launch_count": (C.c_int64, [H]),
@@ -203,6 +206,18 @@ def rhpdhg_get_layout(h):
     out = (C.c_int64 * len(LAYOUT_FIELDS))()
     rc = load().rhpdhg_get_layout(h, out, len(LAYOUT_FIELDS))
     return rc, dict(zip(LAYOUT_FIELDS, list(out)))
+
+
+PLAN_FIELDS = ("tiles", "tile_mult", "long_rows", "chunks", "seg", "nnz_short", "nnz_long")
+
+
+def rhpdhg_plan_layout(row_ptr):
+    """Layout plan of an operator side from its CSR row pointers (host only, no device)."""
+    rp = np.ascontiguousarray(np.asarray(row_ptr, dtype=np.int64))
+    out = (C.c_int64 * len(PLAN_FIELDS))()
+    rc = load().rhpdhg_plan_layout(rp.ctypes.data_as(C.POINTER(C.c_int64)), len(rp) - 1, out,
+                                   len(PLAN_FIELDS))
+    return rc, dict(zip(PLAN_FIELDS, list(out)))
 
 
 def rhpdhg_kernel_times(h):

@@ -15,6 +15,7 @@ import math
 import numpy as np
 import pytest
 
+import layout_rule
 from oracle import rhpdhg_oracle as O
 from paper_2407_16144_gb300 import lpgen
 
@@ -64,34 +65,6 @@ CASES = {
 }
 
 
-def expected_tile_mult(row_ptr):
-    """Tiles per work item for a side with these row pointers, restated from the layout rule:
-    rows over 128 entries are long; while a 32-row tile's short segment exceeds 1024 entries its
-    longest short row becomes long; segments start 4-aligned; M is the largest of 4, 2 with at
-    least 2M tiles, mean group segment <= 256 entries and longest group segment <= 1024."""
-    lens = np.diff(np.asarray(row_ptr, dtype=np.int64))
-    nt = (len(lens) + 31) // 32
-    cur, seg_b, seg_e = 0, [], []
-    for t in range(nt):
-        L = lens[32 * t:32 * (t + 1)]
-        short = L <= 128
-        s = int(L[short].sum())
-        while s > 1024:
-            i = max((i for i in range(len(L)) if short[i]), key=lambda i: (L[i], -i))
-            short[i] = False
-            s -= int(L[i])
-        cur = (cur + 3) & ~3
-        seg_b.append(cur)
-        cur += s
-        seg_e.append(cur)
-    for m in (4, 2):
-        if nt < 2 * m or ((cur + 3) & ~3) * m > nt * 256:
-            continue
-        if max(seg_e[min(nt, t + m) - 1] - seg_b[t] for t in range(0, nt, m)) <= 1024:
-            return m
-    return 1
-
-
 @pytest.mark.parametrize("case", list(CASES))
 def test_walk_layout(rh, case):
     """The device's tiles per work item on K^ and K^T match the rule restated from the CSR."""
@@ -99,8 +72,14 @@ def test_walk_layout(rh, case):
     A = O.csr_matrix(lp)
     with rh.Solver(lp) as s:
         lay = s.layout()
-    assert lay["tile_mult_row"] == expected_tile_mult(A.indptr)
-    assert lay["tile_mult_col"] == expected_tile_mult(A.T.tocsr().indptr)
+    assert lay["tile_mult_row"] == layout_rule.expected_tile_mult(A.indptr)
+    assert lay["tile_mult_col"] == layout_rule.expected_tile_mult(A.T.tocsr().indptr)
+    # the device's layout is the host plan the C ABI reports
+    for side, rp in (("row", A.indptr), ("col", A.T.tocsr().indptr)):
+        rc, pl = rh.rhpdhg_plan_layout(rp)
+        assert rc == 0 and pl["tile_mult"] == lay[f"tile_mult_{side}"]
+        assert pl["long_rows"] == lay[f"long_rows_{side}"] and pl["chunks"] == lay[f"chunks_{side}"]
+        assert pl["seg"] == lay[f"seg_{side}"]
     if case == "short_cols":
         assert lay["tile_mult_col"] == 4
     if case == "c3_small":
