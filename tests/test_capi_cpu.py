@@ -111,3 +111,20 @@ def test_binding_fails_loudly_without_library(tmp_path):
             % (ROOT, str(tmp_path / "missing.so")))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True).stdout
     assert out.startswith("raised")
+
+
+def test_batch_slot_bytes_cover_the_data(rh):
+    """A batched slot's size (host computation, no device) holds at least the LP's two CSR copies
+    (int32 indices and FP64 values), both row-pointer arrays and the per-slot FP64 vectors, and
+    grows with the LP."""
+    from paper_2407_16144_gb300 import lpgen
+    prev = 0
+    for n in (50, 500, 5000):
+        lp = lpgen.make_standard_planted(0, m=n // 2, n=n, col_nnz=3)
+        keep = []
+        need = rh.rhpdhg_batch_bytes_needed(rh.host_problem(lp, keep))
+        m, nnz = lp.m_eq + lp.m_ineq, int(lp.row_ptr[-1])
+        raw = 2 * nnz * (4 + 8) + 4 * (m + 1 + n + 1) + 8 * (n + m)
+        assert need >= raw
+        assert need > prev
+        prev = need
