@@ -74,7 +74,9 @@ class OracleParams:
     primal_weight_update: int = 1
     first_epoch_len: int = 64     # tau^0 of eq. (adaptive-restart)
     max_epoch_len: int = 1000     # 0 = no cap; restart once k >= max_epoch_len
-    restart_scheme: int = 0       # 0 = adaptive (eq. adaptive-restart), 1 = fixed (eq. fixed-restart)
+    restart_scheme: int = 0       # 0 = adaptive (eq. adaptive-restart), 1 = fixed (eq. fixed-restart),
+    #                               2 = two-phase: the first epoch restarts at k >= first_epoch_len,
+    #                               later ones at k >= max_epoch_len (remark after Theorem infeas)
     restart_beta: float = math.exp(-1.0)
     check_every: int = 64
     adaptive_step: int = 0        # 1 = the adaptive step rule (Section 7, "as cuPDLP")
@@ -411,6 +413,8 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
         # restart test (eq. adaptive-restart / eq. fixed-restart, plus the epoch cap)
         if params.restart_scheme == 1:
             restart = params.max_epoch_len > 0 and k >= params.max_epoch_len
+        elif params.restart_scheme == 2:
+            restart = k >= (params.first_epoch_len if n_ep == 0 else params.max_epoch_len)
         else:
             restart = (n_ep == 0 and k > params.first_epoch_len) or \
                       (n_ep >= 1 and fpr2 <= beta2 * fpr0) or \

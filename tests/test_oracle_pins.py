@@ -259,6 +259,31 @@ def test_fixed_frequency_restart():
     assert restarts == list(range(50, 500, 51))[:len(restarts)] and len(restarts) >= 9
 
 
+def test_two_phase_restart_schedule():
+    """The schedule of the remark after Theorem infeas: one long first epoch, then a fixed
+    frequency.  With first epoch 80 and period 30 the restarts fall at t = 80, then every 31
+    evaluations (the restart point itself opens the next epoch at k = 0)."""
+    lp = lpgen.make_c1(0)
+    r = O.solve(lp, O.OracleParams(eps_rel_kkt=1e-14, max_iters=400, restart_scheme=2,
+                                   first_epoch_len=80, max_epoch_len=30), trace=True)
+    restarts = [t for (t, n, k, f, rs, _) in r.trace if rs]
+    assert restarts == list(range(80, 400, 31))[:len(restarts)] and len(restarts) >= 10
+
+
+def test_two_phase_schedule_certifies_infeasibility():
+    """The schedule's purpose is infeasibility detection: on a planted primal-infeasible LP it
+    ends with a Farkas certificate that holds against the unscaled data."""
+    lp = lpgen.make_primal_infeasible(3, m=500, n=1000)
+    r = O.solve(lp, O.OracleParams(max_iters=50_000, restart_scheme=2, first_epoch_len=400,
+                                   max_epoch_len=200))
+    assert r.status == O.PRIMAL_INFEASIBLE
+    y = r.cert_y
+    K = O.csr_matrix(lp)
+    by = lp.q @ y
+    assert by > 0
+    assert (K.T @ y).max() / by <= 1e-8          # A^T y <= 0, b^T y > 0 (Farkas)
+
+
 def test_scaling_properties():
     lp = lpgen.make_c2(2, scale=0.002)
     K = O.csr_matrix(lp)
