@@ -242,6 +242,13 @@ int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t cap
 #define RHPDHG_LAYOUT_FIELDS 12
 int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity);
 
+/* Handles take their device buffers from a process-wide cache of buffers freed by earlier
+ * handles (same device, same size; at most 4 GiB kept), so that creating and freeing handles of
+ * the same sizes costs no device allocation after the first time.  This frees every cached
+ * buffer (for instance before a device reset, or to give the memory back) and returns the bytes
+ * freed.  Handles alive at the time are not affected. */
+int64_t rhpdhg_release_cached_memory(void);
+
 /* Plan of the tiled split-CSR layout that rhpdhg_create builds for an operator side (K^ or K^T)
  * with nrows rows and row pointers row_ptr (host memory, nrows + 1 entries, row_ptr[0] = 0); no
  * device is used.  out receives RHPDHG_PLAN_FIELDS values: 32-row tiles; short tiles per work

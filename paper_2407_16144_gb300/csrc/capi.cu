@@ -895,6 +895,8 @@ int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity) {
   return RHPDHG_OK;
 }
 
+int64_t rhpdhg_release_cached_memory(void) { return (int64_t)buf_drop_cache(); }
+
 int rhpdhg_plan_layout(const int64_t *row_ptr, int32_t nrows, int64_t *out, int32_t capacity) {
   if (!row_ptr || !out || nrows < 0 || capacity < RHPDHG_PLAN_FIELDS || row_ptr[0] != 0)
     return RHPDHG_ERR_INVALID_ARG;

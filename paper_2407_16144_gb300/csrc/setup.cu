@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "bufcache.h"
@@ -363,17 +364,31 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
 }
 
 namespace {
+// Cached buffers are keyed by (device, size): a buffer is only ever reused on the device it was
+// allocated on.
+struct BufInfo {
+  int dev;
+  size_t bytes;
+};
 std::mutex g_buf_mu;
-std::unordered_map<void *, size_t> g_buf_size;   // every buffer from buf_alloc, live or cached
-std::multimap<size_t, void *> g_buf_free;         // cached buffers by size
+std::unordered_map<void *, BufInfo> g_buf_info;              // every buffer from buf_alloc
+std::map<std::pair<int, size_t>, std::vector<void *>> g_buf_free;   // cached, by (device, size)
 size_t g_buf_free_bytes = 0;
 
-void buf_drop_cache() {
-  std::lock_guard<std::mutex> lk(g_buf_mu);
+// Frees every cached buffer (on its own device); the caller holds g_buf_mu.
+void buf_drop_cache_locked() {
+  if (g_buf_free.empty()) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
   for (auto &kv : g_buf_free) {
-    g_buf_size.erase(kv.second);
-    cudaFree(kv.second);
+    if (kv.second.empty()) continue;
+    cudaSetDevice(kv.first.first);
+    for (void *p : kv.second) {
+      g_buf_info.erase(p);
+      cudaFree(p);
+    }
   }
+  if (cur >= 0) cudaSetDevice(cur);
   g_buf_free.clear();
   g_buf_free_bytes = 0;
 }
@@ -381,25 +396,31 @@ void buf_drop_cache() {
 
 cudaError_t buf_alloc(void **p, size_t bytes) {
   bytes = std::max<size_t>(bytes, 1);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   {
     std::lock_guard<std::mutex> lk(g_buf_mu);
-    auto it = g_buf_free.find(bytes);
-    if (it != g_buf_free.end()) {
-      *p = it->second;
-      g_buf_free.erase(it);
+    auto it = g_buf_free.find({dev, bytes});
+    if (it != g_buf_free.end() && !it->second.empty()) {
+      *p = it->second.back();
+      it->second.pop_back();
       g_buf_free_bytes -= bytes;
       return cudaSuccess;
     }
   }
-  cudaError_t e = cudaMalloc(p, bytes);
+  e = cudaMalloc(p, bytes);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
-    buf_drop_cache();
+    {
+      std::lock_guard<std::mutex> lk(g_buf_mu);
+      buf_drop_cache_locked();
+    }
     e = cudaMalloc(p, bytes);
   }
   if (e == cudaSuccess) {
     std::lock_guard<std::mutex> lk(g_buf_mu);
-    g_buf_size[*p] = bytes;
+    g_buf_info[*p] = BufInfo{dev, bytes};
   }
   return e;
 }
@@ -408,18 +429,25 @@ void buf_release(void *p) {
   if (!p) return;
   {
     std::lock_guard<std::mutex> lk(g_buf_mu);
-    auto it = g_buf_size.find(p);
-    if (it != g_buf_size.end()) {
-      const size_t bytes = it->second;
-      if (g_buf_free_bytes + bytes <= kBufferCacheBytes) {
-        g_buf_free.emplace(bytes, p);
-        g_buf_free_bytes += bytes;
+    auto it = g_buf_info.find(p);
+    if (it != g_buf_info.end()) {
+      const BufInfo bi = it->second;
+      if (g_buf_free_bytes + bi.bytes <= kBufferCacheBytes) {
+        g_buf_free[{bi.dev, bi.bytes}].push_back(p);
+        g_buf_free_bytes += bi.bytes;
         return;
       }
-      g_buf_size.erase(it);
+      g_buf_info.erase(it);
     }
   }
   cudaFree(p);
+}
+
+size_t buf_drop_cache() {
+  std::lock_guard<std::mutex> lk(g_buf_mu);
+  const size_t freed = g_buf_free_bytes;
+  buf_drop_cache_locked();
+  return freed;
 }
 
 bool plan_side(const int *hp, int nrows, SidePlan *p) {

@@ -74,6 +74,7 @@ class rhpdhg_trace_rec(C.Structure):
 EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_poll",
             "rhpdhg_cancel", "rhpdhg_free", "rhpdhg_last_error", "rhpdhg_get_state",
             "rhpdhg_get_scaling", "rhpdhg_get_trace", "rhpdhg_get_layout", "rhpdhg_plan_layout",
+            "rhpdhg_release_cached_memory",
             "rhpdhg_kernel_times",
             "rhpdhg_launch_count", "rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc",
             "rhpdhg_batch_create", "rhpdhg_batch_add", "rhpdhg_batch_step", "rhpdhg_batch_poll",
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
         "rhpdhg_get_layout": (C.c_int, [H, C.POINTER(C.c_int64), C.c_int32]),
         "rhpdhg_plan_layout": (C.c_int, [C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_int64),
                                          C.c_int32]),
+        "rhpdhg_release_cached_memory": (C.c_int64, []),
         "rhpdhg_kernel_times": (C.c_int, [H, _dp, _dp, C.POINTER(C.c_int64),
                                           C.POINTER(C.c_int64), _dp, _dp]),
         "rhpdhg_launch_count": (C.c_int64, [H]),
@@ -206,6 +208,11 @@ def rhpdhg_get_layout(h):
     out = (C.c_int64 * len(LAYOUT_FIELDS))()
     rc = load().rhpdhg_get_layout(h, out, len(LAYOUT_FIELDS))
     return rc, dict(zip(LAYOUT_FIELDS, list(out)))
+
+
+def release_cached_memory() -> int:
+    """Frees the device buffers cached from freed handles; returns the bytes freed."""
+    return int(load().rhpdhg_release_cached_memory())
 
 
 PLAN_FIELDS = ("tiles", "tile_mult", "long_rows", "chunks", "seg", "nnz_short", "nnz_long")

@@ -128,3 +128,9 @@ def test_batch_slot_bytes_cover_the_data(rh):
         assert need >= raw
         assert need > prev
         prev = need
+
+
+def test_release_cached_memory_without_handles(rh):
+    """With no handle ever freed the buffer cache is empty: releasing it frees nothing and needs
+    no device."""
+    assert rh.release_cached_memory() == 0

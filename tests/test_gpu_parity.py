@@ -587,3 +587,6 @@ def test_repeated_handles_bit_identical(rh, precision):
     for st, it, x, y in outs[1:]:
         assert (st, it) == outs[0][:2]
         assert np.array_equal(x, outs[0][2]) and np.array_equal(y, outs[0][3])
+    # the freed handles' buffers are cached; releasing them returns their bytes, then nothing
+    assert rh.release_cached_memory() > 0
+    assert rh.release_cached_memory() == 0
