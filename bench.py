@@ -27,6 +27,11 @@ import sys
 import tempfile
 import time
 
+# The CPU baseline is the oracle on one core: keep numpy's BLAS and OpenMP pools to one thread
+# (unless the caller chose otherwise) so that the reported core count is the one used.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
