@@ -62,7 +62,7 @@ def parse():
 
 
 # DRAM bytes (read + write) per launch of the mixed-precision ordinary-iteration kernels on the
-# 100k x 250k LP, from one ncu capture (profiles/k_iter_mx_c2.md) of the kernel sources with
+# 100k x 250k LP, from one ncu capture (summarised under profiles/) of the kernel sources with
 # this digest (their code with comments and whitespace removed).  Reported as roofline.traffic
 # only while that code is unchanged.
 KERNEL_SOURCES = ["paper_2407_16144_gb300/csrc/iterate_mx.cu", "paper_2407_16144_gb300/csrc/common.cuh",
@@ -175,6 +175,15 @@ def replica_throughput(world, units_per_rank, max_ms):
     """Whole-job rate of `world` independent replicas that each ran `units_per_rank` units in
     at most `max_ms` milliseconds (weak scaling)."""
     return world * units_per_rank / (max_ms / 1000.0)
+
+
+def fp64_flops(lp):
+    """Algorithmic FP64 flops of one launch of the FP64 row kernel (K x~ and the dual step) and
+    of the column kernel (K^T y~ and the primal step) of r2HPDHG: one FMA (2 flops) per nonzero,
+    and the fused elementwise work per row (reflected blends of y and K x, the dual step and
+    projection, the three restart-test sums: 23 flops) and per column (blends of x and K^T y,
+    the primal step and clamp, two sums: 19 flops)."""
+    return 2.0 * lp.nnz + 23.0 * lp.m, 2.0 * lp.nnz + 19.0 * lp.n
 
 
 def problem_bytes(lp):
@@ -435,19 +444,39 @@ def run_ours(args):
     ok = all(r.status == rhpdhg.STATUS_OPTIMAL for r in results)
     # e2e through host buffers
     e2e_outs, e2e_ms = timed(step_host, max(2, min(args.steps, 3)))
-    # the other precision on the same workload (reported beside the headline)
+    # the other precision on the same workload (reported beside the headline), timed as the
+    # same create + solve + poll + free step
     other = 1 - args.precision
     oparams = dict(params, precision=other)
-    so = rhpdhg.Solver(dev, device=True, stream=sh, **oparams)
-    so.solve(1)
-    ro = so.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
-    so.close()
-    # kernel timing (CUDA events around each launch of the two iteration kernels)
-    s = rhpdhg.Solver(dev, device=True, stream=sh, profile=1, **params)
-    s.solve(1)
-    rp = s.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
-    kt = s.kernel_times()
-    s.close()
+
+    def step_other():
+        so = rhpdhg.Solver(dev, device=True, stream=sh, **oparams)
+        so.solve(1)
+        r = so.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
+        so.close()
+        return r
+
+    step_other()
+    o_outs, o_ms = timed(step_other, 3)
+    ro = o_outs[-1]
+    # rate probes for the roofline denominators that the driver's peaks do not give: the read
+    # bandwidth of a 64 MiB buffer held in L2, and the FP64 FMA rate
+    rc1, l2_gbs = rhpdhg.rhpdhg_probe_l2_read_bandwidth(64 << 20, sh)
+    rc2, fp64_tflops = rhpdhg.rhpdhg_probe_fp64_fma_rate(sh)
+    if rc1 != rhpdhg.OK or rc2 != rhpdhg.OK:
+        raise RuntimeError("rate probe failed: " + rhpdhg.rhpdhg_last_error(None))
+    # kernel timing (CUDA events around each launch of the two iteration kernels), for the
+    # headline precision and the other one
+    def profiled(prm):
+        s = rhpdhg.Solver(dev, device=True, stream=sh, profile=1, **prm)
+        s.solve(1)
+        r = s.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
+        k = s.kernel_times()
+        s.close()
+        return r, k
+
+    rp, kt = profiled(params)
+    _, kt_other = profiled(oparams)
     total_ms, e2e_total = replica_max(dist, [total_ms, sum(e2e_ms)], "cuda")
     if rank != 0:
         return 0
@@ -461,6 +490,13 @@ def run_ours(args):
     else:
         dom, dom_ms, dom_bytes = "row kernel (K x~ + dual step)", kt["ms_row"], kt["bytes_row"]
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
+    # FP64 path: algorithmic FP64 flops per launch (one FMA per nonzero, the fused elementwise
+    # work per row and per column) against the probed FP64 FMA rate
+    kt64 = kt if args.precision == 0 else kt_other
+    fl_row, fl_col = fp64_flops(lp)
+    fp64_row = fl_row / (kt64["ms_row"] / 1000.0) / 1e12
+    fp64_col = fl_col / (kt64["ms_col"] / 1000.0) / 1e12
+    o_ms_step = statistics.mean(o_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -476,8 +512,17 @@ def run_ours(args):
         "rel_kkt": max(results[-1].rel_p, results[-1].rel_d, results[-1].rel_gap),
         "other_precision": {"precision": "fp64" if other == 0 else "fp32 iterates, fp64 restarts",
                             "status": ro.status_name, "iters": ro.iters,
+                            "value": 1000.0 / o_ms_step, "ms_per_step": o_ms_step,
                             "solve_s": ro.solve_seconds,
-                            "iters_per_s": ro.iters / ro.solve_seconds},
+                            "iters_per_s": ro.iters / ro.solve_seconds,
+                            "ms_per_launch_row": kt_other["ms_row"],
+                            "ms_per_launch_col": kt_other["ms_col"]},
+        "fp64_roofline": {"bound": "fp64 alu", "unit": "TFLOP/s",
+                          "peak": fp64_tflops, "peak_kind": "probed FP64 FMA rate (this run)",
+                          "flops_per_launch_row": fl_row, "flops_per_launch_col": fl_col,
+                          "row_kernel": {"achieved": fp64_row, "frac": fp64_row / fp64_tflops},
+                          "column_kernel": {"achieved": fp64_col,
+                                            "frac": fp64_col / fp64_tflops}},
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": problem_bytes(lp),
@@ -485,6 +530,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
                      "frac": achieved / peak,
+                     "l2_peak": l2_gbs, "l2_peak_kind": "probed read bandwidth of a 64 MiB "
+                                                       "L2-resident buffer (this run)",
+                     "l2_frac": achieved / l2_gbs,
                      "traffic": (PROFILED_TRAFFIC.get(dom) if args.precision == 1 and
                                  kernel_digest() == PROFILED_TRAFFIC["digest"] else None),
                      "ms_per_launch_row": kt["ms_row"], "ms_per_launch_col": kt["ms_col"],

@@ -121,7 +121,10 @@ typedef struct {
                                    first epoch).                                  default 64    */
   int64_t max_epoch_len;        /* restart once k >= this (0 = no cap).           default 1000  */
   int32_t restart_scheme;       /* 0 = adaptive (eq. adaptive-restart); 1 = fixed frequency
-                                   every max_epoch_len (eq. fixed-restart).       default 0     */
+                                   every max_epoch_len (eq. fixed-restart); 2 = two-phase (the
+                                   remark after Theorem infeas): the first epoch restarts once
+                                   k >= first_epoch_len, every later one once k >= max_epoch_len.
+                                   Schemes 1 and 2 need max_epoch_len >= 1.       default 0     */
   double  restart_beta;         /* restart when FPR <= beta * FPR(z^{n,0}).       default e^-1  */
   int32_t check_every;          /* termination-check cadence C (iterations).      default 64    */
   int32_t use_graphs;           /* 1 = replay a captured CUDA graph of C iterations. default 1  */
@@ -272,10 +275,14 @@ int rhpdhg_kernel_times(const rhpdhg_handle *h, double *ms_row, double *ms_col,
  * doubles) and y (m doubles) in device memory, writes to the host array out:
  *     out[0] = rel_p, out[1] = rel_d, out[2] = rel_gap, out[3] = primal_obj, out[4] = dual_obj.
  * Only the CSR of K is needed: K^T y is accumulated with atomic FP64 adds, so the last digits
- * may differ from run to run.  Work is ordered on `cuda_stream` (NULL = legacy default stream)
- * and the call synchronises it.  Scratch (n + 8200 doubles) is allocated with cudaMalloc and
- * freed before returning.  Returns RHPDHG_ERR_INVALID_ARG for host-memory or incomplete input,
- * RHPDHG_ERR_OOM / RHPDHG_ERR_CUDA on CUDA failures. */
+ * may differ from run to run.  The CSR is not validated beforehand: a row whose offsets leave
+ * [0, nnz] or decrease, and an entry whose column leaves [0, n), are skipped on the device and
+ * the call then returns RHPDHG_ERR_INVALID_ARG.  Work is ordered on `cuda_stream` (NULL = legacy
+ * default stream) and the call synchronises it, so it must not be issued on a stream that is
+ * being captured into a graph.  Scratch (n + 8200 doubles) is allocated with cudaMalloc and
+ * freed before returning.  Errors: RHPDHG_ERR_INVALID_ARG for host-memory, incomplete or
+ * out-of-range input, RHPDHG_ERR_OOM / RHPDHG_ERR_CUDA on CUDA failures; each sets the message
+ * of rhpdhg_last_error(NULL). */
 int rhpdhg_kkt_eval(const rhpdhg_problem *lp, const double *x, const double *y,
                     void *cuda_stream, double *out);
 
@@ -289,13 +296,31 @@ int rhpdhg_kkt_eval(const rhpdhg_problem *lp, const double *x, const double *y,
  *   - Size limit: n <= 1,048,576 (2^20).  Larger problems return RHPDHG_ERR_INVALID_ARG with a
  *     message in rhpdhg_last_error(NULL); use rhpdhg_kkt_eval for them.
  *   - The first call on each device looks up the array's device address (with that device
- *     current) and keeps it; make that first call before any stream capture.
+ *     current) and keeps it.  Every call copies its results to the host and synchronises the
+ *     stream, so no call may be issued on a stream that is being captured into a graph.
  *   - All calls share the one array, and it keeps the previous call's contents (the call clears
  *     what has to start at zero).  Calls that overlap on the GPU, on any stream or from any host
  *     thread, race on the array and give wrong results: order them.
  * Arguments, results and other errors are those of rhpdhg_kkt_eval. */
 int rhpdhg_kkt_eval_noalloc(const rhpdhg_problem *lp, const double *x, const double *y,
                             void *cuda_stream, double *out);
+
+/* ---- rate probes (roofline denominators) ------------------------------------------------
+ * Measurements of the current device for the bounds the iteration kernels are compared with;
+ * neither changes a device setting.  Each times its kernel with CUDA events on cuda_stream
+ * (NULL = legacy default stream) after one untimed launch, reports the best launch, allocates
+ * and frees its own buffers and synchronises the stream.  Errors: RHPDHG_ERR_INVALID_ARG for a
+ * NULL output or a size out of range, RHPDHG_ERR_OOM / RHPDHG_ERR_CUDA on CUDA failures, each
+ * with a message in rhpdhg_last_error(NULL). */
+
+/* FP64 fused multiply-add rate in TFLOP/s (2 flops per FMA): every resident thread runs 8
+ * independent FMA chains. */
+int rhpdhg_probe_fp64_fma_rate(void *cuda_stream, double *tflops);
+
+/* Read bandwidth in GB/s of a device buffer of `bytes` (1 MiB .. 4 GiB) read repeatedly with
+ * 16-byte loads that bypass L1: a size well inside L2 (for instance 64 MiB of the 126 MB) gives
+ * the L2 read bandwidth, a size well beyond it the DRAM read bandwidth. */
+int rhpdhg_probe_l2_read_bandwidth(int64_t bytes, void *cuda_stream, double *gbs);
 
 /* ---- batched solver ---------------------------------------------------------------------
  * Many small LPs advance together in one persistent launch, one CTA per LP (the CTA also runs

@@ -38,7 +38,11 @@ Readings of silent or ambiguous passages (each listed with its reason in the des
 Parity pinned by tests/test_oracle_pins.py (vertex enumeration, closed-form box LPs, an
 independent LP solver's optimum, Proposition 1, Lemma (sublinear-feas), Corollary
 (sublinear-feas-reflected), Lemma (iterates-feas)(i), planted optima and planted Farkas
-certificates).
+certificates).  Parity unpinned: the primal-weight update (primal_weight_update), which the
+paper names without defining it; the tests pin only its orientation and degree (the exact
+covariance of the method under c -> alpha c and under (q, l, u) -> beta (q, l, u)), not its
+smoothing exponent or which movement it measures.  Also unpinned: iteration counts to a
+tolerance (the paper gives rates with unknown constants).
 """
 from __future__ import annotations
 
@@ -264,6 +268,18 @@ def infeasibility_test(lp, K, cx, cy, eps):
     return RUNNING, None, None
 
 
+def primal_weight_update(omega, dxa, dya):
+    """Primal weight at a restart (Section 7 names the heuristic only; reading: the smoothed
+    PDLP rule) from the anchor movements dxa = ||x^{n+1,0} - x^{n,0}||, dya = ||y^{n+1,0} -
+    y^{n,0}||: omega <- exp(0.5 log(dya/dxa) + 0.5 log omega), kept when either movement is
+    below 1e-10 or the ratio is not finite.  Parity unpinned beyond the covariance the method
+    has under scaling of the objective and of the right-hand side (tests pin that)."""
+    ratio = dya / dxa if dxa > 1e-10 else 0.0
+    if dxa > 1e-10 and dya > 1e-10 and 0.0 < ratio < math.inf:
+        return math.exp(0.5 * math.log(ratio) + 0.5 * math.log(omega))
+    return omega
+
+
 # ---------------------------------------------------------------------------------------------
 # the solver
 # ---------------------------------------------------------------------------------------------
@@ -438,12 +454,9 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
                 n_ep += 1          # the restart took place: z^{n+1,0} is the new anchor
                 break
             if params.primal_weight_update:
-                dxa = np.linalg.norm(xt - x0)
-                dya = np.linalg.norm(yt - y0)
-                ratio = dya / dxa if dxa > 1e-10 else 0.0
-                if dxa > 1e-10 and dya > 1e-10 and 0.0 < ratio < math.inf:
-                    omega = math.exp(0.5 * math.log(ratio) + 0.5 * math.log(omega))
-                    tau, sigma = eta / omega, eta * omega
+                omega = primal_weight_update(omega, np.linalg.norm(xt - x0),
+                                             np.linalg.norm(yt - y0))
+                tau, sigma = eta / omega, eta * omega
             x, y = xt.copy(), yt.copy()
             x0, y0 = x.copy(), y.copy()
             n_ep += 1

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librhpdhg.so")
-SOURCES = ["setup.cu", "iterate.cu", "iterate_mx.cu", "kkt.cu", "batch.cu", "server.cu", "capi.cu"]
+SOURCES = ["setup.cu", "iterate.cu", "iterate_mx.cu", "kkt.cu", "batch.cu", "server.cu", "capi.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

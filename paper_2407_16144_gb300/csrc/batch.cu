@@ -514,6 +514,12 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
     return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: the batched kernel computes in FP64");
   if (P.adaptive_step)
     return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: batched slots use the constant step");
+  if (P.algorithm < 0 || P.algorithm > 1 || P.check_every < 1 || P.max_iters < 1 ||
+      !(P.eps_rel_kkt > 0) || !(P.eps_infeas > 0) || P.first_epoch_len < 0 ||
+      P.max_epoch_len < 0 || P.restart_scheme < 0 || P.restart_scheme > 2 ||
+      (P.restart_scheme >= 1 && P.max_epoch_len < 1) ||
+      !(P.restart_beta > 0 && P.restart_beta < 1))
+    return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: invalid parameter");
   // host validation and transpose (the batched path serves small LPs)
   const int64_t *rp = lp->row_ptr;
   if (rp[0] != 0 || rp[m] != nnz) return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: malformed row_ptr");

@@ -468,7 +468,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
       P.max_iters < 1 || !(P.eps_rel_kkt > 0) || !(P.eps_infeas > 0) || P.ruiz_iters < 0 ||
       P.power_iters < 1 || P.step_size < 0 || !(P.step_safety > 0) || P.primal_weight < 0 ||
       P.first_epoch_len < 0 || P.max_epoch_len < 0 || P.restart_scheme < 0 ||
-      P.restart_scheme > 1 || (P.restart_scheme == 1 && P.max_epoch_len < 1) ||
+      P.restart_scheme > 2 || (P.restart_scheme >= 1 && P.max_epoch_len < 1) ||
       !(P.restart_beta > 0 && P.restart_beta < 1) || P.trace_capacity < 0 ||
       P.pock_chambolle_alpha > 2.0 || P.adaptive_step < 0 || P.adaptive_step > 1)
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "invalid parameter");

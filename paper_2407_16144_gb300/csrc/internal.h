@@ -61,6 +61,19 @@ struct ColVecsMx {    // mixed precision, n-vectors (offsets from the FP64 ancho
 // Message for rhpdhg_last_error(NULL) (calls without a handle).
 void set_global_error(const std::string &msg);
 
+// Launch through cudaLaunchKernelEx: the return value is this launch's own error (an error left
+// by earlier, unrelated work of the process is neither reported nor cleared).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), int grid, int block, size_t smem,
+                          cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Process-wide count of kernels launched by this library's wrappers (for launch accounting).
 void count_launches(long long n);
 long long launches_so_far();
@@ -126,10 +139,11 @@ int row_iter_blocks_per_sm(int smem);
 constexpr int kKktMaxBlocks = 1024;   // block partials of the evaluation kernels
 constexpr int kKktSlotCount = 8;
 int kkt_blocks(int m, int n);
-// scratch: kty (n doubles), part (kKktMaxBlocks * kKktSlotCount doubles), dout (8 doubles)
+// scratch: kty (n doubles), part (kKktMaxBlocks * kKktSlotCount doubles), dout (8 doubles);
+// *bad_index is set when the CSR held a row offset or column index out of range
 cudaError_t kkt_eval_with_scratch(const rhpdhg_problem *lp, const double *x, const double *y,
                                   cudaStream_t st, double *kty, double *part, double *dout,
-                                  double *out);
+                                  double *out, bool *bad_index);
 
 // ---- mixed-precision iteration (iterate_mx.cu) -------------------------------------------------
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,

@@ -54,8 +54,10 @@ __device__ __forceinline__ int farkas_status(double qv, double uterm, double lte
 }
 
 // Completes ||z_t - T(z_t)||_P^2 = ||dx||^2/tau + ||dy||^2/sigma + 2 dy^T K dx, applies the
-// restart rule of eq. adaptive-restart (first epoch: k > tau^0; later: FPR <= beta FPR_0; plus
-// the epoch cap, or the fixed frequency of eq. fixed-restart) and the primal-weight update.
+// restart rule (scheme 0: eq. adaptive-restart, first epoch k > tau^0, later FPR <= beta FPR_0,
+// plus the epoch cap; scheme 1: the fixed frequency of eq. fixed-restart; scheme 2: the two-phase
+// schedule of the remark after Theorem infeas, a first epoch of first_epoch_len iterations and
+// then the fixed frequency max_epoch_len) and the primal-weight update.
 // With move set (the restart applied by this kernel was decided by a phase-0 column kernel that
 // staged its parts) it first completes the anchor-movement candidate's test.
 __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, const double *r,
@@ -103,6 +105,8 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
   bool rs;
   if (ic.restart_scheme == 1) {
     rs = ic.max_epoch_len > 0 && k >= ic.max_epoch_len;
+  } else if (ic.restart_scheme == 2) {
+    rs = k >= (n_ep == 0 ? (long long)ic.first_epoch_len : ic.max_epoch_len);
   } else {
     rs = (n_ep == 0 && k > ic.first_epoch_len) || (n_ep >= 1 && fpr2 <= ic.beta2 * fpr0) ||
          (ic.max_epoch_len > 0 && k >= ic.max_epoch_len);

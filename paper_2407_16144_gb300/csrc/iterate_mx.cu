@@ -33,17 +33,23 @@ namespace rh {
 
 namespace {
 
-// float accumulators of the per-iteration norms (FP32 products, summed per thread over a few
-// rows, widened to FP64 in the CTA reduction)
-struct F3 {
-  float a = 0.f, b = 0.f, c = 0.f;
-};
+// The restart test's norms (||dy||^2, dy^T K dx, ||y~ - y0||^2 and ||dx||^2, ||x~ - x0||^2) are
+// accumulated in FP64 from the start: each FP32 offset is widened and the product of two widened
+// FP32 values is exact in FP64, so the only rounding is that of the FP64 sums.
+__device__ __forceinline__ double wsq(float a) { return (double)a * (double)a; }
+__device__ __forceinline__ double wmul(float a, float b) { return (double)a * (double)b; }
+
+// Register budgets as resident CTAs per SM: the ordinary kernels (MODE 0) of the plain and
+// grouped walks 8 (64 registers), the wide walk 6 (85), the restart kernels (MODE 1) 4 (128).
+__host__ __device__ constexpr int mx_min_blocks(int mode, int walk) {
+  return mode == 1 ? 4 : (walk == kWalkWide ? 6 : 8);
+}
 
 // MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
 // MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
 // launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
 template <int RHO2, int MODE, int WALK>
-__global__ void __launch_bounds__(kBlockThreads)
+__global__ void __launch_bounds__(kBlockThreads, mx_min_blocks(MODE, WALK))
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
               const double *__restrict__ dxt64, const double *__restrict__ x0, Ctl *ctl,
@@ -67,7 +73,6 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   RowAccL al;     // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
-  F3 fa, fl;
   const unsigned smask = row_smask(check, rp, move);
   const unsigned mmask = row_mmask(rp, move);
 
@@ -139,7 +144,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     auto gB = [&](int j) { return dxt64[j]; };
     walk_tiles<double, double>(lay, v64, gB, my64, wb, epi, gdone);
   } else {
-    auto body = [&](int i, float kd, auto &A, F3 &F) {
+    auto body = [&](int i, float kd, auto &A) {
       const float dytp = v.dyt[i], kdxtp = v.kdxt[i];
       float dy, kdx;
       if (RHO2) {
@@ -156,9 +161,9 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       v.dyt[i] = nd;
       v.kdxt[i] = kd;
       const float ddy = dy - nd;
-      F.a += ddy * ddy;
-      F.b += ddy * (kdx - kd);
-      F.c += nd * nd;
+      A.s[0] += wsq(ddy);
+      A.s[1] += wmul(ddy, kdx - kd);
+      A.s[2] += wsq(nd);
       if (check) {
         const double qi = v.q[i];
         double r = (qi - v.kx0[i] - (double)kd) * v.dinv[i];
@@ -168,16 +173,10 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       }
     };
     auto epi = [&](int i, float kd, bool lg) {
-      if (lg) body(i, kd, al, fl);
-      else body(i, kd, a, fa);
+      if (lg) body(i, kd, al);
+      else body(i, kd, a);
     };
-    auto gdone = [&](int grp) {
-      al.s[0] += (double)fl.a;
-      al.s[1] += (double)fl.b;
-      al.s[2] += (double)fl.c;
-      fl = F3();
-      store_group(al, smask, wb.group_part, grp);
-    };
+    auto gdone = [&](int grp) { store_group(al, smask, wb.group_part, grp); };
     auto gB = [&](int j) { return dxt[j]; };
     auto pre = [&](int i) {
       prefetch_l1(v.dyt + i);
@@ -192,17 +191,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     walk_tiles<float, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
                                                                        epi, gdone, pre);
   }
-  // the FP32 sums (zero in restart mode) are reduced over the warp in FP32, then widened
-  unsigned prewarp = 0u;
-  if constexpr (MODE == 0) {
-    const float f0 = warp_sum(fa.a), f1 = warp_sum(fa.b), f2 = warp_sum(fa.c);
-    a.s[0] = (double)f0;
-    a.s[1] = (double)f1;
-    a.s[2] = (double)f2;
-    prewarp = 0x7u;
-  }
-
-  if (cta_reduce_and_ticket(a, smask, mmask, prewarp, part, &ctl->cnt_row)) {
+  if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
     double r[13];
     grid_finish<7, 6>(part, r, smask, mmask, wb.group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
@@ -211,7 +200,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
 
 // MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
 template <int RHO2, int MODE, int WALK>
-__global__ void __launch_bounds__(kBlockThreads)
+__global__ void __launch_bounds__(kBlockThreads, mx_min_blocks(MODE, WALK))
 k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
               const double *__restrict__ dyt64, const double *__restrict__ y0, Ctl *ctl,
@@ -234,7 +223,6 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   ColAccL al;     // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
-  F3 fa, fl;
   Tel tl;         // active-set telemetry (ordinary check iterations)
   const unsigned smask = col_smask(check, rp, move);
   const unsigned mmask = col_mmask(rp, move);
@@ -257,12 +245,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     // x-part of T(z) - z at the restart point, and K^T of its y-part
     if (rp) col_cert_parts(j, xo, ktd, v, cj, lj, uj, A, a, 5, 0, v.certx);
   };
-  auto gdone = [&](int grp) {
-    al.s[0] += (double)fl.a;
-    al.s[1] += (double)fl.b;
-    fl = F3();
-    store_group(al, smask, (restart ? wa : wb).group_part, grp);
-  };
+  auto gdone = [&](int grp) { store_group(al, smask, (restart ? wa : wb).group_part, grp); };
 
   if constexpr (MODE == 1) {
    if (restart) {
@@ -299,7 +282,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     walk_tiles<double, double>(lay, v64, gA, my64, wa, epi, gdone);
    } else {
     // first iteration of an epoch: K^T (y~ - y0) in FP64 from the exact dyt64 of the row kernel
-    auto body = [&](int j, double ktd, auto &A, F3 &F) {
+    auto body = [&](int j, double ktd, auto &A) {
       const double xo = v.dxt64[j];
       const double x0j = check ? v.x0[j] : 0.0;
       const double kty = check ? v.kty0[j] + ktd : 0.0;
@@ -318,18 +301,18 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
       v.dxt[j] = nt;
       const float ddx = dxn - nt;
-      F.a += ddx * ddx;
-      F.b += nt * nt;
+      A.s[0] += wsq(ddx);
+      A.s[1] += wsq(nt);
     };
     auto epi = [&](int j, double ktd, bool lg) {
-      if (lg) body(j, ktd, al, fl);
-      else body(j, ktd, a, fa);
+      if (lg) body(j, ktd, al);
+      else body(j, ktd, a);
     };
     auto gA = [&](int i) { return dyt64[i]; };
     walk_tiles<double, double>(lay, v64, gA, my64, wb, epi, gdone);
    }
   } else {
-    auto body = [&](int j, float ktdyt, auto &A, F3 &F) {
+    auto body = [&](int j, float ktdyt, auto &A) {
       const float dxtj = v.dxt[j];
       if (check) {
         tel_column(j, dxtj == v.xlo[j] || dxtj == v.xhi[j], v.act, tl);
@@ -349,12 +332,12 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
       v.dxt[j] = nt;
       const float ddx = dxn - nt;
-      F.a += ddx * ddx;
-      F.b += nt * nt;
+      A.s[0] += wsq(ddx);
+      A.s[1] += wsq(nt);
     };
     auto epi = [&](int j, float ktdyt, bool lg) {
-      if (lg) body(j, ktdyt, al, fl);
-      else body(j, ktdyt, a, fa);
+      if (lg) body(j, ktdyt, al);
+      else body(j, ktdyt, a);
     };
     auto gB = [&](int i) { return dyt[i]; };
     auto pre = [&](int j) {
@@ -371,15 +354,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
                                                                        epi, gdone, pre);
     if (check) tel_flush(ctl, tl);
   }
-  unsigned prewarp = 0u;
-  if (!restart) {       // MODE 0, and the restart-point iterations of MODE 1, sum in FP32
-    const float f0 = warp_sum(fa.a), f1 = warp_sum(fa.b);
-    a.s[0] = (double)f0;
-    a.s[1] = (double)f1;
-    prewarp = 0x3u;
-  }
-
-  if (cta_reduce_and_ticket(a, smask, mmask, prewarp, part, &ctl->cnt_col)) {
+  if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[19];
     grid_finish<11, 8>(part, r, smask, mmask, (restart ? wa : wb).group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, rp, move, phase, MODE == 0);

@@ -22,7 +22,9 @@ namespace rh {
 namespace {
 
 constexpr int kKktThreads = 256;
-constexpr int kKktSlots = kKktSlotCount;   // 0 rp2, 1 qy, 2 qq, 3 rd2, 4 cx, 5 bnd, 6 cc
+constexpr int kKktSlots = kKktSlotCount;   // stride of a block's partials
+constexpr int kKktUsed = 7;                // 0 rp2, 1 qy, 2 qq, 3 rd2, 4 cx, 5 bnd, 6 cc
+constexpr int kKktFlag = 5;                // dout[5]: 1 if the CSR held an index out of range
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -36,17 +38,29 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return r;   // valid in thread 0
 }
 
+// Rows whose offsets fall outside [0, nnz] or decrease, and entries whose column lies outside
+// [0, n), are skipped and reported through flag (the caller's CSR is not validated beforehand).
 __global__ void __launch_bounds__(kKktThreads)
-k_kkt_rows(int m, int m_eq, const long long *rp, const int *col, const double *val,
-           const double *x, const double *y, const double *q, double *kty, double *part) {
+k_kkt_rows(int m, int m_eq, int n, long long nnz, const long long *rp, const int *col,
+           const double *val, const double *x, const double *y, const double *q, double *kty,
+           double *part, double *flag) {
   __shared__ double sh[kKktThreads / 32];
   double s_rp2 = 0.0, s_qy = 0.0, s_qq = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
        i += (long long)gridDim.x * blockDim.x) {
     const double yi = y[i], qi = q[i];
     double kx = 0.0;
-    for (long long p = rp[i]; p < rp[i + 1]; ++p) {
+    long long p0 = rp[i], p1 = rp[i + 1];
+    if (p0 < 0 || p1 < p0 || p1 > nnz) {
+      *flag = 1.0;
+      p1 = p0;
+    }
+    for (long long p = p0; p < p1; ++p) {
       const int j = col[p];
+      if (j < 0 || j >= n) {
+        *flag = 1.0;
+        continue;
+      }
       kx += val[p] * x[j];
       atomicAdd(kty + j, val[p] * yi);
     }
@@ -96,9 +110,9 @@ k_kkt_cols(int n, const double *c, const double *l, const double *u, const doubl
 }
 
 __global__ void k_kkt_final(int nb, const double *part, double off, double *out) {
-  // one thread per slot, blocks summed in order
-  __shared__ double tot[kKktSlots];
-  if (threadIdx.x < kKktSlots) {
+  // one thread per used slot, blocks summed in order
+  __shared__ double tot[kKktUsed];
+  if (threadIdx.x < kKktUsed) {
     double s = 0.0;
     for (int b = 0; b < nb; ++b) s += part[b * kKktSlots + threadIdx.x];
     tot[threadIdx.x] = s;
@@ -116,11 +130,13 @@ __global__ void k_kkt_final(int nb, const double *part, double off, double *out)
   }
 }
 
-__global__ void k_kkt_zero(int n, double *v) {
+__global__ void k_kkt_zero(int n, double *v, double *flag) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     v[i] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0.0;
 }
+
 
 }  // namespace
 
@@ -131,21 +147,61 @@ int kkt_blocks(int m, int n) {
 
 // Runs the evaluation with caller-provided scratch: kty (n doubles), part (kKktMaxBlocks *
 // kKktSlots doubles) and dout (8 doubles), all device memory; copies the 5 results to out (host).
+// *bad_index is set when the CSR held a row offset or column index out of range.
 cudaError_t kkt_eval_with_scratch(const rhpdhg_problem *lp, const double *x, const double *y,
                                   cudaStream_t st, double *kty, double *part, double *dout,
-                                  double *out) {
+                                  double *out, bool *bad_index) {
   const int m = lp->m_eq + lp->m_ineq, n = lp->n;
   const int nb = kkt_blocks(m, n);
-  k_kkt_zero<<<nb, kKktThreads, 0, st>>>(n, kty);
-  k_kkt_rows<<<nb, kKktThreads, 0, st>>>(m, lp->m_eq, (const long long *)lp->row_ptr,
-                                          lp->col_idx, lp->val, x, y, lp->rhs, kty, part);
-  k_kkt_cols<<<nb, kKktThreads, 0, st>>>(n, lp->c, lp->l, lp->u, x, kty, part);
-  k_kkt_final<<<1, 32, 0, st>>>(nb, part, lp->obj_offset, dout);
+  double *flag = dout + kKktFlag;
+  cudaError_t e = launch_kernel(k_kkt_zero, nb, kKktThreads, 0, st, n, kty, flag);
+  if (e == cudaSuccess)
+    e = launch_kernel(k_kkt_rows, nb, kKktThreads, 0, st, m, lp->m_eq, n, (long long)lp->nnz,
+               (const long long *)lp->row_ptr, lp->col_idx, lp->val, x, y, lp->rhs, kty, part,
+               flag);
+  if (e == cudaSuccess)
+    e = launch_kernel(k_kkt_cols, nb, kKktThreads, 0, st, n, lp->c, lp->l, lp->u, x, (const double *)kty,
+               part);
+  if (e == cudaSuccess)
+    e = launch_kernel(k_kkt_final, 1, 32, 0, st, nb, (const double *)part, lp->obj_offset, dout);
+  if (e != cudaSuccess) return e;
   count_launches(4);
-  cudaMemcpyAsync(out, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) e = cudaGetLastError();
-  return e;
+  double h[6] = {0};
+  e = cudaMemcpyAsync(h, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < 5; ++i) out[i] = h[i];
+  *bad_index = h[kKktFlag] != 0.0;
+  return cudaSuccess;
+}
+
+// Host checks shared by both entry points; returns an empty string when the arguments are usable.
+std::string kkt_arg_error(const rhpdhg_problem *lp, const double *x, const double *y,
+                          const double *out) {
+  if (!lp || !x || !out) return "lp, x or out is NULL";
+  if (lp->memory != RHPDHG_MEM_DEVICE) return "the problem's arrays must be in device memory";
+  if (lp->n < 1 || lp->m_eq < 0 || lp->m_ineq < 0 || lp->nnz < 0)
+    return "negative size or n < 1";
+  if ((long long)lp->m_eq + lp->m_ineq > 2147483646LL) return "m exceeds the 32-bit range";
+  const bool rows = lp->m_eq + lp->m_ineq > 0;
+  if (!lp->row_ptr || !lp->c || !lp->l || !lp->u || (rows && (!y || !lp->rhs)) ||
+      (lp->nnz > 0 && (!lp->col_idx || !lp->val)))
+    return "missing problem array or point";
+  return "";
+}
+
+// Result of a finished evaluation as a return code, with the message for rhpdhg_last_error.
+int kkt_finish(const char *who, cudaError_t e, bool bad_index) {
+  if (e != cudaSuccess) {
+    set_global_error(std::string(who) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? RHPDHG_ERR_OOM : RHPDHG_ERR_CUDA;
+  }
+  if (bad_index) {
+    set_global_error(std::string(who) +
+                     ": a row offset or column index of the CSR is out of range (entries skipped)");
+    return RHPDHG_ERR_INVALID_ARG;
+  }
+  return RHPDHG_OK;
 }
 
 }  // namespace rh
@@ -153,22 +209,23 @@ cudaError_t kkt_eval_with_scratch(const rhpdhg_problem *lp, const double *x, con
 extern "C" int rhpdhg_kkt_eval(const rhpdhg_problem *lp, const double *x, const double *y,
                                void *stream, double *out) {
   using namespace rh;
-  if (!lp || !x || !out || lp->n < 1 || lp->m_eq < 0 || lp->m_ineq < 0 ||
-      lp->memory != RHPDHG_MEM_DEVICE || (lp->m_eq + lp->m_ineq > 0 && (!y || !lp->rhs)) ||
-      !lp->row_ptr || !lp->c || !lp->l || !lp->u)
+  const std::string bad = kkt_arg_error(lp, x, y, out);
+  if (!bad.empty()) {
+    set_global_error("rhpdhg_kkt_eval: " + bad);
     return RHPDHG_ERR_INVALID_ARG;
+  }
   const int n = lp->n;
   cudaStream_t st = (cudaStream_t)stream;
   double *kty = nullptr, *part = nullptr, *dout = nullptr;
+  bool bad_index = false;
   cudaError_t e = cudaMalloc(&kty, (size_t)n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)kKktMaxBlocks * kKktSlotCount * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&dout, 8 * sizeof(double));
-  if (e == cudaSuccess) e = kkt_eval_with_scratch(lp, x, y, st, kty, part, dout, out);
+  if (e == cudaSuccess) e = kkt_eval_with_scratch(lp, x, y, st, kty, part, dout, out, &bad_index);
   cudaFree(kty);
   cudaFree(part);
   cudaFree(dout);
-  if (e == cudaErrorMemoryAllocation) return RHPDHG_ERR_OOM;
-  return e == cudaSuccess ? RHPDHG_OK : RHPDHG_ERR_CUDA;
+  return kkt_finish("rhpdhg_kkt_eval", e, bad_index);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -197,10 +254,9 @@ double *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
 extern "C" int rhpdhg_kkt_eval_noalloc(const rhpdhg_problem *lp, const double *x,
                                        const double *y, void *stream, double *out) {
   using namespace rh;
-  if (!lp || !x || !out || lp->n < 1 || lp->m_eq < 0 || lp->m_ineq < 0 ||
-      lp->memory != RHPDHG_MEM_DEVICE || (lp->m_eq + lp->m_ineq > 0 && (!y || !lp->rhs)) ||
-      !lp->row_ptr || !lp->c || !lp->l || !lp->u) {
-    set_global_error("rhpdhg_kkt_eval_noalloc: missing or host-memory input");
+  const std::string bad = kkt_arg_error(lp, x, y, out);
+  if (!bad.empty()) {
+    set_global_error("rhpdhg_kkt_eval_noalloc: " + bad);
     return RHPDHG_ERR_INVALID_ARG;
   }
   if ((long long)lp->n > kNoAllocMaxN) {
@@ -211,7 +267,7 @@ extern "C" int rhpdhg_kkt_eval_noalloc(const rhpdhg_problem *lp, const double *x
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return RHPDHG_ERR_CUDA;
+  if (e != cudaSuccess) return kkt_finish("rhpdhg_kkt_eval_noalloc: cudaGetDevice", e, false);
   if (dev < 0 || dev >= kNoAllocMaxDevices) {
     set_global_error("rhpdhg_kkt_eval_noalloc: device ordinal out of range");
     return RHPDHG_ERR_INVALID_ARG;
@@ -232,9 +288,12 @@ extern "C" int rhpdhg_kkt_eval_noalloc(const rhpdhg_problem *lp, const double *x
     }
     base = g_noalloc_addr[dev];
   }
-  double *kty = base;                                            // cleared by the first kernel
-  double *part = base + kNoAllocMaxN;                            // fully rewritten per call
+  // kty and the index flag in dout are cleared by the first kernel; the used slots of every
+  // launched block's partials are written before the final sum reads them
+  double *kty = base;
+  double *part = base + kNoAllocMaxN;
   double *dout = part + (long long)kKktMaxBlocks * kKktSlotCount;
-  e = kkt_eval_with_scratch(lp, x, y, (cudaStream_t)stream, kty, part, dout, out);
-  return e == cudaSuccess ? RHPDHG_OK : RHPDHG_ERR_CUDA;
+  bool bad_index = false;
+  e = kkt_eval_with_scratch(lp, x, y, (cudaStream_t)stream, kty, part, dout, out, &bad_index);
+  return kkt_finish("rhpdhg_kkt_eval_noalloc", e, bad_index);
 }

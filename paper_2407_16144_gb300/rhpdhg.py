@@ -81,7 +81,8 @@ EXPORTED = ["rhpdhg_params_default", "rhpdhg_create", "rhpdhg_solve", "rhpdhg_po
             "rhpdhg_batch_remove", "rhpdhg_batch_slot_status", "rhpdhg_batch_free_bytes",
             "rhpdhg_batch_bytes_needed", "rhpdhg_batch_launch_count", "rhpdhg_batch_free",
             "rhpdhg_server_create", "rhpdhg_server_submit", "rhpdhg_server_poll",
-            "rhpdhg_server_cancel", "rhpdhg_server_stats", "rhpdhg_server_free"]
+            "rhpdhg_server_cancel", "rhpdhg_server_stats", "rhpdhg_server_free",
+            "rhpdhg_probe_fp64_fma_rate", "rhpdhg_probe_l2_read_bandwidth"]
 
 _lib = None
 
@@ -139,6 +140,8 @@ def load(path: str = LIB_PATH):
         "rhpdhg_server_cancel": (C.c_int, [H, C.c_int64]),
         "rhpdhg_server_stats": (C.c_int, [H, C.POINTER(C.c_int64)]),
         "rhpdhg_server_free": (None, [H]),
+        "rhpdhg_probe_fp64_fma_rate": (C.c_int, [C.c_void_p, _dp]),
+        "rhpdhg_probe_l2_read_bandwidth": (C.c_int, [C.c_int64, C.c_void_p, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +258,20 @@ def rhpdhg_kkt_eval_noalloc(lp: rhpdhg_problem, x, y, stream: int = 0):
     rc = load().rhpdhg_kkt_eval_noalloc(C.byref(lp), C.c_void_p(x), C.c_void_p(y or None),
                                         C.c_void_p(stream or None), out)
     return rc, list(out)
+
+
+def rhpdhg_probe_fp64_fma_rate(stream: int = 0):
+    """Returns (rc, FP64 FMA rate in TFLOP/s of the current device)."""
+    v = C.c_double()
+    rc = load().rhpdhg_probe_fp64_fma_rate(C.c_void_p(stream or None), C.byref(v))
+    return rc, v.value
+
+
+def rhpdhg_probe_l2_read_bandwidth(nbytes: int, stream: int = 0):
+    """Returns (rc, read bandwidth in GB/s of a device buffer of nbytes)."""
+    v = C.c_double()
+    rc = load().rhpdhg_probe_l2_read_bandwidth(nbytes, C.c_void_p(stream or None), C.byref(v))
+    return rc, v.value
 
 
 def rhpdhg_batch_create(max_slots: int, arena_bytes: int, stream: int = 0):

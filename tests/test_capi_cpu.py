@@ -31,7 +31,7 @@ def rh():
 def declared_functions():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(rhpdhg_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(rhpdhg_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_exports_every_declared_symbol(rh):
@@ -134,3 +134,49 @@ def test_release_cached_memory_without_handles(rh):
     """With no handle ever freed the buffer cache is empty: releasing it frees nothing and needs
     no device."""
     assert rh.release_cached_memory() == 0
+
+
+def test_restart_scheme_checked_on_host(rh):
+    """Restart schemes 0, 1 (fixed frequency) and 2 (two-phase) are accepted; any other value,
+    and a fixed or two-phase schedule without a positive period, are rejected before the device
+    is touched."""
+    arr = np.zeros(8)
+    rp = np.zeros(2, dtype=np.int64)
+    prob = rh.rhpdhg_problem()
+    prob.m_eq, prob.m_ineq, prob.n, prob.nnz = 1, 0, 3, 0
+    prob.row_ptr, prob.c, prob.l, prob.u, prob.rhs = (rp.ctypes.data, arr.ctypes.data,
+                                                      arr.ctypes.data, arr.ctypes.data,
+                                                      arr.ctypes.data)
+    for scheme, cap in ((3, 100), (-1, 100), (1, 0), (2, 0)):
+        p = rh.rhpdhg_params()
+        rh.rhpdhg_params_default(p)
+        p.restart_scheme, p.max_epoch_len = scheme, cap
+        rc, h = rh.rhpdhg_create(prob, p)
+        assert rc == rh.ERR_INVALID_ARG and not h.value, (scheme, cap)
+        assert "parameter" in rh.rhpdhg_last_error(None)
+
+
+@pytest.mark.parametrize("entry", ["rhpdhg_kkt_eval", "rhpdhg_kkt_eval_noalloc"])
+def test_kkt_eval_rejects_bad_arguments_with_a_message(rh, entry):
+    """Both KKT entry points reject host-memory problems, missing arrays and a CSR with entries
+    but no column indices on the host, and say why in rhpdhg_last_error(NULL)."""
+    fn = getattr(rh, entry)
+    arr = np.zeros(8)
+    rp = np.array([0, 2], dtype=np.int64)
+    prob = rh.rhpdhg_problem()
+    prob.m_eq, prob.m_ineq, prob.n, prob.nnz = 1, 0, 3, 2
+    prob.memory = rh.MEM_HOST
+    prob.row_ptr, prob.c, prob.l, prob.u, prob.rhs = (rp.ctypes.data, arr.ctypes.data,
+                                                      arr.ctypes.data, arr.ctypes.data,
+                                                      arr.ctypes.data)
+    prob.col_idx, prob.val = 16, 16
+    rc, _ = fn(prob, arr.ctypes.data, arr.ctypes.data)
+    assert rc == rh.ERR_INVALID_ARG and "device memory" in rh.rhpdhg_last_error(None)
+    prob.memory = rh.MEM_DEVICE
+    prob.col_idx = None
+    rc, _ = fn(prob, arr.ctypes.data, arr.ctypes.data)
+    assert rc == rh.ERR_INVALID_ARG and "missing" in rh.rhpdhg_last_error(None)
+    prob.col_idx = 16
+    prob.nnz = -1
+    rc, _ = fn(prob, arr.ctypes.data, arr.ctypes.data)
+    assert rc == rh.ERR_INVALID_ARG and "negative" in rh.rhpdhg_last_error(None)

@@ -111,6 +111,25 @@ def test_batch_certificates(rh, C):
             assert cd < 0 and v <= 1e-8
 
 
+@pytest.mark.parametrize("scheme", [1, 2])
+def test_batch_restart_schemes_match_oracle(rh, scheme):
+    """Fixed-frequency and two-phase restart schedules in batched slots: after 150 iterations
+    the PDHG points match the oracle's to 1e-10 and the restart counts are equal."""
+    lps = mix(seed0=60)
+    T = 150
+    common = dict(algorithm=1, eps_rel_kkt=1e-14, max_iters=T, check_every=16,
+                  restart_scheme=scheme, first_epoch_len=45, max_epoch_len=30)
+    with rh.Batch(16, 256 << 20) as b:
+        slots = [b.add(lp, **common) for lp in lps]
+        res = b.run_all(slots, iters=40)
+    for lp, s in zip(lps, slots):
+        r = res[s]
+        o = O.solve(lp, O.OracleParams(**common))
+        assert r.status == rh.STATUS_ITERATION_LIMIT and r.iters == T
+        assert r.restarts == o.restarts
+        assert rel(r.x, o.x) < 1e-10 and rel(r.y, o.y) < 1e-10, (lp.name, rel(r.x, o.x))
+
+
 def test_batch_capacity_limits(rh):
     lp = lpgen.make_c1(0)
     keep = []

@@ -590,3 +590,63 @@ def test_repeated_handles_bit_identical(rh, precision):
     # the freed handles' buffers are cached; releasing them returns their bytes, then nothing
     assert rh.release_cached_memory() > 0
     assert rh.release_cached_memory() == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("alg", [0, 1])
+@pytest.mark.parametrize("case", ["c1", "c2_small", "c3_small"])
+def test_restart_schemes_match_oracle(rh, case, alg, scheme, precision):
+    """The fixed-frequency schedule (eq. fixed-restart) and the two-phase schedule of the remark
+    after Theorem infeas (a first epoch of first_epoch_len, then every max_epoch_len) on the
+    device: over 200 iterations the (t, n, k) sequence and the restart iterations equal the
+    oracle's in both precisions (these schedules depend on k alone, so no tie can occur); in FP64
+    the fixed-point residual and the primal weight also agree to 1e-10, in mixed precision to
+    FP32 accuracy."""
+    lp = CASES[case]()
+    T = 200
+    common = dict(algorithm=alg, eps_rel_kkt=1e-14, restart_scheme=scheme, first_epoch_len=45,
+                  max_epoch_len=30, check_every=16)
+    o = O.solve(lp, O.OracleParams(max_iters=T, **common), trace=True)
+    with rh.Solver(lp, precision=precision, max_iters=T, trace=1, trace_capacity=256,
+                   **common) as s:
+        r = s.run()
+        tr = s.trace()
+    assert r.iters == T and len(tr) == T
+    want = [b[0] for b in o.trace if b[4]]
+    got = [a[0] for a in tr if a[4]]
+    assert got == want, (got, want)
+    first = 45 if scheme == 2 else 30
+    assert want[0] == first and all(b - a == 31 for a, b in zip(want, want[1:]))
+    tol, floor = (1e-10, 1e-8) if precision == 0 else (1e-3, 1e-6)
+    for (a, b) in zip(tr, o.trace):
+        assert a[:3] == b[:3]
+        assert abs(a[3] - b[3]) <= tol * max(abs(b[3]), floor * o.trace[0][3], 1e-300), \
+            (a[0], a[3], b[3])
+        assert abs(a[5] - b[5]) <= tol * b[5], (a[0], a[5], b[5])
+    assert r.restarts == o.restarts
+
+
+def test_kkt_eval_reports_out_of_range_columns(rh):
+    """The standalone KKT evaluation skips a column index outside [0, n) and a row with offsets
+    beyond nnz, and returns RHPDHG_ERR_INVALID_ARG with a message; both entry points."""
+    import torch
+    lp = CASES["c1"]()
+    x = torch.zeros(lp.n, dtype=torch.float64, device="cuda")
+    y = torch.zeros(lp.m, dtype=torch.float64, device="cuda")
+    for bad in ("column", "row"):
+        dlp = _device_lp(lp)
+        if bad == "column":
+            dlp.col_idx = dlp.col_idx.clone()
+            dlp.col_idx[5] = lp.n + 7
+        else:
+            dlp.row_ptr = dlp.row_ptr.clone()
+            dlp.row_ptr[3] = int(lp.row_ptr[-1]) + 100
+        prob = rh.device_problem(dlp)
+        for fn in (rh.rhpdhg_kkt_eval, rh.rhpdhg_kkt_eval_noalloc):
+            rc, _ = fn(prob, x.data_ptr(), y.data_ptr())
+            assert rc == rh.ERR_INVALID_ARG, (bad, fn.__name__)
+            assert "out of range" in rh.rhpdhg_last_error(None)
+    # the library stays usable: a valid evaluation right after succeeds
+    rc, out = rh.rhpdhg_kkt_eval(rh.device_problem(_device_lp(lp)), x.data_ptr(), y.data_ptr())
+    assert rc == rh.OK

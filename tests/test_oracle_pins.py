@@ -469,3 +469,77 @@ def test_iteration_limit_status():
     lp = lpgen.make_c1(0)
     r = O.solve(lp, O.OracleParams(eps_rel_kkt=1e-12, max_iters=100))
     assert r.status == O.ITERATION_LIMIT and r.iters == 100
+
+
+def _scaled_copy(lp, alpha=1.0, beta=1.0):
+    """The LP with objective alpha c and right-hand side and bounds beta (q, l, u)."""
+    import dataclasses
+    return dataclasses.replace(lp, c=alpha * lp.c, q=beta * lp.q, l=beta * lp.l, u=beta * lp.u,
+                               x_star=None, y_star=None)
+
+
+def _covariance_gaps(lp, alpha, beta, T=300):
+    """Largest relative deviation from exact covariance over T iterations of the restarted
+    method with primal-weight updates: with c -> alpha c and (q, l, u) -> beta (q, l, u) the
+    scaled iterates map as x -> beta x, y -> alpha y, the primal weight as omega -> omega
+    alpha / beta and the PDHG-norm residual as FPR^2 -> alpha beta FPR^2, and the restart
+    decisions are the same (the steps tau = eta / omega and sigma = eta omega absorb the
+    scalings in eq. pdhg).  Iterations after the residual has fallen to 1e-12 of its start are
+    rounding-dominated and are not compared.  Returns (restart flags equal, max omega gap, max FPR
+    gap, max iterate gap at the last compared snapshot, restarts compared)."""
+    common = dict(algorithm=1, eps_rel_kkt=1e-300, max_iters=T, first_epoch_len=20,
+                  check_every=10 ** 6, primal_weight_update=1)
+    snaps = list(range(25, T, 25))
+    a = O.solve(lp, O.OracleParams(**common), trace=True, snapshot_iters=snaps)
+    b = O.solve(_scaled_copy(lp, alpha, beta), O.OracleParams(**common), trace=True,
+                snapshot_iters=snaps)
+    f0 = a.trace[0][3]
+    stop = next((i for i, r in enumerate(a.trace) if r[3] < 1e-12 * f0), len(a.trace))
+    stop = min(stop, len(b.trace))
+    ta, tb = a.trace[:stop], b.trace[:stop]
+    same = [r[4] for r in ta] == [r[4] for r in tb]
+    om = max(abs(rb[5] - ra[5] * alpha / beta) / (ra[5] * alpha / beta)
+             for ra, rb in zip(ta, tb))
+    fp = max(abs(rb[3] - ra[3] * alpha * beta) / max(ra[3] * alpha * beta, 1e-300)
+             for ra, rb in zip(ta, tb))
+    last = max((t for t in snaps if t < stop and t in a.snapshots and t in b.snapshots),
+               default=None)
+    it = np.inf
+    if last is not None:
+        sa, sb = a.snapshots[last], b.snapshots[last]
+        it = max(np.abs(sb["xt"] - beta * sa["xt"]).max() /
+                 max(1.0, np.abs(beta * sa["xt"]).max()),
+                 np.abs(sb["yt"] - alpha * sa["yt"]).max() /
+                 max(1.0, np.abs(alpha * sa["yt"]).max()))
+    nrestarts = sum(r[4] for r in ta)
+    return same, om, fp, it, nrestarts
+
+
+@pytest.mark.parametrize("make", [lambda: lpgen.make_c1(0),
+                                  lambda: lpgen.make_tiny_general(4, 3, 3, 8)])
+def test_primal_weight_update_is_scale_covariant(make):
+    """The primal-weight update (Section 7 names it without a definition; the oracle takes the
+    smoothed rule omega <- sqrt(omega * dy / dx) over anchor movements) keeps the exact
+    covariance of the method under c -> 2 c and under (q, l, u) -> 4 (q, l, u).  Powers of two
+    keep every step exact except the update's logarithm and exponential, so the two runs agree
+    to rounding.  The run has several restarts, so the update is exercised."""
+    lp = make()
+    for alpha, beta in ((2.0, 1.0), (1.0, 4.0), (2.0, 4.0)):
+        same, om, fp, it, nr = _covariance_gaps(lp, alpha, beta)
+        assert nr >= 3
+        assert same and om < 1e-9 and fp < 1e-8 and it < 1e-9, (alpha, beta, om, fp, it)
+
+
+def test_primal_weight_covariance_catches_a_wrong_update(monkeypatch):
+    """The covariance pin above fails for plausible mistakes in the update, planted in the
+    oracle: the ratio inverted (dx / dy), or the movement ratio taken without the old weight
+    (not of degree one)."""
+    lp = lpgen.make_c1(0)
+    wrong = {
+        "inverted": lambda om, dx, dy: math.exp(0.5 * math.log(dx / dy) + 0.5 * math.log(om)),
+        "no smoothing of omega, ratio squared": lambda om, dx, dy: (dy / dx) ** 2,
+    }
+    for name, fn in wrong.items():
+        monkeypatch.setattr(O, "primal_weight_update", fn)
+        same, om, fp, it, nr = _covariance_gaps(lp, 2.0, 1.0)
+        assert not (same and om < 1e-6 and it < 1e-6), name
