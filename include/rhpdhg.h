@@ -30,6 +30,7 @@
 #ifndef RHPDHG_H
 #define RHPDHG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -97,6 +98,15 @@ typedef struct {
   double obj_offset;
 } rhpdhg_problem;
 
+/* A caller's device allocator (for instance a framework's caching allocator), used by
+ * rhpdhg_create for every device buffer of the handle and for its own temporaries.  alloc
+ * returns `bytes` of device memory of the current device, aligned to 256 bytes, usable on
+ * cuda_stream (the handle's stream), or NULL when it cannot; free takes back a pointer alloc
+ * returned, with the same stream and ctx.  The library calls free only when no work on the
+ * buffer is pending, from the thread that calls rhpdhg_free (or rhpdhg_create, on failure). */
+typedef void *(*rhpdhg_dev_alloc_fn)(size_t bytes, void *cuda_stream, void *ctx);
+typedef void (*rhpdhg_dev_free_fn)(void *ptr, void *cuda_stream, void *ctx);
+
 /* Algorithm parameters.  rhpdhg_params_default() fills the documented defaults. */
 typedef struct {
   int32_t algorithm;            /* 0 = rHPDHG (Algorithm 1, eq. hpdhg); 1 = r2HPDHG
@@ -140,7 +150,15 @@ typedef struct {
                                    next one is min((1 - j^-0.3) eta_bar, (1 + j^-0.6) eta) with
                                    j = iteration + 2, and a rejected step is redone with it.
                                    precision 0 only; not in batched slots.       default 0    */
+  int32_t cta_warps;            /* warps per CTA of the iteration kernels: 4, 8 or 16; 0 = the
+                                   library's choice.                              default 0    */
   int32_t reserved;
+  /* Caller's allocator for the handle's device memory (both functions or neither; NULL = the
+   * library's own cache of device buffers), with its context pointer.  Used by rhpdhg_create
+   * only; the batched solver and the server ignore it.                          default NULL */
+  rhpdhg_dev_alloc_fn dev_alloc;
+  rhpdhg_dev_free_fn  dev_free;
+  void *alloc_ctx;
 } rhpdhg_params;
 
 /* Result of a finished solve, filled by rhpdhg_poll. */
@@ -239,10 +257,10 @@ int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t cap
  * K^ and on K^T; the staging stride (entries per warp) of K^ and of K^T; the walk of the
  * ordinary mixed-precision kernels on K^ and on K^T (0 = one tile per item, 1 = one tile per
  * item with twice the loads in flight per staging round, 2 = groups of tiles per item; 0 for
- * FP64 handles).
+ * FP64 handles); warps per CTA of the row kernels and of the column kernels.
  * capacity: entries available at out.  Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG for a NULL
  * handle or out, or capacity < RHPDHG_LAYOUT_FIELDS. */
-#define RHPDHG_LAYOUT_FIELDS 12
+#define RHPDHG_LAYOUT_FIELDS 14
 int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity);
 
 /* Handles take their device buffers from a process-wide cache of buffers freed by earlier

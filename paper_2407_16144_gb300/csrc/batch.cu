@@ -264,8 +264,7 @@ __device__ void batch_setup(const BatchDesc &d, double *sh) {
     ctl->restart_pending = 1;
     ctl->w = 0.0;
     ctl->omega = om0;
-    ctl->tau = eta / om0;
-    ctl->sigma = eta * om0;
+    set_steps(ctl, eta, om0);
     ctl->eta = eta;
     ctl->stage = 1;
     ctl->check_t = -1;

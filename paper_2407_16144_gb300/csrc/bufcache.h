@@ -18,4 +18,27 @@ void buf_release(void *p);
 // Frees every cached buffer; returns the bytes freed.
 size_t buf_drop_cache();
 
+// A caller's device allocator (rhpdhg_params.dev_alloc, dev_free, alloc_ctx) and the stream its
+// buffers are used on.  While an AllocScope is alive on a thread, buf_alloc on that thread takes
+// buffers from it; buf_release (on any thread) hands such a buffer back to the allocator's own
+// free function and never caches it.
+struct DevAllocator {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx) = nullptr;
+  void (*free)(void *ptr, void *stream, void *ctx) = nullptr;
+  void *ctx = nullptr;
+  void *stream = nullptr;
+};
+
+class AllocScope {
+ public:
+  explicit AllocScope(const DevAllocator &a);
+  ~AllocScope();
+  AllocScope(const AllocScope &) = delete;
+  AllocScope &operator=(const AllocScope &) = delete;
+
+ private:
+  const DevAllocator *prev_;
+  DevAllocator mine_;
+};
+
 }  // namespace rh

@@ -166,6 +166,42 @@ void algorithmic_bytes(rhpdhg_handle *h) {
   h->bytes_col = nnz * (vb + ib) + (h->n + 1) * ib + h->m * vb + h->n * vb * col_vec;
 }
 
+// Launch geometry of the iteration kernels for CTAs of wr warps (row side) and wc warps (column
+// side): dynamic shared memory for each warp's staging area, the walk instantiation of the
+// ordinary mixed row kernel (wide_row: 1 = the wide staging round, 0 = the plain walk, -1 = the
+// rule below) and grids of one work item per warp within the resident CTAs.
+void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
+  SideLayout &lr = h->rows.lay, &lc = h->cols.lay;
+  lr.cta_warps = wr;
+  lc.cta_warps = wc;
+  h->smem_row = wr * lr.seg * (int)sizeof(double);
+  h->smem_col = wc * lc.seg * (int)sizeof(double);
+  if (h->mixed) {
+    lr.walk = lr.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
+    lc.walk = lc.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
+    // The row kernels stage twice as many groups per round (fewer dependent rounds, more
+    // registers) when their tiles are long and the grid stays set by the tile count at the
+    // wider kernel's residency, so that the registers cost no CTAs.
+    if (lr.walk == kWalkPlain && lr.n_short_tiles > 0) {
+      bool wide = wide_row == 1;
+      if (wide_row < 0 &&
+          h->rows.nnz_short > (long long)lr.n_short_tiles * kWarp * kStageUnroll * 4) {
+        const int bw = iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide, wr * kWarp);
+        const long long need = ((long long)lr.total_items() + wr - 1) / wr;
+        wide = bw > 0 && need <= (long long)bw * h->sm_count;
+      }
+      if (wide) lr.walk = kWalkWide;
+    }
+    h->grid_row = tile_grid(lr, h->sm_count,
+                            iter_mx_blocks_per_sm(h->smem_row, true, lr.walk, wr * kWarp));
+    h->grid_col = tile_grid(lc, h->sm_count,
+                            iter_mx_blocks_per_sm(h->smem_col, false, lc.walk, wc * kWarp));
+  } else {
+    h->grid_row = tile_grid(lr, h->sm_count, row_iter_blocks_per_sm(h->smem_row, wr * kWarp));
+    h->grid_col = tile_grid(lc, h->sm_count, col_iter_blocks_per_sm(h->smem_col, wc * kWarp));
+  }
+}
+
 void launch_row(rhpdhg_handle *h) {
   if (h->mixed)
     launch_row_iter_mx(h->st, h->rows, h->rvm, h->dxt, h->dxt64, h->x0, h->ctl, h->part_row,
@@ -212,8 +248,7 @@ int reset_state(rhpdhg_handle *h) {
   c.stage = 1;           // the set-up column kernel runs first
   c.w = 0.0;
   c.omega = h->omega0;
-  c.tau = h->eta / h->omega0;
-  c.sigma = h->eta * h->omega0;
+  set_steps(&c, h->eta, h->omega0);
   c.eta = h->eta;
   CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
   CK(cudaMemsetAsync(h->act, 0, (size_t)std::max(h->n, 1), h->st));
@@ -470,8 +505,12 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
       P.first_epoch_len < 0 || P.max_epoch_len < 0 || P.restart_scheme < 0 ||
       P.restart_scheme > 2 || (P.restart_scheme >= 1 && P.max_epoch_len < 1) ||
       !(P.restart_beta > 0 && P.restart_beta < 1) || P.trace_capacity < 0 ||
-      P.pock_chambolle_alpha > 2.0 || P.adaptive_step < 0 || P.adaptive_step > 1)
+      P.pock_chambolle_alpha > 2.0 || P.adaptive_step < 0 || P.adaptive_step > 1 ||
+      (P.cta_warps != 0 && P.cta_warps != 4 && P.cta_warps != 8 && P.cta_warps != 16))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "invalid parameter");
+  if ((P.dev_alloc == nullptr) != (P.dev_free == nullptr))
+    return set_err(nullptr, RHPDHG_ERR_INVALID_ARG,
+                   "invalid parameter: dev_alloc and dev_free are given together or not at all");
   if (P.adaptive_step && P.precision == 1)
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG,
                    "the adaptive step rule runs with precision 0 (FP64) only");
@@ -515,6 +554,13 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     h->own_stream = true;
   }
   CKC(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->dev));
+  // every device buffer of this create comes from the caller's allocator when one is given
+  DevAllocator hook;
+  hook.alloc = P.dev_alloc;
+  hook.free = P.dev_free;
+  hook.ctx = P.alloc_ctx;
+  hook.stream = (void *)h->st;
+  AllocScope alloc_scope(hook);
   const int n = h->n;
   const int nnz = (int)h->nnz;
   const cudaStream_t st = h->st;
@@ -640,29 +686,13 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   free_tmp();
 
   // ---- launch geometry ----
-  h->smem_row = kBlockWarps * h->rows.lay.seg * (int)sizeof(double);
-  h->smem_col = kBlockWarps * h->cols.lay.seg * (int)sizeof(double);
   allow_large_smem(kMaxTileSmem);
   allow_large_smem_setup(kMaxTileSmem);
   allow_large_smem_mx(kMaxTileSmem);
-  if (h->mixed) {
-    SideLayout &lr = h->rows.lay, &lc = h->cols.lay;
-    lr.walk = lr.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
-    lc.walk = lc.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
-    // The row kernels stage twice as many groups per round (fewer dependent rounds, more
-    // registers) when their tiles are long and the grid stays set by the tile count at the
-    // wider kernel's residency, so that the registers cost no CTAs.
-    if (lr.walk == kWalkPlain && lr.n_short_tiles > 0 &&
-        h->rows.nnz_short > (long long)lr.n_short_tiles * kWarp * kStageUnroll * 4) {
-      const int bw = iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide);
-      const long long need = ((long long)lr.total_items() + kBlockWarps - 1) / kBlockWarps;
-      if (bw > 0 && need <= (long long)bw * h->sm_count) lr.walk = kWalkWide;
-    }
-    h->grid_row = tile_grid(lr, h->sm_count, iter_mx_blocks_per_sm(h->smem_row, true, lr.walk));
-    h->grid_col = tile_grid(lc, h->sm_count, iter_mx_blocks_per_sm(h->smem_col, false, lc.walk));
-  } else {
-    h->grid_row = tile_grid(h->rows.lay, h->sm_count, row_iter_blocks_per_sm(h->smem_row));
-    h->grid_col = tile_grid(h->cols.lay, h->sm_count, col_iter_blocks_per_sm(h->smem_col));
+  {
+    const int wr = P.cta_warps > 0 ? P.cta_warps : kBlockWarps;
+    const int wc = P.cta_warps > 0 ? P.cta_warps : kBlockWarps;
+    set_geometry(h, wr, wc, -1);
   }
 
   // ---- power iteration for sigma_max(K^) ----
@@ -890,7 +920,8 @@ int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity) {
   const SideLayout &r = h->rows.lay, &c = h->cols.lay;
   const int64_t v[RHPDHG_LAYOUT_FIELDS] = {h->grid_row,  h->grid_col,  r.tile_mult, c.tile_mult,
                                            r.n_long,     c.n_long,     r.n_chunks,  c.n_chunks,
-                                           r.seg,        c.seg,        r.walk,      c.walk};
+                                           r.seg,        c.seg,        r.walk,      c.walk,
+                                           r.cta_warps,  c.cta_warps};
   for (int i = 0; i < RHPDHG_LAYOUT_FIELDS; ++i) out[i] = v[i];
   return RHPDHG_OK;
 }

@@ -24,12 +24,16 @@ namespace rh {
 
 constexpr int kWarp = 32;
 constexpr int kTileRows = 32;          // rows per tile = lanes per warp
-constexpr int kBlockWarps = 4;         // warps per CTA of the tile kernels
+constexpr int kBlockWarps = 4;         // default warps per CTA of the tile kernels
 constexpr int kBlockThreads = kBlockWarps * kWarp;
+constexpr int kMaxBlockWarps = 16;     // widest CTA of the tile kernels (the width is a launch
+                                       // parameter: walk and reductions read blockDim.x)
+constexpr int kMaxBlockThreads = kMaxBlockWarps * kWarp;
 constexpr int kMaxPartials = 20;       // reduction slots per CTA
 constexpr int kShortMax = 128;         // rows with more entries are always long
 constexpr int kSegBudget = 1024;       // entries of one tile's short segment (staging area)
-constexpr int kMaxTileSmem = kBlockWarps * (kSegBudget + 8) * 8;   // bytes, FP64 staging
+constexpr int kMaxTileSmem = kMaxBlockWarps * (kSegBudget + 8) * 8;   // bytes, FP64 staging
+                                                                      // at the widest CTA
 constexpr int kChunk = 256;            // entries per long-row chunk (8 per lane)
 constexpr int kStageUnroll = 2;        // 4-entry groups staged per lane per round
 constexpr int kMaxTileMult = 4;        // most short tiles walked as one work item
@@ -76,6 +80,7 @@ struct SideLayout {
   const int *chunk_row = nullptr;   // n_chunks: long-row index of each chunk
   int tile_mult = 1;         // consecutive short tiles per work item (1 .. kMaxTileMult)
   int walk = 0;              // instantiation of the ordinary mixed kernels' walk (kWalk*)
+  int cta_warps = kBlockWarps;  // warps per CTA of this side's iteration kernels (host only)
   int n_tile_groups = 0;     // ceil(n_short_tiles / tile_mult)
   __host__ __device__ int total_items() const { return n_chunks + n_tile_groups; }
 };
@@ -107,6 +112,8 @@ struct Ctl {
   int restart_pending;   // 1: iterate t+1 is the restart point T(z^{n,k})
   double w;              // Halpern weight (k+1)/(k+2) of the pending blend
   double omega, tau, sigma, eta;
+  double tau_inv, sigma_inv;   // 1 / tau, 1 / sigma (set with tau and sigma: the restart test
+                               // multiplies instead of dividing on the narrow FP64 pipe)
   double fpr0_sq;        // ||z^{n,0} - T(z^{n,0})||_P^2
   double fpr_sq;         // last ||z - T(z)||_P^2
   double dx_sq;          // ||x_t - x~_t||^2          (column kernel -> next row kernel)
@@ -136,6 +143,14 @@ struct Ctl {
                          // (each finalisation advances it, so of two kernels launched for the
                          // same stage only the first one whose mode matches does the work)
 };
+
+// Primal and dual steps tau = eta / omega, sigma = eta omega and their reciprocals.
+__host__ __device__ __forceinline__ void set_steps(Ctl *ctl, double eta, double omega) {
+  ctl->tau = eta / omega;
+  ctl->sigma = eta * omega;
+  ctl->tau_inv = 1.0 / ctl->tau;
+  ctl->sigma_inv = 1.0 / ctl->sigma;
+}
 
 struct TraceRec {      // mirrors rhpdhg_trace_rec
   long long t, epoch, k;
@@ -186,36 +201,124 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// Per-thread accumulators of NS sums and NM maxima, reduced per CTA in a fixed order.
-template <int NS, int NM>
+// ---------------------------------------------------------------------------------------------
+// Double-float sums.  The FP64 pipe of this part is narrow (about 2 FP64 operations per clock per
+// SM, against 128 FP32), so the per-iteration sums of the mixed-precision kernels are carried as
+// double-floats: an unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi) / 2), updated
+// with error-free transformations on the FP32 pipe.  Products of two FP32 numbers are exact
+// (FMA-based TwoProd) and a sum of double-floats has a relative error of at most 3 u^2 with
+// u = 2^-24 (Joldes, Muller and Popescu, "Tight and rigorous error bounds for basic building
+// blocks of double-word arithmetic", 2017, Algorithm 6), so the sums carry about 46 bits where
+// plain FP32 sums carry 24.  The _rn intrinsics keep the compiler from contracting or
+// reassociating the transformations.
+
+struct DF {
+  float hi, lo;
+};
+
+// s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker's Fast2Sum)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  float sh, sl, th, tl, vh, vl;
+  two_sum(x.hi, y.hi, sh, sl);
+  two_sum(x.lo, y.lo, th, tl);
+  fast_two_sum(sh, __fadd_rn(sl, th), vh, vl);
+  DF z;
+  fast_two_sum(vh, __fadd_rn(tl, vl), z.hi, z.lo);
+  return z;
+}
+
+// a * b exactly (while the product neither overflows nor underflows FP32)
+__device__ __forceinline__ DF df_prod(float a, float b) {
+  DF r;
+  r.hi = __fmul_rn(a, b);
+  r.lo = __fmaf_rn(a, b, -r.hi);
+  return r;
+}
+
+__device__ __forceinline__ DF df_warp_sum(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+// A double-float travels through the 8-byte partial slots bit-packed (no FP64 arithmetic).
+__device__ __forceinline__ double df_pack(DF a) {
+  return __hiloint2double(__float_as_int(a.hi), __float_as_int(a.lo));
+}
+__device__ __forceinline__ DF df_unpack(double v) {
+  DF r;
+  r.hi = __int_as_float(__double2hiint(v));
+  r.lo = __int_as_float(__double2loint(v));
+  return r;
+}
+__device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
+
+// Per-thread accumulators of NS sums and NM maxima, reduced per CTA in a fixed order.  The first
+// ND sums are double-floats (d[0 .. ND-1]; s[0 .. ND-1] are unused), the others FP64.
+template <int NS, int NM, int ND = 0>
 struct Acc {
   double s[NS > 0 ? NS : 1];
   double mx[NM > 0 ? NM : 1];
+  DF d[ND > 0 ? ND : 1];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < NS; ++i) s[i] = 0.0;
 #pragma unroll
     for (int i = 0; i < NM; ++i) mx[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) d[i] = DF{0.f, 0.f};
   }
 };
 
+// Per-warp results of a CTA-level reduction; cta_reduce_and_ticket and grid_finish use it one
+// after the other (each ends with a barrier).
+__device__ __forceinline__ double (*cta_red())[kMaxPartials] {
+  __shared__ double red[kMaxBlockWarps][kMaxPartials];
+  return red;
+}
+
 // Reduce Acc over the CTA (deterministic: fixed shuffle tree, warps summed in index order) and
-// write the CTA's partials to part[blockIdx.x * kMaxPartials + slot].  Only the slots set in
-// smask (sums) and mmask (maxima) are reduced and written; slots set in prewarp hold, in lane 0,
-// a value already summed over the warp.  Returns true in every thread of the last CTA to finish
-// (after a fence), which then owns the grid-level reduction.
-template <int NS, int NM>
-__device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, unsigned smask, unsigned mmask,
+// write the CTA's partials to part[blockIdx.x * kMaxPartials + slot] (double-float slots
+// bit-packed).  Only the slots set in smask (sums) and mmask (maxima) are reduced and written;
+// slots set in prewarp hold, in lane 0, a value already summed over the warp (FP64 slots only).
+// Returns true in every thread of the last CTA to finish (after a fence), which then owns the
+// grid-level reduction.
+template <int NS, int NM, int ND>
+__device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND> &a, unsigned smask, unsigned mmask,
                                       unsigned prewarp, double *part, unsigned int *ticket) {
-  __shared__ double red[kBlockWarps][kMaxPartials];
+  double (*red)[kMaxPartials] = cta_red();
   __shared__ bool last;
   static_assert(NS + NM <= kMaxPartials, "too many partial slots");
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  static_assert(ND <= NS, "double-float slots are sums");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     if (!((smask >> i) & 1u)) continue;
-    const double v = ((prewarp >> i) & 1u) ? a.s[i] : warp_sum(a.s[i]);
-    if (lane == 0) red[warp][i] = v;
+    if (i < ND) {
+      const DF v = df_warp_sum(a.d[i < ND ? i : 0]);
+      if (lane == 0) red[warp][i] = df_pack(v);
+    } else {
+      const double v = ((prewarp >> i) & 1u) ? a.s[i] : warp_sum(a.s[i]);
+      if (lane == 0) red[warp][i] = v;
+    }
   }
 #pragma unroll
   for (int i = 0; i < NM; ++i) {
@@ -229,15 +332,21 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, unsigned smask, unsigned m
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       if (!((smask >> i) & 1u)) continue;
-      double v = red[0][i];
-      for (int w = 1; w < kBlockWarps; ++w) v += red[w][i];
-      dst[i] = v;
+      if (i < ND) {
+        DF v = df_unpack(red[0][i]);
+        for (int w = 1; w < nw; ++w) v = df_add(v, df_unpack(red[w][i]));
+        dst[i] = df_pack(v);
+      } else {
+        double v = red[0][i];
+        for (int w = 1; w < nw; ++w) v += red[w][i];
+        dst[i] = v;
+      }
     }
 #pragma unroll
     for (int i = 0; i < NM; ++i) {
       if (!((mmask >> i) & 1u)) continue;
       double v = red[0][NS + i];
-      for (int w = 1; w < kBlockWarps; ++w) v = fmax(v, red[w][NS + i]);
+      for (int w = 1; w < nw; ++w) v = fmax(v, red[w][NS + i]);
       dst[NS + i] = v;
     }
     __threadfence();
@@ -250,24 +359,30 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM> &a, unsigned smask, unsigned m
 }
 
 // Warp-collective: reduce the long-row sums al of every lane and store them as group grp's
-// partials (lane 0), then clear al.  Only sums need this (their order decides the rounding);
-// long-row maxima are taken into the finishing warp's own accumulator.
-template <int NS>
-__device__ __forceinline__ void store_group(Acc<NS, 0> &al, unsigned smask, double *gpart,
+// partials (lane 0; double-float slots bit-packed), then clear al.  Only sums need this (their
+// order decides the rounding); long-row maxima are taken into the finishing warp's own
+// accumulator.
+template <int NS, int ND>
+__device__ __forceinline__ void store_group(Acc<NS, 0, ND> &al, unsigned smask, double *gpart,
                                             int grp) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     if (!((smask >> i) & 1u)) continue;
-    const double v = warp_sum(al.s[i]);
-    if (lane == 0) gpart[(size_t)grp * kMaxPartials + i] = v;
+    if (i < ND) {
+      const DF v = df_warp_sum(al.d[i < ND ? i : 0]);
+      if (lane == 0) gpart[(size_t)grp * kMaxPartials + i] = df_pack(v);
+    } else {
+      const double v = warp_sum(al.s[i]);
+      if (lane == 0) gpart[(size_t)grp * kMaxPartials + i] = v;
+    }
   }
   al.zero();
 }
 
 // In the last CTA: reduce the grid's partials in block order, then the long-row groups'
-// partials in group order, for the slots in the masks (others return 0).  out[i] valid in all
-// threads.
+// partials in group order, for the slots in the masks (others return 0; the first ND sums are
+// double-floats, returned as hi + lo).  out[i] valid in all threads.
 //
 // Thread t sums blocks t, t + blockDim, ... of each slot in that order, then groups t,
 // t + blockDim, ...; each warp reduces its lanes with a fixed shuffle tree and the warps' results
@@ -279,15 +394,23 @@ __device__ __forceinline__ void store_group(Acc<NS, 0> &al, unsigned smask, doub
 // BATCH = false keeps only the first (the FP64 kernels: ALU-bound, with fewer CTAs, where the
 // second gains nothing and its registers cost).
 constexpr int kGridBatch = 10;
-template <int NS, int NM, bool BATCH = true>
+template <int NS, int NM, bool BATCH = true, int ND = 0>
 __device__ void grid_finish(const double *part, double *out, unsigned smask, unsigned mmask,
                             const double *gpart = nullptr, int ngroups = 0) {
-  __shared__ double red[kBlockWarps][kMaxPartials];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double (*red)[kMaxPartials] = cta_red();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nb = gridDim.x;
   double v[NS + NM];
+  DF vd[ND > 0 ? ND : 1];
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) v[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < ND; ++i) vd[i] = DF{0.f, 0.f};
+  // one partial p of slot i into the thread's running value
+  auto take = [&](int i, double p) {
+    if (i < ND) vd[i < ND ? i : 0] = df_add(vd[i < ND ? i : 0], df_unpack(p));
+    else v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
+  };
   const unsigned all = smask | (mmask << NS);
   const int rounds_by_block = (nb + (int)blockDim.x - 1) / (int)blockDim.x;
   if (!BATCH || rounds_by_block <= __popc(all)) {
@@ -297,8 +420,7 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 #pragma unroll
       for (int i = 0; i < NS + NM; ++i) {
         if (!((all >> i) & 1u)) continue;
-        const double p = __ldcg(src + i);
-        v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
+        take(i, __ldcg(src + i));
       }
     }
   } else {
@@ -313,7 +435,7 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
           p[j] = b < nb ? __ldcg(part + (size_t)b * kMaxPartials + i) : 0.0;
         }
 #pragma unroll
-        for (int j = 0; j < kGridBatch; ++j) v[i] = (i < NS) ? v[i] + p[j] : fmax(v[i], p[j]);
+        for (int j = 0; j < kGridBatch; ++j) take(i, p[j]);
       }
     }
   }
@@ -323,22 +445,33 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       if (!((smask >> i) & 1u)) continue;
-      v[i] += __ldcg(src + i);
+      take(i, __ldcg(src + i));
     }
   }
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) {
     if (!((all >> i) & 1u)) continue;
-    const double r = (i < NS) ? warp_sum(v[i]) : warp_max(v[i]);
-    if (lane == 0) red[warp][i] = r;
+    if (i < ND) {
+      const DF r = df_warp_sum(vd[i < ND ? i : 0]);
+      if (lane == 0) red[warp][i] = df_pack(r);
+    } else {
+      const double r = (i < NS) ? warp_sum(v[i]) : warp_max(v[i]);
+      if (lane == 0) red[warp][i] = r;
+    }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NS + NM; ++i) {
     if (!((all >> i) & 1u)) { out[i] = 0.0; continue; }
-    double r = red[0][i];
-    for (int w = 1; w < kBlockWarps; ++w) r = (i < NS) ? r + red[w][i] : fmax(r, red[w][i]);
-    out[i] = r;
+    if (i < ND) {
+      DF r = df_unpack(red[0][i]);
+      for (int w = 1; w < nw; ++w) r = df_add(r, df_unpack(red[w][i]));
+      out[i] = df_value(r);
+    } else {
+      double r = red[0][i];
+      for (int w = 1; w < nw; ++w) r = (i < NS) ? r + red[w][i] : fmax(r, red[w][i]);
+      out[i] = r;
+    }
   }
   __syncthreads();
 }
@@ -547,8 +680,8 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
                                            Epi &epi, GroupDone &gdone,
                                            const Pre &pre = Pre()) {
   const int lane = threadIdx.x & 31;
-  const int gwarp = blockIdx.x * kBlockWarps + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * kBlockWarps;
+  const int gwarp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
   const int total = lay.total_items();
   for (int item = gwarp; item < total; item += nwarps) {
     if (item < lay.n_chunks) {

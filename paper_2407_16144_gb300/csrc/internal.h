@@ -103,7 +103,8 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
                        const double *val, const double *rscale, const double *cscale,
                        bool with32, SideStore *out);
 void free_side(SideStore *s);
-// Launch geometry of the tile kernels for a side with L.
+// Launch geometry of the tile kernels for a side with L: enough CTAs of lay.cta_warps warps for
+// one work item per warp, at most blocks_per_sm resident CTAs per SM.
 int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm);
 // out = side * src   (plain product, FP64)
 void side_spmv(cudaStream_t st, const SideStore &side, const double *src, double *out, int grid);
@@ -133,7 +134,7 @@ void launch_col_iter(cudaStream_t st, const SideStore &side, const double *yt, c
 // x_out = E .* xout ; y_out = D .* yt
 void launch_unscale(cudaStream_t st, int n, int m, const double *e, const double *xs,
                     const double *d, const double *ys, double *xo, double *yo);
-int row_iter_blocks_per_sm(int smem);
+int row_iter_blocks_per_sm(int smem, int threads);
 
 // ---- standalone KKT evaluation (kkt.cu) --------------------------------------------------------
 constexpr int kKktMaxBlocks = 1024;   // block partials of the evaluation kernels
@@ -158,11 +159,11 @@ void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const dou
 void zero_f32(cudaStream_t st, int n, float *x);
 void allow_large_smem_mx(int bytes);
 // Resident CTAs per SM of the ordinary mixed kernels of one side (row: K^, else K^T) in one
-// walk instantiation (kWalk*).
-int iter_mx_blocks_per_sm(int smem, bool row, int walk);
+// walk instantiation (kWalk*), for CTAs of `threads` threads.
+int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads);
 // opt in to dynamic shared memory above 48 KB for the tile kernels
 void allow_large_smem(int bytes);
 void allow_large_smem_setup(int bytes);
-int col_iter_blocks_per_sm(int smem);
+int col_iter_blocks_per_sm(int smem, int threads);
 
 }  // namespace rh

@@ -91,8 +91,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
       ctl->retries += 1;
       if (ctl->retries > 64 || !(nxt > 0.0) || !isfinite(nxt)) ctl->status = kNumericalError;
       ctl->eta = nxt;
-      ctl->tau = nxt / omega;
-      ctl->sigma = nxt * omega;
+      set_steps(ctl, nxt, omega);
       ctl->redo = 1;
       ctl->cnt_row = 0;
       ctl->stage = 1;
@@ -100,7 +99,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
     }
     ctl->eta_next = nxt;
   }
-  const double fpr2 = ctl->dx_sq / tau + r[0] / sigma + 2.0 * r[1];
+  const double fpr2 = ctl->dx_sq * ctl->tau_inv + r[0] * ctl->sigma_inv + 2.0 * r[1];
   const double fpr0 = (k == 0) ? fpr2 : ctl->fpr0_sq;
   bool rs;
   if (ic.restart_scheme == 1) {
@@ -131,8 +130,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
   const double eta_now = ic.adaptive ? ctl->eta_next : ic.eta;
   if (ic.adaptive) {
     ctl->eta = eta_now;
-    ctl->tau = eta_now / omega;
-    ctl->sigma = eta_now * omega;
+    set_steps(ctl, eta_now, omega);
     ctl->redo = 0;
     ctl->retries = 0;
   }
@@ -143,8 +141,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
       if (dxa > 1e-10 && dya > 1e-10 && ratio > 0.0 && isfinite(ratio)) {
         const double om = exp(0.5 * log(ratio) + 0.5 * log(omega));
         ctl->omega = om;
-        ctl->tau = eta_now / om;
-        ctl->sigma = eta_now * om;
+        set_steps(ctl, eta_now, om);
       }
     }
     ctl->k_next = 0;

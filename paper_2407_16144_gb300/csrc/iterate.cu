@@ -25,12 +25,12 @@ namespace rh {
 
 namespace {
 
-// The FP64 iteration kernels are bound by the FP64 pipe; four resident CTAs per SM (128
-// registers a thread) keep it busy, and the register cap keeps the grid at that size.
-constexpr int kFp64BlocksPerSm = 4;
+// The FP64 iteration kernels are bound by the FP64 pipe; 128 registers a thread (16 resident
+// warps per SM) keep it busy, and the register cap keeps the grid at that size.
+constexpr int kFp64MaxRegs = 128;
 
 template <int RHO2, bool GRP>
-__global__ void __launch_bounds__(kBlockThreads, kFp64BlocksPerSm)
+__global__ void __maxnreg__(kFp64MaxRegs)
 k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ xt,
            RowVecs v, Ctl *ctl, double *part, IterConsts ic) {
   extern __shared__ double smem[];
@@ -69,7 +69,7 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
 }
 
 template <int RHO2, bool GRP>
-__global__ void __launch_bounds__(kBlockThreads, kFp64BlocksPerSm)
+__global__ void __maxnreg__(kFp64MaxRegs)
 k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ ytv,
            ColVecs v, Ctl *ctl, double *part, IterConsts ic, int phase) {
   extern __shared__ double smem[];
@@ -142,8 +142,9 @@ __global__ void k_unscale(int n, int m, const double *e, const double *xs, const
 // GRP: the grouped walk for sides whose short tiles are walked several at a time.
 void launch_row_iter(cudaStream_t st, const SideStore &side, const double *xt, const RowVecs &v,
                      Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem) {
+  const int threads = side.lay.cta_warps * kWarp;
   auto go = [&](auto kern) {
-    kern<<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl, part, ic);
+    kern<<<grid, threads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl, part, ic);
   };
   const bool grp = side.lay.tile_mult > 1;
   if (ic.rho2) grp ? go(k_row_iter<1, true>) : go(k_row_iter<1, false>);
@@ -153,9 +154,9 @@ void launch_row_iter(cudaStream_t st, const SideStore &side, const double *xt, c
 void launch_col_iter(cudaStream_t st, const SideStore &side, const double *yt, const ColVecs &v,
                      Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem,
                      int phase) {
+  const int threads = side.lay.cta_warps * kWarp;
   auto go = [&](auto kern) {
-    kern<<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, yt, v, ctl, part, ic,
-                                            phase);
+    kern<<<grid, threads, smem, st>>>(side.lay, side.v64, side.wa, yt, v, ctl, part, ic, phase);
   };
   const bool grp = side.lay.tile_mult > 1;
   if (ic.rho2) grp ? go(k_col_iter<1, true>) : go(k_col_iter<1, false>);
@@ -177,26 +178,26 @@ void allow_large_smem(int bytes) {
 }
 
 // Resident CTAs per SM of the FP64 iteration kernels of one side (all instantiations).
-static int fp64_blocks_per_sm(const void *const *k, int nk, int smem) {
+static int fp64_blocks_per_sm(const void *const *k, int nk, int smem, int threads) {
   int mn = 1 << 30;
   for (int i = 0; i < nk; ++i) {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k[i], kBlockThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k[i], threads, smem);
     mn = b < mn ? b : mn;
   }
   return mn;
 }
 
-int row_iter_blocks_per_sm(int smem) {
+int row_iter_blocks_per_sm(int smem, int threads) {
   const void *k[] = {(const void *)k_row_iter<0, false>, (const void *)k_row_iter<1, false>,
                      (const void *)k_row_iter<0, true>, (const void *)k_row_iter<1, true>};
-  return fp64_blocks_per_sm(k, 4, smem);
+  return fp64_blocks_per_sm(k, 4, smem, threads);
 }
 
-int col_iter_blocks_per_sm(int smem) {
+int col_iter_blocks_per_sm(int smem, int threads) {
   const void *k[] = {(const void *)k_col_iter<0, false>, (const void *)k_col_iter<1, false>,
                      (const void *)k_col_iter<0, true>, (const void *)k_col_iter<1, true>};
-  return fp64_blocks_per_sm(k, 4, smem);
+  return fp64_blocks_per_sm(k, 4, smem, threads);
 }
 
 }  // namespace rh

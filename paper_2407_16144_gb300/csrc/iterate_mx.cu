@@ -33,23 +33,27 @@ namespace rh {
 
 namespace {
 
-// The restart test's norms (||dy||^2, dy^T K dx, ||y~ - y0||^2 and ||dx||^2, ||x~ - x0||^2) are
-// accumulated in FP64 from the start: each FP32 offset is widened and the product of two widened
-// FP32 values is exact in FP64, so the only rounding is that of the FP64 sums.
-__device__ __forceinline__ double wsq(float a) { return (double)a * (double)a; }
-__device__ __forceinline__ double wmul(float a, float b) { return (double)a * (double)b; }
+// The restart test's norms (||dy||^2, dy^T K dx, ||y~ - y0||^2 and ||dx||^2, ||x~ - x0||^2) of
+// the ordinary kernels are double-float sums (common.cuh) of exact products of the FP32 offsets:
+// FP64-grade sums that run on the FP32 pipe.  The restart kernels (MODE 1) sum in FP64.
+template <int MODE>
+constexpr int row_df_slots() { return MODE == 0 ? 3 : 0; }
+template <int MODE>
+constexpr int col_df_slots() { return MODE == 0 ? 2 : 0; }
+__device__ __forceinline__ void df_acc(DF &d, float a, float b) { d = df_add(d, df_prod(a, b)); }
 
-// Register budgets as resident CTAs per SM: the ordinary kernels (MODE 0) of the plain and
-// grouped walks 8 (64 registers), the wide walk 6 (85), the restart kernels (MODE 1) 4 (128).
-__host__ __device__ constexpr int mx_min_blocks(int mode, int walk) {
-  return mode == 1 ? 4 : (walk == kWalkWide ? 6 : 8);
+// Register budgets: the ordinary kernels (MODE 0) of the plain and grouped walks 64 (32 resident
+// warps per SM), the wide walk 80, the restart kernels (MODE 1) 128.  The CTA width is chosen
+// at launch (up to kMaxBlockThreads).
+__host__ __device__ constexpr int mx_max_regs(int mode, int walk) {
+  return mode == 1 ? 128 : (walk == kWalkWide ? 80 : 64);
 }
 
 // MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
 // MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
 // launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
 template <int RHO2, int MODE, int WALK>
-__global__ void __launch_bounds__(kBlockThreads, mx_min_blocks(MODE, WALK))
+__global__ void __maxnreg__(mx_max_regs(MODE, WALK))
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
               const double *__restrict__ dxt64, const double *__restrict__ x0, Ctl *ctl,
@@ -69,8 +73,9 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   // FP32-only kernels are launched with half the shared memory)
   double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
   float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
-  RowAcc a;
-  RowAccL al;     // long-row sums (see walk_tiles); long-row maxima go to a
+  constexpr int ND = row_df_slots<MODE>();
+  Acc<7, 6, ND> a;
+  Acc<7, 0, ND> al;     // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
   const unsigned smask = row_smask(check, rp, move);
@@ -161,9 +166,9 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       v.dyt[i] = nd;
       v.kdxt[i] = kd;
       const float ddy = dy - nd;
-      A.s[0] += wsq(ddy);
-      A.s[1] += wmul(ddy, kdx - kd);
-      A.s[2] += wsq(nd);
+      df_acc(A.d[0], ddy, ddy);
+      df_acc(A.d[1], ddy, kdx - kd);
+      df_acc(A.d[2], nd, nd);
       if (check) {
         const double qi = v.q[i];
         double r = (qi - v.kx0[i] - (double)kd) * v.dinv[i];
@@ -193,14 +198,14 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   }
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
     double r[13];
-    grid_finish<7, 6>(part, r, smask, mmask, wb.group_part, lay.n_long_tiles);
+    grid_finish<7, 6, true, ND>(part, r, smask, mmask, wb.group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
   }
 }
 
 // MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
 template <int RHO2, int MODE, int WALK>
-__global__ void __launch_bounds__(kBlockThreads, mx_min_blocks(MODE, WALK))
+__global__ void __maxnreg__(mx_max_regs(MODE, WALK))
 k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
               const double *__restrict__ dyt64, const double *__restrict__ y0, Ctl *ctl,
@@ -219,8 +224,9 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   // FP32-only kernels are launched with half the shared memory)
   double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
   float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
-  ColAcc a;
-  ColAccL al;     // long-row sums (see walk_tiles); long-row maxima go to a
+  constexpr int ND = col_df_slots<MODE>();
+  Acc<11, 8, ND> a;
+  Acc<11, 0, ND> al;    // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
   Tel tl;         // active-set telemetry (ordinary check iterations)
@@ -301,8 +307,8 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
       v.dxt[j] = nt;
       const float ddx = dxn - nt;
-      A.s[0] += wsq(ddx);
-      A.s[1] += wsq(nt);
+      A.s[0] += (double)ddx * (double)ddx;
+      A.s[1] += (double)nt * (double)nt;
     };
     auto epi = [&](int j, double ktd, bool lg) {
       if (lg) body(j, ktd, al);
@@ -332,8 +338,8 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
       v.dxt[j] = nt;
       const float ddx = dxn - nt;
-      A.s[0] += wsq(ddx);
-      A.s[1] += wsq(nt);
+      df_acc(A.d[0], ddx, ddx);
+      df_acc(A.d[1], nt, nt);
     };
     auto epi = [&](int j, float ktdyt, bool lg) {
       if (lg) body(j, ktdyt, al);
@@ -356,7 +362,8 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   }
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[19];
-    grid_finish<11, 8>(part, r, smask, mmask, (restart ? wa : wb).group_part, lay.n_long_tiles);
+    grid_finish<11, 8, true, ND>(part, r, smask, mmask, (restart ? wa : wb).group_part,
+                                 lay.n_long_tiles);
     if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, rp, move, phase, MODE == 0);
   }
 }
@@ -387,9 +394,10 @@ __global__ void k_zero_f32(int n, float *x) {
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int smem) {
+  const int threads = side.lay.cta_warps * kWarp;
   auto go = [&](auto kern, int sm) {
-    kern<<<grid, kBlockThreads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dxt,
-                                          dxt64, x0, ctl, part, ic);
+    kern<<<grid, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dxt,
+                                    dxt64, x0, ctl, part, ic);
   };
   const int w = side.lay.walk;
   if (ic.rho2) {
@@ -408,9 +416,10 @@ void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx 
 void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx &v,
                         const float *dyt, const double *dyt64, const double *y0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int smem, int phase) {
+  const int threads = side.lay.cta_warps * kWarp;
   auto go = [&](auto kern, int sm) {
-    kern<<<grid, kBlockThreads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dyt,
-                                          dyt64, y0, ctl, part, ic, phase);
+    kern<<<grid, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dyt,
+                                    dyt64, y0, ctl, part, ic, phase);
   };
   const bool grp = side.lay.walk == kWalkGrouped;
   if (ic.rho2) {
@@ -446,7 +455,7 @@ void allow_large_smem_mx(int bytes) {
   for (const void *f : k) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-int iter_mx_blocks_per_sm(int smem, bool row, int walk) {
+int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads) {
   // the ordinary kernels of one side in one walk instantiation (both reflection settings)
   const void *k[2];
   if (row) {
@@ -465,7 +474,7 @@ int iter_mx_blocks_per_sm(int smem, bool row, int walk) {
   int mn = 1 << 30;
   for (const void *f : k) {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kBlockThreads, smem / 2);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, smem / 2);
     mn = b < mn ? b : mn;
   }
   return mn;

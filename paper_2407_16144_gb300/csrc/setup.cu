@@ -273,11 +273,11 @@ cudaError_t build_transpose(cudaStream_t st, int m, int n, int nnz, const int *r
   void *tmp = nullptr;
   size_t tmp_bytes = 0, scan_bytes = 0;
   const size_t nz = (size_t)std::max(nnz, 1);
-  if ((err = cudaMalloc(&rows_of, nz * sizeof(int)))) goto done;
-  if ((err = cudaMalloc(&iota, nz * sizeof(int)))) goto done;
-  if ((err = cudaMalloc(&keys_out, nz * sizeof(int)))) goto done;
-  if ((err = cudaMalloc(&perm, nz * sizeof(int)))) goto done;
-  if ((err = cudaMalloc(&cnt, (size_t)(n + 1) * sizeof(int)))) goto done;
+  if ((err = buf_alloc((void **)&rows_of, nz * sizeof(int)))) goto done;
+  if ((err = buf_alloc((void **)&iota, nz * sizeof(int)))) goto done;
+  if ((err = buf_alloc((void **)&keys_out, nz * sizeof(int)))) goto done;
+  if ((err = buf_alloc((void **)&perm, nz * sizeof(int)))) goto done;
+  if ((err = buf_alloc((void **)&cnt, (size_t)(n + 1) * sizeof(int)))) goto done;
   {
     int end_bit = 1;
     while ((1LL << end_bit) < (long long)n) ++end_bit;
@@ -285,7 +285,7 @@ cudaError_t build_transpose(cudaStream_t st, int m, int n, int nnz, const int *r
                                     st);
     cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, cnt, cp, n + 1, st);
     tmp_bytes = std::max(tmp_bytes, scan_bytes);
-    if ((err = cudaMalloc(&tmp, std::max<size_t>(tmp_bytes, 16)))) goto done;
+    if ((err = buf_alloc(&tmp, std::max<size_t>(tmp_bytes, 16)))) goto done;
     k_expand_rows<<<nblocks(m, 256), 256, 0, st>>>(m, rp, rows_of);
     k_iota<<<nblocks(nnz, 256), 256, 0, st>>>(nnz, iota);
     if (nnz > 0)
@@ -300,12 +300,13 @@ cudaError_t build_transpose(cudaStream_t st, int m, int n, int nnz, const int *r
     if (err == cudaSuccess) err = cudaGetLastError();
   }
 done:
-  cudaFree(rows_of);
-  cudaFree(iota);
-  cudaFree(keys_out);
-  cudaFree(perm);
-  cudaFree(cnt);
-  cudaFree(tmp);
+  cudaStreamSynchronize(st);     // nothing in flight uses the scratch when it goes back
+  buf_release(rows_of);
+  buf_release(iota);
+  buf_release(keys_out);
+  buf_release(perm);
+  buf_release(cnt);
+  buf_release(tmp);
   return err;
 }
 
@@ -365,11 +366,14 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
 
 namespace {
 // Cached buffers are keyed by (device, size): a buffer is only ever reused on the device it was
-// allocated on.
+// allocated on.  Buffers from a caller's allocator carry it (hook.free set) and are never cached.
 struct BufInfo {
   int dev;
   size_t bytes;
+  DevAllocator hook;
 };
+
+thread_local const DevAllocator *tl_alloc = nullptr;   // set by AllocScope
 std::mutex g_buf_mu;
 std::unordered_map<void *, BufInfo> g_buf_info;              // every buffer from buf_alloc
 std::map<std::pair<int, size_t>, std::vector<void *>> g_buf_free;   // cached, by (device, size)
@@ -394,11 +398,29 @@ void buf_drop_cache_locked() {
 }
 }  // namespace
 
+AllocScope::AllocScope(const DevAllocator &a) : prev_(tl_alloc), mine_(a) {
+  tl_alloc = (mine_.alloc && mine_.free) ? &mine_ : nullptr;
+}
+AllocScope::~AllocScope() { tl_alloc = prev_; }
+
 cudaError_t buf_alloc(void **p, size_t bytes) {
   bytes = std::max<size_t>(bytes, 1);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (tl_alloc) {
+    // 256-byte alignment covers every vector load of the kernels
+    void *q = tl_alloc->alloc(bytes, tl_alloc->stream, tl_alloc->ctx);
+    if (!q) return cudaErrorMemoryAllocation;
+    if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+      tl_alloc->free(q, tl_alloc->stream, tl_alloc->ctx);
+      return cudaErrorInvalidValue;
+    }
+    *p = q;
+    std::lock_guard<std::mutex> lk(g_buf_mu);
+    g_buf_info[q] = BufInfo{dev, bytes, *tl_alloc};
+    return cudaSuccess;
+  }
   {
     std::lock_guard<std::mutex> lk(g_buf_mu);
     auto it = g_buf_free.find({dev, bytes});
@@ -420,7 +442,7 @@ cudaError_t buf_alloc(void **p, size_t bytes) {
   }
   if (e == cudaSuccess) {
     std::lock_guard<std::mutex> lk(g_buf_mu);
-    g_buf_info[*p] = BufInfo{dev, bytes};
+    g_buf_info[*p] = BufInfo{dev, bytes, DevAllocator()};
   }
   return e;
 }
@@ -428,10 +450,16 @@ cudaError_t buf_alloc(void **p, size_t bytes) {
 void buf_release(void *p) {
   if (!p) return;
   {
-    std::lock_guard<std::mutex> lk(g_buf_mu);
+    std::unique_lock<std::mutex> lk(g_buf_mu);
     auto it = g_buf_info.find(p);
     if (it != g_buf_info.end()) {
       const BufInfo bi = it->second;
+      if (bi.hook.free) {
+        g_buf_info.erase(it);
+        lk.unlock();
+        bi.hook.free(p, bi.hook.stream, bi.hook.ctx);
+        return;
+      }
       if (g_buf_free_bytes + bi.bytes <= kBufferCacheBytes) {
         g_buf_free[{bi.dev, bi.bytes}].push_back(p);
         g_buf_free_bytes += bi.bytes;
@@ -664,7 +692,8 @@ void free_side(SideStore *s) {
 }
 
 int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm) {
-  long long need = ((long long)lay.total_items() + kBlockWarps - 1) / kBlockWarps;
+  const int w = lay.cta_warps > 0 ? lay.cta_warps : kBlockWarps;
+  long long need = ((long long)lay.total_items() + w - 1) / w;
   long long cap = (long long)sm_count * std::max(blocks_per_sm, 1);
   long long g = std::min(need, cap);
   return (int)std::max<long long>(g, 1);

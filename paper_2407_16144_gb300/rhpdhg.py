@@ -40,6 +40,10 @@ class rhpdhg_problem(C.Structure):
                 ("obj_offset", C.c_double)]
 
 
+DEV_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+DEV_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 class rhpdhg_params(C.Structure):
     _fields_ = [("algorithm", C.c_int32), ("precision", C.c_int32),
                 ("eps_rel_kkt", C.c_double), ("eps_infeas", C.c_double),
@@ -52,7 +56,9 @@ class rhpdhg_params(C.Structure):
                 ("restart_beta", C.c_double), ("check_every", C.c_int32),
                 ("use_graphs", C.c_int32), ("trace", C.c_int32), ("profile", C.c_int32),
                 ("trace_capacity", C.c_int64), ("x0", C.c_void_p), ("y0", C.c_void_p),
-                ("adaptive_step", C.c_int32), ("reserved", C.c_int32)]
+                ("adaptive_step", C.c_int32), ("cta_warps", C.c_int32),
+                ("reserved", C.c_int32), ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
+                ("alloc_ctx", C.c_void_p)]
 
 
 class rhpdhg_result(C.Structure):
@@ -204,7 +210,7 @@ def rhpdhg_get_trace(h, capacity: int):
 
 LAYOUT_FIELDS = ("grid_row", "grid_col", "tile_mult_row", "tile_mult_col", "long_rows_row",
                  "long_rows_col", "chunks_row", "chunks_col", "seg_row", "seg_col", "walk_row",
-                 "walk_col")
+                 "walk_col", "cta_warps_row", "cta_warps_col")
 
 
 def rhpdhg_get_layout(h):
@@ -561,11 +567,50 @@ def _check(rc, h=None, what=""):
     return rc
 
 
+class TorchAllocator:
+    """Device allocator callbacks for rhpdhg_params.dev_alloc / dev_free that take a handle's
+    device memory from PyTorch's caching allocator (torch.cuda.caching_allocator_alloc on the
+    handle's stream, caching_allocator_delete to give it back), so the solver's buffers count in
+    torch's memory statistics and are reused by torch after the handle is freed.  Keep the
+    object alive as long as any handle created with it."""
+
+    def __init__(self, device=None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.live = {}
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                ptr = self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                               int(stream or 0))
+            except Exception:
+                return None
+            self.live[ptr] = int(nbytes)
+            return ptr
+
+        def _free(ptr, stream, ctx):
+            if ptr in self.live:
+                del self.live[ptr]
+                self._torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = DEV_ALLOC_FN(_alloc)
+        self.free_fn = DEV_FREE_FN(_free)
+
+    def apply(self, p: "rhpdhg_params"):
+        p.dev_alloc = self.alloc_fn
+        p.dev_free = self.free_fn
+        p.alloc_ctx = None
+
+
 def default_params(**kw) -> rhpdhg_params:
     p = rhpdhg_params()
     _check(rhpdhg_params_default(p))
     for k, v in kw.items():
         if k in ("x0", "y0"):
+            continue
+        if k == "allocator":
+            v.apply(p)
             continue
         if not hasattr(p, k):
             raise KeyError(k)

@@ -180,3 +180,22 @@ def test_kkt_eval_rejects_bad_arguments_with_a_message(rh, entry):
     prob.nnz = -1
     rc, _ = fn(prob, arr.ctypes.data, arr.ctypes.data)
     assert rc == rh.ERR_INVALID_ARG and "negative" in rh.rhpdhg_last_error(None)
+
+
+def test_allocator_hook_given_whole_or_not_at_all(rh):
+    """rhpdhg_params.dev_alloc and dev_free come as a pair: one without the other is rejected on
+    the host, before any device work."""
+    arr = np.zeros(8)
+    rp = np.zeros(2, dtype=np.int64)
+    prob = rh.rhpdhg_problem()
+    prob.m_eq, prob.m_ineq, prob.n, prob.nnz = 1, 0, 3, 0
+    prob.row_ptr, prob.c, prob.l, prob.u, prob.rhs = (rp.ctypes.data, arr.ctypes.data,
+                                                      arr.ctypes.data, arr.ctypes.data,
+                                                      arr.ctypes.data)
+    p = rh.rhpdhg_params()
+    rh.rhpdhg_params_default(p)
+    assert not p.dev_alloc and not p.dev_free and not p.alloc_ctx      # defaults: no hook
+    p.dev_alloc = rh.DEV_ALLOC_FN(lambda n, s, c: None)
+    rc, h = rh.rhpdhg_create(prob, p)
+    assert rc == rh.ERR_INVALID_ARG and not h.value
+    assert "dev_alloc and dev_free" in rh.rhpdhg_last_error(None)

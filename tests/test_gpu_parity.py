@@ -650,3 +650,29 @@ def test_kkt_eval_reports_out_of_range_columns(rh):
     # the library stays usable: a valid evaluation right after succeeds
     rc, out = rh.rhpdhg_kkt_eval(rh.device_problem(_device_lp(lp)), x.data_ptr(), y.data_ptr())
     assert rc == rh.OK
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_caller_allocator_supplies_device_memory(rh, precision):
+    """With a caller allocator (here PyTorch's caching allocator through rhpdhg_params.dev_alloc
+    / dev_free) every device buffer of the handle comes from it and goes back to it at free, and
+    the solve is bit-identical to one on the library's own buffers."""
+    import torch
+    lp = CASES["c2_small"]()
+    with rh.Solver(lp, precision=precision, eps_rel_kkt=1e-7) as s:
+        ref = s.run()
+    alloc = rh.TorchAllocator()
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    s = rh.Solver(lp, stream=stream, precision=precision, eps_rel_kkt=1e-7, allocator=alloc)
+    held, held_bytes = len(alloc.live), sum(alloc.live.values())
+    during = torch.cuda.memory_allocated()
+    r = s.run()
+    s.close()
+    torch.cuda.synchronize()
+    assert held >= 30, held                       # the handle's vectors, layouts and scratch
+    assert during - before >= held_bytes
+    assert not alloc.live and torch.cuda.memory_allocated() == before
+    assert (r.status, r.iters) == (ref.status, ref.iters)
+    assert np.array_equal(r.x, ref.x) and np.array_equal(r.y, ref.y)
