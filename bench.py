@@ -54,10 +54,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 120M-nonzero multicommodity-flow section")
-    ap.add_argument("--serve-requests", type=int, default=40,
+    ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the 50/s Poisson stream replayed through the serving loop "
                          "(0 = skip)")
-    ap.add_argument("--serve-max-iters", type=int, default=10_000)
+    ap.add_argument("--serve-max-iters", type=int, default=1_000_000)
     return ap.parse_args()
 
 
@@ -177,6 +177,10 @@ def replica_throughput(world, units_per_rank, max_ms):
     return world * units_per_rank / (max_ms / 1000.0)
 
 
+TUNE_KEYS = ("tuned", "tune_ns_rule", "tune_ns_best", "cta_warps_row", "cta_warps_col",
+             "walk_row", "grid_row", "grid_col")
+
+
 def fp64_flops(lp):
     """Algorithmic FP64 flops of one launch of the FP64 row kernel (K x~ and the dual step) and
     of the column kernel (K^T y~ and the primal step) of r2HPDHG: one FMA (2 flops) per nonzero,
@@ -214,9 +218,11 @@ def sgm10(times):
 
 
 def run_serving(args, rhpdhg, lpgen):
-    """Replays the first requests of the serving stream (Poisson arrivals at 50/s, m log-uniform
-    in [100, 200k], n = 2.5 m, C1 structure, tolerance 1e-4 or 1e-6 each) through the serving loop
-    and, for comparison, one at a time through the plain FP64 single-LP path."""
+    """Replays a prefix of the serving stream (Poisson arrivals at 50/s, m log-uniform in
+    [100, 200k], n = 2.5 m, C1 structure, tolerance 1e-4 or 1e-6 each) through the serving loop in
+    mixed precision (FP32 iterates and matrix values, FP64 restarts and checks; LPs with at most
+    small_nnz nonzeros become batched slots, larger ones get their own handle and stream), and,
+    for comparison, through the plain FP64 single-LP path one request at a time."""
     import threading
     import numpy as np
     nreq = args.serve_requests
@@ -224,6 +230,7 @@ def run_serving(args, rhpdhg, lpgen):
     lps = [lpgen.make_standard_planted(seed=r["seed"], m=r["m"], n=r["n"]) for r in reqs]
     small_nnz = 20_000
     cap = args.serve_max_iters
+    limit_s = 120.0
     results = {}
     with rhpdhg.Server(150 << 30, small_nnz=small_nnz, max_slots=256, iters_per_step=64) as srv:
         tick = {}
@@ -234,8 +241,8 @@ def run_serving(args, rhpdhg, lpgen):
                 now = time.perf_counter() - start
                 if r["arrival_s"] > now:
                     time.sleep(r["arrival_s"] - now)
-                prec = 0 if lp.nnz <= small_nnz else 1
-                tick[i] = srv.submit(lp, eps_rel_kkt=r["tol"], precision=prec, max_iters=cap)
+                tick[i] = srv.submit(lp, eps_rel_kkt=r["tol"], precision=1, max_iters=cap,
+                                     time_limit_s=limit_s)
 
         th = threading.Thread(target=producer)
         th.start()
@@ -251,11 +258,13 @@ def run_serving(args, rhpdhg, lpgen):
         st = srv.stats()
     lat = np.array([results[i][1] for i in range(nreq)])
     solved = sum(results[i][0].status == rhpdhg.STATUS_OPTIMAL for i in range(nreq))
-    # the same stream through the plain FP64 single-LP path, one LP at a time
+    # the plain FP64 single-LP path: each request alone (create, solve, poll, free), its service
+    # time measured; latencies from a FIFO replay of those service times against the same arrivals
     svc, solved_b = [], 0
     for r, lp in zip(reqs, lps):
         t0 = time.perf_counter()
-        with rhpdhg.Solver(lp, eps_rel_kkt=r["tol"], precision=0, max_iters=cap) as s:
+        with rhpdhg.Solver(lp, eps_rel_kkt=r["tol"], precision=0, max_iters=cap,
+                           time_limit_s=limit_s) as s:
             rr = s.run()
         svc.append(time.perf_counter() - t0)
         solved_b += rr.status == rhpdhg.STATUS_OPTIMAL
@@ -267,20 +276,23 @@ def run_serving(args, rhpdhg, lpgen):
     lat_b = np.array(lat_b)
     return {
         "workload": f"first {nreq} requests of the stream: Poisson arrivals at 50/s, m log-uniform "
-                    "in [100, 200k], n = 2.5 m, 5 nnz per column, tol 1e-4 or 1e-6 (seed 4), "
-                    f"at most {cap} iterations each",
-        "lps_per_s": nreq / makespan, "makespan_s": makespan,
+                    "in [100, 200k], n = 2.5 m, 5 nnz per column, planted optimum, tol 1e-4 or "
+                    f"1e-6 (seed 4); at most {cap} iterations and {limit_s:.0f} s each",
+        "solved_lps_per_s": solved / makespan, "makespan_s": makespan,
         "p50_latency_s": float(np.percentile(lat, 50)),
         "p99_latency_s": float(np.percentile(lat, 99)),
         "sgm10_latency_s": sgm10(list(lat)), "solved": int(solved), "requests": nreq,
-        "policy": f"nnz <= {small_nnz}: batched slots (FP64, one CTA each); larger: own handle, "
-                  "FP32 iterates / FP64 restarts",
+        "policy": f"all requests FP32 iterates / FP64 restarts; nnz <= {small_nnz}: batched slots "
+                  "(one CTA per LP, one launch for all slots); larger: own handle and stream",
         "admitted_batched": st["admitted_batched"], "admitted_single": st["admitted_single"],
         "peak_bytes_in_use": st["peak_bytes_in_use"],
-        "plain_fp64_single_lp": {"lps_per_s": nreq / fin, "makespan_s": fin,
-                                 "p50_latency_s": float(np.percentile(lat_b, 50)),
-                                 "p99_latency_s": float(np.percentile(lat_b, 99)),
-                                 "sgm10_latency_s": sgm10(list(lat_b)), "solved": int(solved_b)},
+        "plain_fp64_single_lp": {
+            "how": "each request solved alone through the FP64 single-LP path (service time "
+                   "measured); arrivals replayed through a simulated FIFO queue of those times",
+            "solved_lps_per_s": solved_b / fin, "makespan_s": fin,
+            "p50_latency_s": float(np.percentile(lat_b, 50)),
+            "p99_latency_s": float(np.percentile(lat_b, 99)),
+            "sgm10_latency_s": sgm10(list(lat_b)), "solved": int(solved_b)},
     }
 
 
@@ -391,13 +403,17 @@ def run_ours(args):
     xh = torch.empty(lp.n, dtype=torch.float64).pin_memory().numpy()
     yh = torch.empty(lp.m, dtype=torch.float64).pin_memory().numpy()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
-    params = dict(algorithm=args.algorithm, precision=args.precision, eps_rel_kkt=args.tol)
+    params = dict(algorithm=args.algorithm, precision=args.precision, eps_rel_kkt=args.tol,
+                  autotune=1)
+
+    layouts = []
 
     def step_device():
         s = rhpdhg.Solver(dev, device=True, stream=sh, **params)
         s.solve(1)
         r = s.poll(x=xo, y=yo, out_memory=rhpdhg.MEM_DEVICE)
         nl = s.launch_count()
+        layouts.append(s.layout())
         s.close()
         return r, nl
 
@@ -524,6 +540,10 @@ def run_ours(args):
                           "column_kernel": {"achieved": fp64_col,
                                             "frac": fp64_col / fp64_tflops}},
         "gpu_launches": int(launches),
+        "autotune": {"first_create": {k: layouts[0][k] for k in TUNE_KEYS},
+                     "timed_steps": {k: layouts[-1][k] for k in TUNE_KEYS},
+                     "note": "the first warm-up create times the candidate geometries; later "
+                             "creates of the same LP structure take the cached choice"},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": problem_bytes(lp),
                 "d2h_bytes_per_step": 8 * (lp.n + lp.m)},

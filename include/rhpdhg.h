@@ -152,13 +152,28 @@ typedef struct {
                                    precision 0 only; not in batched slots.       default 0    */
   int32_t cta_warps;            /* warps per CTA of the iteration kernels: 4, 8 or 16; 0 = the
                                    library's choice.                              default 0    */
-  int32_t reserved;
+  int32_t df_sums;              /* precision 1: sums of the restart test's norms (Section 3,
+                                   eq. adaptive-restart).  0 = each warp adds its rows' FP32
+                                   products in FP32 (fused multiply-adds, a fixed shuffle tree;
+                                   relative error below 1e-6), FP64 above the warp; 1 = double-
+                                   float (two FP32 numbers, error-free transformations) from the
+                                   row up: FP64-grade sums, slower on GPUs with a narrow FP64
+                                   pipe.                                          default 0    */
   /* Caller's allocator for the handle's device memory (both functions or neither; NULL = the
    * library's own cache of device buffers), with its context pointer.  Used by rhpdhg_create
    * only; the batched solver and the server ignore it.                          default NULL */
   rhpdhg_dev_alloc_fn dev_alloc;
   rhpdhg_dev_free_fn  dev_free;
   void *alloc_ctx;
+  int32_t autotune;             /* 1 = rhpdhg_create times candidate launch geometries of the
+                                   iteration kernels (warps per CTA of each side; plain or wide
+                                   staging walk of the mixed row kernel) on the handle's stream
+                                   and keeps the fastest per side; the choice is cached for the
+                                   process by a signature of the LP's structure (sizes, precision,
+                                   algorithm, row-length histograms), so handles of the same shape
+                                   reuse it without timing.  Ignored when cta_warps is set.
+                                                                                  default 0    */
+  int32_t reserved;
 } rhpdhg_params;
 
 /* Result of a finished solve, filled by rhpdhg_poll. */
@@ -257,10 +272,13 @@ int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t cap
  * K^ and on K^T; the staging stride (entries per warp) of K^ and of K^T; the walk of the
  * ordinary mixed-precision kernels on K^ and on K^T (0 = one tile per item, 1 = one tile per
  * item with twice the loads in flight per staging round, 2 = groups of tiles per item; 0 for
- * FP64 handles); warps per CTA of the row kernels and of the column kernels.
+ * FP64 handles); warps per CTA of the row kernels and of the column kernels; the autotuner's
+ * outcome (0 = the fixed rule, 1 = timed at create, 2 = taken from the cache), and the time of
+ * one iteration (row plus column stage, median, nanoseconds) with the rule's geometry and with
+ * the chosen one (0 when not tuned).
  * capacity: entries available at out.  Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG for a NULL
  * handle or out, or capacity < RHPDHG_LAYOUT_FIELDS. */
-#define RHPDHG_LAYOUT_FIELDS 14
+#define RHPDHG_LAYOUT_FIELDS 17
 int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity);
 
 /* Handles take their device buffers from a process-wide cache of buffers freed by earlier
@@ -344,8 +362,9 @@ int rhpdhg_probe_l2_read_bandwidth(int64_t bytes, void *cuda_stream, double *gbs
  * Many small LPs advance together in one persistent launch, one CTA per LP (the CTA also runs
  * the LP's set-up: scaling, power iteration, primal weight).  Each LP's computation stays inside
  * its CTA, so its result does not depend on which other LPs share the launch.  The method and
- * its statuses are those of rhpdhg_solve (FP64).  Slots are described by a table in device
- * memory, so one captured graph is replayed while LPs are added and removed. */
+ * its statuses are those of rhpdhg_solve, in FP64 or (per slot) mixed precision.  Slots are
+ * described by a table in device memory, so one captured graph is replayed while LPs are added
+ * and removed. */
 typedef struct rhpdhg_batch rhpdhg_batch;
 
 /* Creates a batch with max_slots slots and a device arena of arena_bytes for the LPs' data.
@@ -354,9 +373,13 @@ int rhpdhg_batch_create(int32_t max_slots, int64_t arena_bytes, void *cuda_strea
                         rhpdhg_batch **out);
 
 /* Copies an LP (host memory, validated and transposed on the host) into a free slot; its set-up
- * runs in the next step.  params: as for rhpdhg_create (precision must be 0; NULL = defaults).
+ * runs in the next step.  params: as for rhpdhg_create (NULL = defaults; the constant step only).
+ * precision 1 runs the slot's ordinary iterations with FP32 matrix values and FP32 offsets from
+ * FP64 anchors, and its restarts, restart points and checks in FP64, like rhpdhg_solve (the
+ * restart-norm sums are FP32 within each warp and FP64 across warps; a near-certificate at a
+ * restart point moves the slot to FP64 for the rest of its solve).
  * Returns RHPDHG_BUSY when no slot is free and RHPDHG_ERR_OOM when the arena lacks
- * rhpdhg_batch_bytes_needed(lp) contiguous bytes. */
+ * rhpdhg_batch_bytes_needed(lp, precision) contiguous bytes. */
 int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_params *params,
                      int32_t *slot);
 
@@ -373,9 +396,10 @@ int rhpdhg_batch_remove(rhpdhg_batch *b, int32_t slot);
 /* Status of a slot after the last step (RHPDHG_STATUS_*), or -1 for an empty slot. */
 int rhpdhg_batch_slot_status(const rhpdhg_batch *b, int32_t slot);
 
-/* Free arena bytes (sum of free regions), and the bytes one LP needs. */
+/* Free arena bytes (sum of free regions), and the bytes one LP needs in a slot of the given
+ * precision (0 or 1; -1 for a NULL lp or another precision). */
 int64_t rhpdhg_batch_free_bytes(const rhpdhg_batch *b);
-int64_t rhpdhg_batch_bytes_needed(const rhpdhg_problem *lp);
+int64_t rhpdhg_batch_bytes_needed(const rhpdhg_problem *lp, int32_t precision);
 
 /* Kernel launches issued by the batch so far (steps and result extractions). */
 int64_t rhpdhg_batch_launch_count(const rhpdhg_batch *b);
@@ -384,9 +408,10 @@ void rhpdhg_batch_free(rhpdhg_batch *b);
 
 /* ---- serving: continuous batching under a device-memory budget ---------------------------
  * A worker thread admits submitted LPs first-come first-served while the budget allows (a
- * later request may pass one that does not fit yet).  LPs with at most small_nnz nonzeros and
- * precision 0 become slots of an internal batched solver (its arena, budget_bytes / 4 at most,
- * counts against the budget); the others get their own single-LP handle, solved on its own
+ * later request may pass one that does not fit yet).  LPs with at most small_nnz nonzeros
+ * (and the constant step) become slots of an internal batched solver, in the precision the
+ * request asks for (its arena, budget_bytes / 4 at most, counts against the budget); the others
+ * get their own single-LP handle, solved on its own
  * stream concurrently with the batch.  Memory is released as each request finishes, and waiting
  * requests are admitted in the next turn.  Results are kept until polled. */
 typedef struct rhpdhg_server rhpdhg_server;

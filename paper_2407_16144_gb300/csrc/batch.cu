@@ -21,6 +21,7 @@
 #include "../../include/rhpdhg.h"
 #include "internal.h"
 #include "iter_common.cuh"
+#include "iter_mx_common.cuh"
 
 namespace rh {
 
@@ -42,11 +43,18 @@ struct BatchDesc {
   RowVecs rv_;             // y, y~, y0, Kx, Kx~, Kx0, certy, q (scaled in place), D, Dinv
   ColVecs cv_;             // x, x~, x0, K^T y, K^T y0, xout, certx, c, l, u (scaled), E, Einv
   Ctl *ctl;
-  IterConsts *ic;          // per-slot constants (eta, norms filled by set-up)
+  IterConsts *ic;          // per-slot constants (eta, norms filled by set-up); ic->mixed is the
+                           // slot's current mode (a mixed slot that escalates turns it to 0)
   double *setup_out;       // sigma_max, omega0 (for inspection)
+  // mixed precision (precision 1): FP32 copies of the scaled values and the FP32-offset state
+  int mixed;
+  float *rv32, *cv32;
+  RowVecsMx rvm;
+  ColVecsMx cvm;
 };
 
-__device__ __forceinline__ double group_sum(double v, int g) {
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int g) {
   for (int o = g >> 1; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, g);
   return v;
 }
@@ -56,10 +64,11 @@ __device__ __forceinline__ double group_max(double v, int g) {
 }
 
 // Block reduction of the NS sums and NM maxima selected by the masks into out (valid in thread
-// 0; other slots 0); deterministic.
+// 0; other slots 0); deterministic.  Sum slots set in prewarp already hold their warp's sum.
 template <int NS, int NM>
 __device__ void block_reduce(const Acc<NS, NM> &a, double *out, double *sh,
-                             unsigned smask = 0xFFFFu, unsigned mmask = 0xFFFFu) {
+                             unsigned smask = 0xFFFFu, unsigned mmask = 0xFFFFu,
+                             unsigned prewarp = 0u) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned all = (smask & ((1u << NS) - 1u)) | ((mmask & ((1u << NM) - 1u)) << NS);
   __syncthreads();
@@ -67,7 +76,8 @@ __device__ void block_reduce(const Acc<NS, NM> &a, double *out, double *sh,
   for (int i = 0; i < NS + NM; ++i) {
     if (!((all >> i) & 1u)) continue;
     double v = i < NS ? a.s[i] : a.mx[i - NS];
-    v = i < NS ? warp_sum(v) : warp_max(v);
+    if (i >= NS) v = warp_max(v);
+    else if (!((prewarp >> i) & 1u)) v = warp_sum(v);
     if (lane == 0) sh[warp * (NS + NM) + i] = v;
   }
   __syncthreads();
@@ -98,21 +108,22 @@ __device__ double block_sum1(double v, double *sh) {
 // For each row r of a CSR (rows, ptr, idx, val): dot = sum val * src[idx], then fn(r, dot).
 // A warp owns 32 consecutive rows; groups of g lanes compute 32/g rows per pass (g passes),
 // each result is handed to the lane that owns the row, and fn then runs for 32 rows at once,
-// one per lane, so the FP64 epilogue keeps every lane busy.  Trip counts are warp-uniform.
-template <typename Src, typename Fn>
+// one per lane, so the epilogue keeps every lane busy.  Trip counts are warp-uniform.  VT is
+// the value and sum type (FP64, or FP32 for the ordinary mixed-precision iterations).
+template <typename VT, typename Src, typename Fn>
 __device__ __forceinline__ void rows_apply(int nrows, const int *ptr, const int *idx,
-                                           const double *val, int g, const Src &src, Fn &fn) {
+                                           const VT *val, int g, const Src &src, Fn &fn) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rpp = 32 / g, gid = lane / g, gl = lane % g;
   for (int base = warp * 32; base < nrows; base += kBT) {
-    double mine = 0.0;
+    VT mine = VT(0);
     for (int pass = 0; pass < g; ++pass) {
       const int r = base + pass * rpp + gid;
-      double s = 0.0;
+      VT s = VT(0);
       if (r < nrows)
-        for (int p = ptr[r] + gl; p < ptr[r + 1]; p += g) s += val[p] * src(idx[p]);
+        for (int p = ptr[r] + gl; p < ptr[r + 1]; p += g) s += val[p] * VT(src(idx[p]));
       s = group_sum(s, g);
-      const double got = __shfl_sync(0xffffffffu, s, (lane % rpp) * g);
+      const VT got = __shfl_sync(0xffffffffu, s, (lane % rpp) * g);
       if (lane / rpp == pass) mine = got;
     }
     const int r = base + lane;
@@ -190,6 +201,13 @@ __device__ void batch_setup(const BatchDesc &d, double *sh) {
     const int g2 = d.gc, gid2 = threadIdx.x / g2, gl2 = threadIdx.x % g2, ng2 = kBT / g2;
     for (int r = gid2; r < n; r += ng2)
       for (int p = d.cp[r] + gl2; p < d.cp[r + 1]; p += g2) d.cv[p] = E[r] * d.cv[p] * D[d.ri[p]];
+    if (d.mixed) {
+      __syncthreads();
+      for (int p = threadIdx.x; p < d.nnz; p += kBT) {
+        d.rv32[p] = (float)d.rv[p];
+        d.cv32[p] = (float)d.cv[p];
+      }
+    }
   }
   for (int i = threadIdx.x; i < m; i += kBT) {
     q[i] = D[i] * q[i];
@@ -251,6 +269,24 @@ __device__ void batch_setup(const BatchDesc &d, double *sh) {
     auto f1 = [&](int r, double s) { rvv.kxt[r] = s; };
     auto g1 = [&](int j) { return cvv.xt[j]; };
     rows_apply(m, d.rp, d.ci, d.rv, d.gr, g1, f1);
+  }
+  if (d.mixed) {
+    // anchors z^{0,0} and zero FP32 offsets; the set-up column pass then runs in restart mode
+    const RowVecsMx &rm = d.rvm;
+    const ColVecsMx &cm = d.cvm;
+    for (int j = threadIdx.x; j < n; j += kBT) {
+      cm.x0[j] = cvv.xt[j];
+      cm.dxt[j] = 0.f;
+      cm.dx[j] = 0.f;
+      cm.ktdy[j] = 0.f;
+    }
+    for (int i = threadIdx.x; i < m; i += kBT) {
+      rm.y0[i] = 0.0;
+      rm.dyt[i] = 0.f;
+      rm.kdxt[i] = 0.f;
+      rm.dy[i] = 0.f;
+      rm.kdx[i] = 0.f;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -321,15 +357,157 @@ __device__ void batch_row_pass(const BatchDesc &d, const IterConsts &ic, double 
   __syncthreads();
 }
 
+// The FP32 restart-norm sums of a thread, summed over its warp in FP32 and placed in the FP64
+// slots of a (lane 0 holds the warp's sum; block_reduce adds the warps in FP64).
+template <int N, class A>
+__device__ __forceinline__ unsigned warp_sums_to(FprSums<N, 0> &f, A &a) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) a.s[i] = (double)warp_sum(f.v[i].hi);
+  return (1u << N) - 1u;
+}
+
+// ---- mixed precision in a slot: the bodies of the tiled mixed kernels (iter_mx_common.cuh) over
+// the slot's CSR copies, FP32 matrix values in ordinary iterations and FP64 at restarts and
+// restart points; the restart-norm sums are FP32 within each warp and FP64 across the warps.
+
 template <int RHO2>
-__device__ void batch_iterate(const BatchDesc &d, const IterConsts &ic, int iters, double *sh) {
+__device__ void batch_row_pass_mx(const BatchDesc &d, const IterConsts &ic, double *sh) {
+  Ctl *ctl = d.ctl;
+  const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
+  const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
+  const bool rp = (k == 0 && n_ep >= 1);
+  const int restart = ctl->restart_pending;
+  const bool move = restart && ctl->mv_ready;
+  const double sigma = ctl->sigma;
+  const float wf = (float)ctl->w, sigf = (float)sigma;
+  const RowVecsMx &v = d.rvm;
+  const int m_eq = ic.m_eq;
+  Acc<7, 6> a;
+  a.zero();
+  unsigned prewarp = 0u;
+  if (restart) {
+    // K x0' with the FP64 values (and the anchor movement's row parts), then the dual step of
+    // the restart point in FP64 from K dxt (dxt exact in dxt64)
+    const double *x0 = d.cvm.x0;
+    auto gA = [&](int j) { return x0[j]; };
+    auto fA = [&](int i, double dot) {
+      if (move) row_mx_move(i, dot, v, m_eq, a, a);
+      v.kx0[i] = dot;
+    };
+    rows_apply(d.m, d.rp, d.ci, d.rv, d.gr, gA, fA);
+    __syncthreads();
+    const double *dxt64 = d.cvm.dxt64;
+    auto gB = [&](int j) { return dxt64[j]; };
+    auto fB = [&](int i, double kd) {
+      row_mx_restart<RHO2>(i, kd, v, sigma, m_eq, check, rp, a, a);
+    };
+    rows_apply(d.m, d.rp, d.ci, d.rv, d.gr, gB, fB);
+  } else {
+    FprSums<3, 0> f;
+    const float *dxt = d.cvm.dxt;
+    auto g = [&](int j) { return dxt[j]; };
+    auto fn = [&](int i, float kd) { row_mx_ordinary<RHO2>(i, kd, v, wf, sigf, m_eq, check, a, f); };
+    rows_apply(d.m, d.rp, d.ci, d.rv32, d.gr, g, fn);
+    prewarp = warp_sums_to(f, a);
+  }
+  double r[13];
+  block_reduce(a, r, sh, row_smask(check, rp, move), row_mmask(rp, move), prewarp);
+  if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
+  __syncthreads();
+}
+
+template <int RHO2>
+__device__ void batch_col_pass_mx(const BatchDesc &d, const IterConsts &ic, int phase,
+                                  double *sh) {
+  Ctl *ctl = d.ctl;
+  const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
+  const int restart = ctl->restart_pending;
+  const bool rp = phase == 0 && (k == 0 && n_ep >= 1);
+  const bool move = phase == 0 && restart;
+  const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
+  const double tau = ctl->tau;
+  const float wf = (float)ctl->w, tauf = (float)tau;
+  const ColVecsMx &v = d.cvm;
+  Acc<11, 8> a;
+  a.zero();
+  Tel tl;
+  unsigned prewarp = 0u;
+  if (restart) {
+    // z^{n+1,0} = T(z^{n,k}): K^T y0' with the FP64 values from the gathered y0 + dyt
+    const double *y0 = d.rvm.y0;
+    const float *dyt = d.rvm.dyt;
+    auto g = [&](int i) { return y0[i] + (double)dyt[i]; };
+    auto fn = [&](int j, double kty) {
+      col_mx_restart<RHO2>(j, kty, v, tau, check, rp, move, a, a);
+    };
+    rows_apply(d.n, d.cp, d.ri, d.cv, d.gc, g, fn);
+  } else if (rp) {
+    const double *dyt64 = d.rvm.dyt64;
+    auto g = [&](int i) { return dyt64[i]; };
+    auto fn = [&](int j, double ktd) { col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, a, a); };
+    rows_apply(d.n, d.cp, d.ri, d.cv, d.gc, g, fn);
+  } else {
+    FprSums<2, 0> f;
+    const float *dyt = d.rvm.dyt;
+    auto g = [&](int i) { return dyt[i]; };
+    auto fn = [&](int j, float ktdyt) {
+      col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, a, a, f, tl);
+    };
+    rows_apply(d.n, d.cp, d.ri, d.cv32, d.gc, g, fn);
+    if (check) tel_flush(ctl, tl);
+    prewarp = warp_sums_to(f, a);
+  }
+  double r[19];
+  block_reduce(a, r, sh, col_smask(check, rp, move), col_mmask(rp, move), prewarp);
+  if (threadIdx.x == 0)
+    col_finalize(ctl, ic, r, t, check, rp, rp, move, phase, !restart && !rp);
+  __syncthreads();
+}
+
+// A mixed slot whose restart-point certificate candidate came within 1e-3 of the test
+// (kEscalate) continues in FP64 from that restart point, the FP64 anchor z^{n,0}: the FP64 state
+// starts there as at the start of a solve, with the iteration and epoch counters, the primal
+// weight and the step carried on, and the slot stays FP64.
+template <int RHO2>
+__device__ void batch_escalate(const BatchDesc &d, IterConsts &ic, double *sh) {
+  const RowVecs &rv = d.rv_;
+  const ColVecs &cv = d.cv_;
+  for (int j = threadIdx.x; j < d.n; j += kBT) cv.xt[j] = cv.x0[j];
+  for (int i = threadIdx.x; i < d.m; i += kBT) rv.yt[i] = rv.y0[i];
+  __syncthreads();
+  auto f1 = [&](int r, double s) { rv.kxt[r] = s; };
+  auto g1 = [&](int j) { return cv.xt[j]; };
+  rows_apply(d.m, d.rp, d.ci, d.rv, d.gr, g1, f1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Ctl *ctl = d.ctl;
+    ctl->status = kRunning;
+    ctl->restart_pending = 1;
+    ctl->stage = 1;
+    ctl->k = 0;
+    ctl->k_next = 0;
+    ctl->n_next = ctl->n;
+    ctl->mv_ready = 0;
+    d.ic->mixed = 0;
+    ic.mixed = 0;
+  }
+  __syncthreads();
+  batch_col_pass<RHO2>(d, ic, 1, sh);
+}
+
+template <int RHO2>
+__device__ void batch_iterate(const BatchDesc &d, IterConsts &ic, int iters, double *sh) {
   Ctl *ctl = d.ctl;
   for (int it = 0; it < iters; ++it) {
+    if (ctl->status == kEscalate) batch_escalate<RHO2>(d, ic, sh);
     if (ctl->status != kRunning) break;
-    batch_row_pass<RHO2>(d, ic, sh);
-    if (ctl->status != kRunning) break;
-    batch_col_pass<RHO2>(d, ic, 0, sh);
+    if (ic.mixed) batch_row_pass_mx<RHO2>(d, ic, sh);
+    else batch_row_pass<RHO2>(d, ic, sh);
+    if (ctl->status != kRunning) continue;
+    if (ic.mixed) batch_col_pass_mx<RHO2>(d, ic, 0, sh);
+    else batch_col_pass<RHO2>(d, ic, 0, sh);
   }
+  if (ctl->status == kEscalate) batch_escalate<RHO2>(d, ic, sh);
 }
 
 __global__ void __launch_bounds__(kBT)
@@ -341,13 +519,18 @@ k_batch(const BatchDesc *__restrict__ descs, int nslots, int iters) {
   const BatchDesc d = descs[slot];
   if (!d.active) return;
   Ctl *ctl = d.ctl;
-  if (ctl->status != kRunning) return;
+  if (ctl->status != kRunning && ctl->status != kEscalate) return;
   if (ctl->stage == 2) {            // new slot: set-up, then the set-up column step
     batch_setup(d, sh);
     if (threadIdx.x == 0) ics = *d.ic;
     __syncthreads();
-    if (ics.rho2) batch_col_pass<1>(d, ics, 1, sh);
-    else batch_col_pass<0>(d, ics, 1, sh);
+    if (ics.mixed) {
+      if (ics.rho2) batch_col_pass_mx<1>(d, ics, 1, sh);
+      else batch_col_pass_mx<0>(d, ics, 1, sh);
+    } else {
+      if (ics.rho2) batch_col_pass<1>(d, ics, 1, sh);
+      else batch_col_pass<0>(d, ics, 1, sh);
+    }
   } else {
     if (threadIdx.x == 0) ics = *d.ic;
     __syncthreads();
@@ -356,13 +539,16 @@ k_batch(const BatchDesc *__restrict__ descs, int nslots, int iters) {
   else batch_iterate<0>(d, ics, iters, sh);
 }
 
+// Unscaled result of a slot: x = E x~ of the last check; y = D y~, where a slot still in mixed
+// precision holds y~ as y0 + dyt.
 __global__ void k_batch_unscale(const BatchDesc *__restrict__ descs, int slot, double *xo,
                                 double *yo) {
   const BatchDesc d = descs[slot];
+  const bool mixed = d.mixed && d.ic->mixed;
   for (int j = threadIdx.x + blockIdx.x * blockDim.x; j < d.n; j += blockDim.x * gridDim.x)
     xo[j] = d.cv_.e[j] * d.cv_.xout[j];
   for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < d.m; i += blockDim.x * gridDim.x)
-    yo[i] = d.rv_.d[i] * d.rv_.yt[i];
+    yo[i] = d.rv_.d[i] * (mixed ? d.rvm.y0[i] + (double)d.rvm.dyt[i] : d.rv_.yt[i]);
 }
 
 int pick_group(double avg) {
@@ -407,12 +593,19 @@ namespace {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-size_t slot_bytes(int m, int n, long long nnz) {
+// Arena bytes of one slot: both CSR copies, the FP64 vectors, and for a mixed-precision slot the
+// FP32 values of both copies, six FP32 offset vectors per side and the exact FP64 offsets of the
+// restart points.
+size_t slot_bytes(int m, int n, long long nnz, bool mixed) {
   size_t b = 0;
+  const size_t nn = (size_t)std::max(n, 1), mm = (size_t)std::max(m, 1);
   b += align256((m + 1) * sizeof(int)) + align256(nnz * sizeof(int)) + align256(nnz * 8);
   b += align256((n + 1) * sizeof(int)) + align256(nnz * sizeof(int)) + align256(nnz * 8);
-  b += 15 * align256((size_t)std::max(n, 1) * 8) + 13 * align256((size_t)std::max(m, 1) * 8);
-  b += align256(sizeof(rh::IterConsts)) + align256(16) + align256((size_t)std::max(n, 1));
+  b += 15 * align256(nn * 8) + 13 * align256(mm * 8);
+  b += align256(sizeof(rh::IterConsts)) + align256(16) + align256(nn);
+  if (mixed)
+    b += 2 * align256(nnz * 4) + 6 * align256(nn * 4) + 6 * align256(mm * 4) + align256(nn * 8) +
+         align256(mm * 8);
   return b;
 }
 
@@ -509,8 +702,8 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   rhpdhg_params P;
   if (p) P = *p;
   else rhpdhg_params_default(&P);
-  if (P.precision != 0)
-    return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: the batched kernel computes in FP64");
+  if (P.precision != 0 && P.precision != 1)
+    return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: precision is 0 (FP64) or 1 (mixed)");
   if (P.adaptive_step)
     return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: batched slots use the constant step");
   if (P.algorithm < 0 || P.algorithm > 1 || P.check_every < 1 || P.max_iters < 1 ||
@@ -559,7 +752,8 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   for (int s = 0; s < b->max_slots; ++s)
     if (!b->host_desc[s].active) { slot = s; break; }
   if (slot < 0) return berr(b, RHPDHG_BUSY, "batch: no free slot");
-  const size_t need = slot_bytes(m, n, nnz);
+  const bool mixed = P.precision == 1;
+  const size_t need = slot_bytes(m, n, nnz, mixed);
   size_t off = 0;
   if (!arena_alloc(b, need, &off)) return berr(b, RHPDHG_ERR_OOM, "batch: arena full");
   char *base = b->arena + off;
@@ -605,6 +799,21 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   d.tmp_n = tmp_n;
   d.rv_ = rh::RowVecs{y, yt, y0, kx, kxt, kx0, certy, q, D, Dinv, certy2};
   d.cv_ = rh::ColVecs{x, xt, x0, kty, kty0, xout, certx, c, l, u, E, Einv, certx2, act};
+  d.mixed = mixed ? 1 : 0;
+  if (mixed) {
+    // the FP64 anchors, their products, outputs and certificates are shared with the FP64 state
+    const size_t nf = (size_t)std::max(n, 1) * 4, mf = (size_t)std::max(m, 1) * 4;
+    d.rv32 = (float *)take(nnz * 4);
+    d.cv32 = (float *)take(nnz * 4);
+    float *fx[6], *fy[6];
+    for (auto &f : fx) f = (float *)take(nf);
+    for (auto &f : fy) f = (float *)take(mf);
+    double *dxt64 = (double *)take(nb), *dyt64 = (double *)take(mb);
+    d.rvm = rh::RowVecsMx{fy[0], fy[1], fy[2], fy[3], fy[4], fy[5], y0, kx0, certy, dyt64, q, D,
+                          Dinv, certy2};
+    d.cvm = rh::ColVecsMx{fx[0], fx[1], fx[2], fx[3], fx[4], fx[5], x0, kty0, xout, certx, dxt64,
+                          c, l, u, E, Einv, certx2, act};
+  }
   d.ctl = ctl;
   d.ic = ic;
   d.setup_out = setup_out;
@@ -645,6 +854,7 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   ic0.obj_offset = lp->obj_offset;
   ic0.trace_cap = 0;
   ic0.trace = nullptr;
+  ic0.mixed = mixed ? 1 : 0;
   // the host copies must outlive the async copies: stage through a synchronisation
   cudaMemcpyAsync(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(ic, &ic0, sizeof(ic0), cudaMemcpyHostToDevice, st);
@@ -760,9 +970,9 @@ int64_t rhpdhg_batch_free_bytes(const rhpdhg_batch *b) {
   return (int64_t)t;
 }
 
-int64_t rhpdhg_batch_bytes_needed(const rhpdhg_problem *lp) {
-  if (!lp) return -1;
-  return (int64_t)slot_bytes(lp->m_eq + lp->m_ineq, lp->n, lp->nnz);
+int64_t rhpdhg_batch_bytes_needed(const rhpdhg_problem *lp, int32_t precision) {
+  if (!lp || (precision != 0 && precision != 1)) return -1;
+  return (int64_t)slot_bytes(lp->m_eq + lp->m_ineq, lp->n, lp->nnz, precision == 1);
 }
 
 int64_t rhpdhg_batch_launch_count(const rhpdhg_batch *b) { return b ? b->launches : -1; }

@@ -1,10 +1,13 @@
 // C ABI (include/rhpdhg.h): problem upload and preprocessing, the host driver of the device
 // iteration (CUDA-graph replays of C iterations, two in flight), polling and inspection.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -70,6 +73,7 @@ struct rhpdhg_handle {
   RowVecs rv{};
   ColVecs cv{};
   int grid_row = 1, grid_col = 1, smem_row = 0, smem_col = 0;
+  int grid_row1 = 1, grid_col1 = 1;   // restart-mode mixed kernels: at most one resident wave
   double eta = 1.0, omega0 = 1.0, sigma_max = 0.0;
 
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -90,6 +94,12 @@ struct rhpdhg_handle {
   bool escalated = false;      // this solve switched from mixed precision to FP64
   bool created_mixed = false;  // precision requested at create
   double bytes_row = 0, bytes_col = 0;
+  // autotuner: structure signature, outcome (0 = rule, 1 = timed at create, 2 = taken from the
+  // cache of an earlier handle with the same signature), and the per-iteration times (us) of
+  // the rule's geometry and of the chosen one
+  std::string tune_sig;
+  int tuned = 0;
+  double tune_us_rule = 0.0, tune_us_best = 0.0;
 };
 
 namespace {
@@ -186,16 +196,23 @@ void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
       bool wide = wide_row == 1;
       if (wide_row < 0 &&
           h->rows.nnz_short > (long long)lr.n_short_tiles * kWarp * kStageUnroll * 4) {
-        const int bw = iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide, wr * kWarp);
+        const int bw =
+            iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide, wr * kWarp, h->ic.df_sums);
         const long long need = ((long long)lr.total_items() + wr - 1) / wr;
         wide = bw > 0 && need <= (long long)bw * h->sm_count;
       }
       if (wide) lr.walk = kWalkWide;
     }
     h->grid_row = tile_grid(lr, h->sm_count,
-                            iter_mx_blocks_per_sm(h->smem_row, true, lr.walk, wr * kWarp));
+                            iter_mx_blocks_per_sm(h->smem_row, true, lr.walk, wr * kWarp,
+                                                  h->ic.df_sums));
     h->grid_col = tile_grid(lc, h->sm_count,
-                            iter_mx_blocks_per_sm(h->smem_col, false, lc.walk, wc * kWarp));
+                            iter_mx_blocks_per_sm(h->smem_col, false, lc.walk, wc * kWarp,
+                                                  h->ic.df_sums));
+    const int br = iter_mx_restart_blocks_per_sm(h->smem_row, true, wr * kWarp);
+    const int bc = iter_mx_restart_blocks_per_sm(h->smem_col, false, wc * kWarp);
+    h->grid_row1 = std::max(1, std::min(h->grid_row, h->sm_count * std::max(br, 1)));
+    h->grid_col1 = std::max(1, std::min(h->grid_col, h->sm_count * std::max(bc, 1)));
   } else {
     h->grid_row = tile_grid(lr, h->sm_count, row_iter_blocks_per_sm(h->smem_row, wr * kWarp));
     h->grid_col = tile_grid(lc, h->sm_count, col_iter_blocks_per_sm(h->smem_col, wc * kWarp));
@@ -205,7 +222,7 @@ void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
 void launch_row(rhpdhg_handle *h) {
   if (h->mixed)
     launch_row_iter_mx(h->st, h->rows, h->rvm, h->dxt, h->dxt64, h->x0, h->ctl, h->part_row,
-                       h->ic, h->grid_row, h->smem_row);
+                       h->ic, h->grid_row, h->grid_row1, h->smem_row);
   else
     launch_row_iter(h->st, h->rows, h->xt, h->rv, h->ctl, h->part_row, h->ic, h->grid_row,
                     h->smem_row);
@@ -214,7 +231,7 @@ void launch_row(rhpdhg_handle *h) {
 void launch_col(rhpdhg_handle *h, int phase) {
   if (h->mixed)
     launch_col_iter_mx(h->st, h->cols, h->cvm, h->dyt, h->dyt64, h->y0, h->ctl, h->part_col,
-                       h->ic, h->grid_col, h->smem_col, phase);
+                       h->ic, h->grid_col, h->grid_col1, h->smem_col, phase);
   else
     launch_col_iter(h->st, h->cols, h->yt, h->cv, h->ctl, h->part_col, h->ic, h->grid_col,
                     h->smem_col, phase);
@@ -305,6 +322,159 @@ int escalate_to_fp64(rhpdhg_handle *h) {
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   h->escalated = true;
+  return RHPDHG_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------------------
+// The launch geometry of the iteration kernels (warps per CTA of each side; for the mixed row
+// kernel also the plain or the wide staging walk) is chosen by timing candidates on the
+// handle's own stream: the solve's iteration kernels run on its state, every candidate
+// interleaved with the others, and each side keeps the candidate with the smallest median time
+// per launch.  The choice is cached for the process by a signature of the LP's structure, so
+// later handles of the same shape take it without timing.
+
+struct TuneChoice {
+  int wr = kBlockWarps, wc = kBlockWarps, wide = 0;
+  double us_rule = 0.0, us_best = 0.0;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune_cache;
+
+struct RowCand {
+  int warps, wide;
+};
+
+std::vector<RowCand> row_candidates(const rhpdhg_handle *h) {
+  std::vector<RowCand> c;
+  const bool can_widen = h->mixed && h->rows.lay.tile_mult == 1 && h->rows.lay.n_short_tiles > 0;
+  for (int w : {4, 8}) {
+    c.push_back({w, 0});
+    if (can_widen) c.push_back({w, 1});
+  }
+  return c;
+}
+const int kColCands[] = {4, 8};
+
+// Largest grid of each side over all candidates (the partial buffers are sized for it).
+void candidate_grids(rhpdhg_handle *h, int *max_row, int *max_col) {
+  const int wr = h->rows.lay.cta_warps, wc = h->cols.lay.cta_warps;
+  const int wide = h->rows.lay.walk == kWalkWide ? 1 : 0;
+  *max_row = h->grid_row;
+  *max_col = h->grid_col;
+  for (const RowCand &r : row_candidates(h))
+    for (int c : kColCands) {
+      set_geometry(h, r.warps, c, r.wide);
+      *max_row = std::max(*max_row, h->grid_row);
+      *max_col = std::max(*max_col, h->grid_col);
+    }
+  set_geometry(h, wr, wc, wide);
+}
+
+// Signature of the LP's structure for the cache: precision, algorithm, sum mode, sizes, SM
+// count, and the histograms (log2 buckets) of the row lengths of K and of K^T.
+std::string shape_signature(const rhpdhg_handle *h, const std::vector<int> &rp,
+                            const std::vector<int> &cp) {
+  std::string sig = std::to_string(h->mixed) + "/" + std::to_string(h->ic.rho2) + "/" +
+                    std::to_string(h->ic.df_sums) + "/" + std::to_string(h->m_eq) + "/" +
+                    std::to_string(h->m_ineq) + "/" + std::to_string(h->n) + "/" +
+                    std::to_string(h->nnz) + "/" + std::to_string(h->sm_count);
+  for (const std::vector<int> *v : {&rp, &cp}) {
+    long long hist[33] = {0};
+    for (size_t i = 0; i + 1 < v->size(); ++i) {
+      const int len = (*v)[i + 1] - (*v)[i];
+      int b = 0;
+      while (b < 32 && (1 << b) <= len) ++b;
+      hist[b]++;
+    }
+    sig += "|";
+    for (long long c : hist) sig += std::to_string(c) + ",";
+  }
+  return sig;
+}
+
+double median(std::vector<float> v) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  return 0.5 * (v[(v.size() - 1) / 2] + v[v.size() / 2]);
+}
+
+// Times the candidates (see above) and applies the fastest.  The state the timing leaves
+// behind is discarded: every solve starts with reset_state.
+int autotune(rhpdhg_handle *h) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(h->tune_sig);
+    if (it != g_tune_cache.end()) {
+      set_geometry(h, it->second.wr, it->second.wc, it->second.wide);
+      h->tuned = 2;
+      h->tune_us_rule = it->second.us_rule;
+      h->tune_us_best = it->second.us_best;
+      return RHPDHG_OK;
+    }
+  }
+  const std::vector<RowCand> rows = row_candidates(h);
+  const int nr = (int)rows.size(), nc = 2;
+  const RowCand rule_r{h->rows.lay.cta_warps, h->rows.lay.walk == kWalkWide ? 1 : 0};
+  const int rule_c = h->cols.lay.cta_warps;
+  // ordinary iterations only: no check, no restart, no trace while timing
+  const IterConsts saved = h->ic;
+  h->ic.check_every = INT_MAX;
+  h->ic.max_iters = LLONG_MAX / 4;
+  h->ic.restart_scheme = 0;
+  h->ic.first_epoch_len = INT_MAX / 2;
+  h->ic.max_epoch_len = 0;
+  h->ic.trace_cap = 0;
+  int rc = reset_state(h);
+  const int warm = 2, reps = 3;
+  const int K = warm + reps * nr * nc;
+  std::vector<cudaEvent_t> ev(3 * K);
+  for (auto &e : ev) cudaEventCreate(&e);
+  for (int i = 0; i < K && rc == RHPDHG_OK; ++i) {
+    const RowCand &r = rows[i % nr];
+    set_geometry(h, r.warps, kColCands[(i / nr) % nc], r.wide);
+    cudaEventRecord(ev[3 * i], h->st);
+    launch_row(h);
+    cudaEventRecord(ev[3 * i + 1], h->st);
+    launch_col(h, 0);
+    cudaEventRecord(ev[3 * i + 2], h->st);
+  }
+  h->launches += (h->mixed ? 8 : 2) + (long long)K * (h->mixed ? 4 : 2);
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  std::vector<std::vector<float>> tr(nr), tc(nc);
+  for (int i = warm; i < K && e == cudaSuccess; ++i) {
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
+    cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
+    tr[i % nr].push_back(a);
+    tc[(i / nr) % nc].push_back(b);
+  }
+  for (auto &ev_ : ev) cudaEventDestroy(ev_);
+  h->ic = saved;
+  if (rc != RHPDHG_OK) return rc;
+  if (e != cudaSuccess)
+    return set_err(h, RHPDHG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  int br = 0, bc = 0, ir = 0, icr = 0;
+  for (int i = 0; i < nr; ++i) {
+    if (median(tr[i]) < median(tr[br])) br = i;
+    if (rows[i].warps == rule_r.warps && rows[i].wide == rule_r.wide) ir = i;
+  }
+  for (int i = 0; i < nc; ++i) {
+    if (median(tc[i]) < median(tc[bc])) bc = i;
+    if (kColCands[i] == rule_c) icr = i;
+  }
+  TuneChoice ch;
+  ch.wr = rows[br].warps;
+  ch.wide = rows[br].wide;
+  ch.wc = kColCands[bc];
+  ch.us_rule = 1e3 * (median(tr[ir]) + median(tc[icr]));
+  ch.us_best = 1e3 * (median(tr[br]) + median(tc[bc]));
+  set_geometry(h, ch.wr, ch.wc, ch.wide);
+  h->tuned = 1;
+  h->tune_us_rule = ch.us_rule;
+  h->tune_us_best = ch.us_best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[h->tune_sig] = ch;
   return RHPDHG_OK;
 }
 
@@ -506,7 +676,8 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
       P.restart_scheme > 2 || (P.restart_scheme >= 1 && P.max_epoch_len < 1) ||
       !(P.restart_beta > 0 && P.restart_beta < 1) || P.trace_capacity < 0 ||
       P.pock_chambolle_alpha > 2.0 || P.adaptive_step < 0 || P.adaptive_step > 1 ||
-      (P.cta_warps != 0 && P.cta_warps != 4 && P.cta_warps != 8 && P.cta_warps != 16))
+      (P.cta_warps != 0 && P.cta_warps != 4 && P.cta_warps != 8 && P.cta_warps != 16) ||
+      P.df_sums < 0 || P.df_sums > 1 || P.autotune < 0 || P.autotune > 1)
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "invalid parameter");
   if ((P.dev_alloc == nullptr) != (P.dev_free == nullptr))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG,
@@ -655,6 +826,9 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     CKT(cudaMemcpy(hrp.data(), rp, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost));
     CKT(cudaMemcpy(hcp.data(), cp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
     const bool with32 = P.precision == 1;
+    h->ic.rho2 = P.algorithm == 1 ? 1 : 0;
+    h->ic.df_sums = P.df_sums;
+    if (P.autotune) h->tune_sig = shape_signature(h, hrp, hcp);
     CKT(build_side(st, m, nnz, rp, col, val, h->D, h->E, with32, &h->rows));
     CKT(build_side(st, n, nnz, cp, ridx, cval, h->E, h->D, with32, &h->cols));
   }
@@ -765,8 +939,12 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   CKC(dalloc(&h->ctl, 1));
   CKC(cudaHostAlloc((void **)&h->h_mirror, 2 * sizeof(Ctl), cudaHostAllocDefault));
   std::memset(h->h_mirror, 0, 2 * sizeof(Ctl));
-  CKC(dalloc(&h->part_row, (size_t)h->grid_row * kMaxPartials));
-  CKC(dalloc(&h->part_col, (size_t)h->grid_col * kMaxPartials));
+  {
+    int gr = h->grid_row, gc = h->grid_col;
+    if (P.autotune && P.cta_warps == 0) candidate_grids(h, &gr, &gc);
+    CKC(dalloc(&h->part_row, (size_t)gr * kMaxPartials));
+    CKC(dalloc(&h->part_col, (size_t)gc * kMaxPartials));
+  }
   if (P.trace && P.trace_capacity > 0) CKC(dalloc(&h->trace, (size_t)P.trace_capacity));
   CKC(cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), st));
 
@@ -806,6 +984,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   ic.trace_cap = h->trace ? P.trace_capacity : 0;
   ic.trace = h->trace;
   ic.mixed = h->mixed ? 1 : 0;
+  ic.df_sums = P.df_sums;
   ic.adaptive = P.adaptive_step ? 1 : 0;
   h->rv = RowVecs{h->y, h->yt, h->y0, h->kx, h->kxt, h->kx0, h->certy, h->q, h->D, h->Dinv,
                   h->certy2};
@@ -819,6 +998,10 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   h->launches = launches_so_far() - launches0;
   CKC(cudaStreamSynchronize(st));
   CKC(cudaGetLastError());
+  if (P.autotune && P.cta_warps == 0) {
+    const int rc = autotune(h);
+    if (rc != RHPDHG_OK) return fail(rc);
+  }
   *out = h;
   return RHPDHG_OK;
 #undef CKC
@@ -921,7 +1104,9 @@ int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity) {
   const int64_t v[RHPDHG_LAYOUT_FIELDS] = {h->grid_row,  h->grid_col,  r.tile_mult, c.tile_mult,
                                            r.n_long,     c.n_long,     r.n_chunks,  c.n_chunks,
                                            r.seg,        c.seg,        r.walk,      c.walk,
-                                           r.cta_warps,  c.cta_warps};
+                                           r.cta_warps,  c.cta_warps,  h->tuned,
+                                           (int64_t)std::llround(1e3 * h->tune_us_rule),
+                                           (int64_t)std::llround(1e3 * h->tune_us_best)};
   for (int i = 0; i < RHPDHG_LAYOUT_FIELDS; ++i) out[i] = v[i];
   return RHPDHG_OK;
 }

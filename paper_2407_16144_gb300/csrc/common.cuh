@@ -177,6 +177,8 @@ struct IterConsts {
   long long trace_cap;
   TraceRec *trace;
   int mixed;                  // 1 = FP32-offset iterates (certificates escalate to FP64)
+  int df_sums;                // mixed: 1 = double-float restart-norm sums from the lane up,
+                              // 0 = FP32 within each warp and FP64 above
   int adaptive;               // 1 = adaptive step rule (inadmissible steps are redone)
 };
 
@@ -259,6 +261,20 @@ __device__ __forceinline__ DF df_warp_sum(DF v) {
   return v;
 }
 
+// The packed slots carry either double-floats (EXACT) or plain FP32 sums in hi (lo = 0), which
+// the same reductions add with single FP32 additions: the FP32 option of the mixed-precision
+// restart-norm sums, whose dependent chains in the grid reduction stay short.
+template <bool EXACT>
+__device__ __forceinline__ DF dfx_add(DF x, DF y) {
+  if constexpr (EXACT) return df_add(x, y);
+  else return DF{__fadd_rn(x.hi, y.hi), 0.f};
+}
+template <bool EXACT>
+__device__ __forceinline__ DF dfx_warp_sum(DF v) {
+  if constexpr (EXACT) return df_warp_sum(v);
+  else return DF{warp_sum(v.hi), 0.f};
+}
+
 // A double-float travels through the 8-byte partial slots bit-packed (no FP64 arithmetic).
 __device__ __forceinline__ double df_pack(DF a) {
   return __hiloint2double(__float_as_int(a.hi), __float_as_int(a.lo));
@@ -272,8 +288,9 @@ __device__ __forceinline__ DF df_unpack(double v) {
 __device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
 
 // Per-thread accumulators of NS sums and NM maxima, reduced per CTA in a fixed order.  The first
-// ND sums are double-floats (d[0 .. ND-1]; s[0 .. ND-1] are unused), the others FP64.
-template <int NS, int NM, int ND = 0>
+// ND sums are packed slots (d[0 .. ND-1]; s[0 .. ND-1] are unused): double-floats when EXACT,
+// plain FP32 sums otherwise; the others are FP64.
+template <int NS, int NM, int ND = 0, bool EXACT = true>
 struct Acc {
   double s[NS > 0 ? NS : 1];
   double mx[NM > 0 ? NM : 1];
@@ -301,8 +318,8 @@ __device__ __forceinline__ double (*cta_red())[kMaxPartials] {
 // slots set in prewarp hold, in lane 0, a value already summed over the warp (FP64 slots only).
 // Returns true in every thread of the last CTA to finish (after a fence), which then owns the
 // grid-level reduction.
-template <int NS, int NM, int ND>
-__device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND> &a, unsigned smask, unsigned mmask,
+template <int NS, int NM, int ND, bool EXACT>
+__device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND, EXACT> &a, unsigned smask, unsigned mmask,
                                       unsigned prewarp, double *part, unsigned int *ticket) {
   double (*red)[kMaxPartials] = cta_red();
   __shared__ bool last;
@@ -313,7 +330,7 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND> &a, unsigned smask, unsign
   for (int i = 0; i < NS; ++i) {
     if (!((smask >> i) & 1u)) continue;
     if (i < ND) {
-      const DF v = df_warp_sum(a.d[i < ND ? i : 0]);
+      const DF v = dfx_warp_sum<EXACT>(a.d[i < ND ? i : 0]);
       if (lane == 0) red[warp][i] = df_pack(v);
     } else {
       const double v = ((prewarp >> i) & 1u) ? a.s[i] : warp_sum(a.s[i]);
@@ -334,7 +351,7 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND> &a, unsigned smask, unsign
       if (!((smask >> i) & 1u)) continue;
       if (i < ND) {
         DF v = df_unpack(red[0][i]);
-        for (int w = 1; w < nw; ++w) v = df_add(v, df_unpack(red[w][i]));
+        for (int w = 1; w < nw; ++w) v = dfx_add<EXACT>(v, df_unpack(red[w][i]));
         dst[i] = df_pack(v);
       } else {
         double v = red[0][i];
@@ -362,15 +379,15 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND> &a, unsigned smask, unsign
 // partials (lane 0; double-float slots bit-packed), then clear al.  Only sums need this (their
 // order decides the rounding); long-row maxima are taken into the finishing warp's own
 // accumulator.
-template <int NS, int ND>
-__device__ __forceinline__ void store_group(Acc<NS, 0, ND> &al, unsigned smask, double *gpart,
-                                            int grp) {
+template <int NS, int ND, bool EXACT>
+__device__ __forceinline__ void store_group(Acc<NS, 0, ND, EXACT> &al, unsigned smask,
+                                            double *gpart, int grp) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
     if (!((smask >> i) & 1u)) continue;
     if (i < ND) {
-      const DF v = df_warp_sum(al.d[i < ND ? i : 0]);
+      const DF v = dfx_warp_sum<EXACT>(al.d[i < ND ? i : 0]);
       if (lane == 0) gpart[(size_t)grp * kMaxPartials + i] = df_pack(v);
     } else {
       const double v = warp_sum(al.s[i]);
@@ -394,7 +411,7 @@ __device__ __forceinline__ void store_group(Acc<NS, 0, ND> &al, unsigned smask, 
 // BATCH = false keeps only the first (the FP64 kernels: ALU-bound, with fewer CTAs, where the
 // second gains nothing and its registers cost).
 constexpr int kGridBatch = 10;
-template <int NS, int NM, bool BATCH = true, int ND = 0>
+template <int NS, int NM, bool BATCH = true, int ND = 0, bool EXACT = true>
 __device__ void grid_finish(const double *part, double *out, unsigned smask, unsigned mmask,
                             const double *gpart = nullptr, int ngroups = 0) {
   double (*red)[kMaxPartials] = cta_red();
@@ -408,7 +425,7 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
   for (int i = 0; i < ND; ++i) vd[i] = DF{0.f, 0.f};
   // one partial p of slot i into the thread's running value
   auto take = [&](int i, double p) {
-    if (i < ND) vd[i < ND ? i : 0] = df_add(vd[i < ND ? i : 0], df_unpack(p));
+    if (i < ND) vd[i < ND ? i : 0] = dfx_add<EXACT>(vd[i < ND ? i : 0], df_unpack(p));
     else v[i] = (i < NS) ? v[i] + p : fmax(v[i], p);
   };
   const unsigned all = smask | (mmask << NS);
@@ -452,7 +469,7 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
   for (int i = 0; i < NS + NM; ++i) {
     if (!((all >> i) & 1u)) continue;
     if (i < ND) {
-      const DF r = df_warp_sum(vd[i < ND ? i : 0]);
+      const DF r = dfx_warp_sum<EXACT>(vd[i < ND ? i : 0]);
       if (lane == 0) red[warp][i] = df_pack(r);
     } else {
       const double r = (i < NS) ? warp_sum(v[i]) : warp_max(v[i]);
@@ -465,7 +482,7 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
     if (!((all >> i) & 1u)) { out[i] = 0.0; continue; }
     if (i < ND) {
       DF r = df_unpack(red[0][i]);
-      for (int w = 1; w < nw; ++w) r = df_add(r, df_unpack(red[w][i]));
+      for (int w = 1; w < nw; ++w) r = dfx_add<EXACT>(r, df_unpack(red[w][i]));
       out[i] = df_value(r);
     } else {
       double r = red[0][i];

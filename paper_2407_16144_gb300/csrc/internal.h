@@ -147,20 +147,25 @@ cudaError_t kkt_eval_with_scratch(const rhpdhg_problem *lp, const double *x, con
                                   double *out, bool *bad_index);
 
 // ---- mixed-precision iteration (iterate_mx.cu) -------------------------------------------------
+// grid: CTAs of the ordinary kernel; grid1: CTAs of the restart-mode kernel (at most one wave)
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
-                        double *part, const IterConsts &ic, int grid, int smem);
+                        double *part, const IterConsts &ic, int grid, int grid1, int smem);
 void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx &v,
                         const float *dyt, const double *dyt64, const double *y0, Ctl *ctl,
-                        double *part, const IterConsts &ic, int grid, int smem, int phase);
+                        double *part, const IterConsts &ic, int grid, int grid1, int smem,
+                        int phase);
+// Resident CTAs per SM of the restart-mode mixed kernels of one side (FP64 staging smem).
+int iter_mx_restart_blocks_per_sm(int smem, bool row, int threads);
 void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const double *xs,
                        const double *d, const double *y0, const float *dyt, double *xo,
                        double *yo, double *yt64);
 void zero_f32(cudaStream_t st, int n, float *x);
 void allow_large_smem_mx(int bytes);
 // Resident CTAs per SM of the ordinary mixed kernels of one side (row: K^, else K^T) in one
-// walk instantiation (kWalk*), for CTAs of `threads` threads.
-int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads);
+// walk instantiation (kWalk*) and one kind of restart-norm sums (IterConsts::df_sums), for
+// CTAs of `threads` threads.
+int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs);
 // opt in to dynamic shared memory above 48 KB for the tile kernels
 void allow_large_smem(int bytes);
 void allow_large_smem_setup(int bytes);

@@ -26,34 +26,34 @@
 // FP64 matrix, and the column kernel after it K^T (y~ - y0') in FP64.  The restart point's
 // displacement T(z^{n,0}) - z^{n,0}, the certificate candidate of Theorem infeas, is therefore
 // exact to FP64; all offsets restart from there.
+#include <type_traits>
+
 #include "internal.h"
 #include "iter_common.cuh"
+#include "iter_mx_common.cuh"
 
 namespace rh {
 
 namespace {
 
-// The restart test's norms (||dy||^2, dy^T K dx, ||y~ - y0||^2 and ||dx||^2, ||x~ - x0||^2) of
-// the ordinary kernels are double-float sums (common.cuh) of exact products of the FP32 offsets:
-// FP64-grade sums that run on the FP32 pipe.  The restart kernels (MODE 1) sum in FP64.
+// packed slots of the CTA accumulators: the restart-norm sums of the ordinary kernels
 template <int MODE>
 constexpr int row_df_slots() { return MODE == 0 ? 3 : 0; }
 template <int MODE>
 constexpr int col_df_slots() { return MODE == 0 ? 2 : 0; }
-__device__ __forceinline__ void df_acc(DF &d, float a, float b) { d = df_add(d, df_prod(a, b)); }
 
 // Register budgets: the ordinary kernels (MODE 0) of the plain and grouped walks 64 (32 resident
-// warps per SM), the wide walk 80, the restart kernels (MODE 1) 128.  The CTA width is chosen
-// at launch (up to kMaxBlockThreads).
-__host__ __device__ constexpr int mx_max_regs(int mode, int walk) {
-  return mode == 1 ? 128 : (walk == kWalkWide ? 80 : 64);
+// warps per SM), the wide walk 80 (96 with double-float sums), the restart kernels (MODE 1) 128.
+// The CTA width is chosen at launch (up to kMaxBlockThreads).
+__host__ __device__ constexpr int mx_max_regs(int mode, int walk, int dfs) {
+  return mode == 1 ? 128 : (walk == kWalkWide ? (dfs ? 96 : 80) : 64);
 }
 
 // MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
 // MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
 // launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
-template <int RHO2, int MODE, int WALK>
-__global__ void __maxnreg__(mx_max_regs(MODE, WALK))
+template <int RHO2, int MODE, int WALK, int DFS>
+__global__ void __maxnreg__(mx_max_regs(MODE, WALK, DFS))
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
               const double *__restrict__ dxt64, const double *__restrict__ x0, Ctl *ctl,
@@ -74,8 +74,8 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
   float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
   constexpr int ND = row_df_slots<MODE>();
-  Acc<7, 6, ND> a;
-  Acc<7, 0, ND> al;     // long-row sums (see walk_tiles); long-row maxima go to a
+  Acc<7, 6, ND, DFS == 1> a;
+  Acc<7, 0, ND, DFS == 1> al;   // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
   const unsigned smask = row_smask(check, rp, move);
@@ -88,100 +88,33 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     // Theorem infeas uses as the certificate candidate, carries no FP32 rounding.
     // With move set, the old anchor first gives the row parts of the anchor movement
     // z^{n+1,0} - z^{n,0} (y0' = y0 + dyt, K x0' from this walk), in FP64.
-    auto moveparts = [&](int i, double dot, auto &S) {
-      const double y0i = v.y0[i];
-      const double dyb = (y0i + (double)v.dyt[i]) - y0i;
-      const double kdb = (dot - v.kx0[i]) * v.dinv[i];
-      const double di = v.d[i];
-      S.s[6] += v.q[i] * dyb;
-      if (i >= m_eq) a.mx[3] = fmax(a.mx[3], fmax(-dyb * di, 0.0));
-      if (i < m_eq) a.mx[4] = fmax(a.mx[4], fabs(kdb));
-      else a.mx[5] = fmax(a.mx[5], fmax(-kdb, 0.0));
-      v.certy2[i] = dyb * di;
-    };
     auto epiA = [&](int i, double dot, bool lg) {
       if (move) {
-        if (lg) moveparts(i, dot, al);
-        else moveparts(i, dot, a);
+        if (lg) row_mx_move(i, dot, v, m_eq, al, a);
+        else row_mx_move(i, dot, v, m_eq, a, a);
       }
       v.kx0[i] = dot;
     };
     auto gA = [&](int j) { return x0[j]; };
     auto gdoneA = [&](int grp) { store_group(al, smask & 0x40u, wb.group_part, grp); };
     walk_tiles<double, double>(lay, v64, gA, my64, wa, epiA, gdoneA);
-    auto body = [&](int i, double kd, auto &A) {
-      const double y0i = v.y0[i] + (double)v.dyt[i];     // y0' = y~ of the restart iteration
-      v.y0[i] = y0i;
-      const double kx0i = __ldcg(v.kx0 + i);              // may come from another warp
-      const double qi = v.q[i];
-      v.r0[i] = (float)(sigma * (qi - kx0i));
-      v.ylo[i] = (i >= m_eq) ? __double2float_ru(-y0i) : -INFINITY;
-      if (RHO2) { v.dy[i] = 0.f; v.kdx[i] = 0.f; }
-      double nd = sigma * (qi - kx0i - 2.0 * kd);
-      if (i >= m_eq) nd = fmax(nd, -y0i);
-      v.dyt64[i] = nd;
-      v.dyt[i] = (float)nd;
-      v.kdxt[i] = (float)kd;
-      A.s[0] += nd * nd;            // dy = 0
-      A.s[1] += -nd * (-kd);        // (dy - dyt) (K dx - K dxt) with dy = 0, K dx = 0
-      A.s[2] += nd * nd;
-      if (check) {
-        double r = (qi - kx0i - kd) * v.dinv[i];
-        if (i >= m_eq) r = fmax(r, 0.0);
-        A.s[3] += r * r;
-        A.s[4] += qi * (y0i + nd);
-      }
-      if (rp) {
-        A.s[5] += qi * nd;
-        const double di = v.d[i];
-        if (i >= m_eq) a.mx[0] = fmax(a.mx[0], fmax(-nd * di, 0.0));
-        const double kdd = kd * v.dinv[i];
-        if (i < m_eq) a.mx[1] = fmax(a.mx[1], fabs(kdd));
-        else a.mx[2] = fmax(a.mx[2], fmax(-kdd, 0.0));
-        v.certy[i] = nd * di;
-      }
-    };
     auto epi = [&](int i, double kd, bool lg) {
-      if (lg) body(i, kd, al);
-      else body(i, kd, a);
+      if (lg) row_mx_restart<RHO2>(i, kd, v, sigma, m_eq, check, rp, al, a);
+      else row_mx_restart<RHO2>(i, kd, v, sigma, m_eq, check, rp, a, a);
     };
     auto gdone = [&](int grp) { store_group(al, smask & ~0x40u, wb.group_part, grp); };
     auto gB = [&](int j) { return dxt64[j]; };
     walk_tiles<double, double>(lay, v64, gB, my64, wb, epi, gdone);
   } else {
-    auto body = [&](int i, float kd, auto &A) {
-      const float dytp = v.dyt[i], kdxtp = v.kdxt[i];
-      float dy, kdx;
-      if (RHO2) {
-        dy = wf * (2.f * dytp - v.dy[i]);
-        kdx = wf * (2.f * kdxtp - v.kdx[i]);
-        v.dy[i] = dy;
-        v.kdx[i] = kdx;
-      } else {
-        dy = wf * dytp;
-        kdx = wf * kdxtp;
-      }
-      float nd = dy + v.r0[i] + sigf * (kdx - 2.f * kd);
-      if (i >= m_eq) nd = fmaxf(nd, v.ylo[i]);
-      v.dyt[i] = nd;
-      v.kdxt[i] = kd;
-      const float ddy = dy - nd;
-      df_acc(A.d[0], ddy, ddy);
-      df_acc(A.d[1], ddy, kdx - kd);
-      df_acc(A.d[2], nd, nd);
-      if (check) {
-        const double qi = v.q[i];
-        double r = (qi - v.kx0[i] - (double)kd) * v.dinv[i];
-        if (i >= m_eq) r = fmax(r, 0.0);
-        A.s[3] += r * r;
-        A.s[4] += qi * (v.y0[i] + (double)nd);
-      }
-    };
+    FprSums<3, DFS> fa, fl;   // restart-norm sums of short rows and of long rows
     auto epi = [&](int i, float kd, bool lg) {
-      if (lg) body(i, kd, al);
-      else body(i, kd, a);
+      if (lg) row_mx_ordinary<RHO2>(i, kd, v, wf, sigf, m_eq, check, al, fl);
+      else row_mx_ordinary<RHO2>(i, kd, v, wf, sigf, m_eq, check, a, fa);
     };
-    auto gdone = [&](int grp) { store_group(al, smask, wb.group_part, grp); };
+    auto gdone = [&](int grp) {
+      fl.flush(al);
+      store_group(al, smask, wb.group_part, grp);
+    };
     auto gB = [&](int j) { return dxt[j]; };
     auto pre = [&](int i) {
       prefetch_l1(v.dyt + i);
@@ -195,17 +128,19 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     };
     walk_tiles<float, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
                                                                        epi, gdone, pre);
+    fa.flush(a);
   }
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
     double r[13];
-    grid_finish<7, 6, true, ND>(part, r, smask, mmask, wb.group_part, lay.n_long_tiles);
+    grid_finish<7, 6, true, ND, DFS == 1>(part, r, smask, mmask, wb.group_part,
+                                          lay.n_long_tiles);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
   }
 }
 
 // MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
-template <int RHO2, int MODE, int WALK>
-__global__ void __maxnreg__(mx_max_regs(MODE, WALK))
+template <int RHO2, int MODE, int WALK, int DFS>
+__global__ void __maxnreg__(mx_max_regs(MODE, WALK, DFS))
 k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
               const double *__restrict__ dyt64, const double *__restrict__ y0, Ctl *ctl,
@@ -225,125 +160,44 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
   float *my32 = reinterpret_cast<float *>(smem) + (threadIdx.x >> 5) * lay.seg;
   constexpr int ND = col_df_slots<MODE>();
-  Acc<11, 8, ND> a;
-  Acc<11, 0, ND> al;    // long-row sums (see walk_tiles); long-row maxima go to a
+  Acc<11, 8, ND, DFS == 1> a;
+  Acc<11, 0, ND, DFS == 1> al;  // long-row sums (see walk_tiles); long-row maxima go to a
   a.zero();
   al.zero();
+  FprSums<2, DFS> fa, fl;   // restart-norm sums of the ordinary iterations (MODE 0)
   Tel tl;         // active-set telemetry (ordinary check iterations)
   const unsigned smask = col_smask(check, rp, move);
   const unsigned mmask = col_mmask(rp, move);
 
-  // checks and certificates at (x~_t, y~_t) given x~_t - x0 (xo), K^T y~_t (kty) and
-  // K^T (y~_t - y_t) (ktd), all FP64
-  auto checks = [&](int j, double x0j, double xo, double kty, double ktd, auto &A) {
-    const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
-    if (check) {
-      const double g = cj - kty;
-      const double lam = proj_lambda(g, lj, uj);
-      const double rd = (g - lam) * v.einv[j];
-      A.s[2] += rd * rd;
-      const double xt = x0j + xo;
-      A.s[3] += cj * xt;
-      if (lam > 0.0) A.s[4] += lj * lam;
-      else if (lam < 0.0) A.s[4] += uj * lam;
-      v.xout[j] = xt;
-    }
-    // x-part of T(z) - z at the restart point, and K^T of its y-part
-    if (rp) col_cert_parts(j, xo, ktd, v, cj, lj, uj, A, a, 5, 0, v.certx);
+  auto gdone = [&](int grp) {
+    if constexpr (MODE == 0) fl.flush(al);
+    store_group(al, smask, (restart ? wa : wb).group_part, grp);
   };
-  auto gdone = [&](int grp) { store_group(al, smask, (restart ? wa : wb).group_part, grp); };
 
   if constexpr (MODE == 1) {
    if (restart) {
     // z^{n+1,0} = T(z^{n,k}): K^T y0' exactly (FP64 matrix, gathered y0 + dyt), x0' = x0 + dxt,
     // and the next PDHG point x~_{t+1} - x0' in FP64 (kept in dxt64 for the restart point's
     // certificate test)
-    auto body = [&](int j, double kty, auto &A) {
-      const double x0j = v.x0[j];
-      const float dxtj = v.dxt[j];
-      const double ktd = kty - v.kty0[j];
-      checks(j, x0j, (double)dxtj, kty, ktd, A);
-      const double x0n = x0j + (double)dxtj;
-      // column parts of the anchor movement z^{n+1,0} - z^{n,0}, against the old anchor
-      if (move)
-        col_cert_parts(j, x0n - x0j, ktd, v, v.c[j], v.l[j], v.u[j], A, a, 8, 4, v.certx2);
-      v.x0[j] = x0n;
-      v.kty0[j] = kty;
-      const double cj = v.c[j], lj = v.l[j], uj = v.u[j];
-      v.s0[j] = (float)(-tau * (cj - kty));
-      v.xlo[j] = __double2float_ru(lj - x0n);
-      v.xhi[j] = __double2float_rd(uj - x0n);
-      if (RHO2) { v.dx[j] = 0.f; v.ktdy[j] = 0.f; }
-      const double nt = fmin(fmax(x0n - tau * (cj - kty), lj), uj) - x0n;
-      v.dxt64[j] = nt;
-      v.dxt[j] = (float)nt;
-      A.s[0] += nt * nt;
-      A.s[1] += nt * nt;
-    };
     auto epi = [&](int j, double kty, bool lg) {
-      if (lg) body(j, kty, al);
-      else body(j, kty, a);
+      if (lg) col_mx_restart<RHO2>(j, kty, v, tau, check, rp, move, al, a);
+      else col_mx_restart<RHO2>(j, kty, v, tau, check, rp, move, a, a);
     };
     auto gA = [&](int i) { return y0[i] + (double)dyt[i]; };
     walk_tiles<double, double>(lay, v64, gA, my64, wa, epi, gdone);
    } else {
     // first iteration of an epoch: K^T (y~ - y0) in FP64 from the exact dyt64 of the row kernel
-    auto body = [&](int j, double ktd, auto &A) {
-      const double xo = v.dxt64[j];
-      const double x0j = check ? v.x0[j] : 0.0;
-      const double kty = check ? v.kty0[j] + ktd : 0.0;
-      checks(j, x0j, xo, kty, ktd, A);
-      const float dxtj = (float)xo, ktdyt = (float)ktd;
-      float dxn, ktn;
-      if (RHO2) {
-        dxn = wf * (2.f * dxtj - v.dx[j]);
-        ktn = wf * (2.f * ktdyt - v.ktdy[j]);
-        v.dx[j] = dxn;
-        v.ktdy[j] = ktn;
-      } else {
-        dxn = wf * dxtj;
-        ktn = wf * ktdyt;
-      }
-      const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
-      v.dxt[j] = nt;
-      const float ddx = dxn - nt;
-      A.s[0] += (double)ddx * (double)ddx;
-      A.s[1] += (double)nt * (double)nt;
-    };
     auto epi = [&](int j, double ktd, bool lg) {
-      if (lg) body(j, ktd, al);
-      else body(j, ktd, a);
+      if (lg) col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, al, a);
+      else col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, a, a);
     };
     auto gA = [&](int i) { return dyt64[i]; };
     walk_tiles<double, double>(lay, v64, gA, my64, wb, epi, gdone);
    }
   } else {
-    auto body = [&](int j, float ktdyt, auto &A) {
-      const float dxtj = v.dxt[j];
-      if (check) {
-        tel_column(j, dxtj == v.xlo[j] || dxtj == v.xhi[j], v.act, tl);
-        const double x0j = v.x0[j];
-        checks(j, x0j, (double)dxtj, v.kty0[j] + (double)ktdyt, (double)ktdyt, A);
-      }
-      float dxn, ktn;
-      if (RHO2) {
-        dxn = wf * (2.f * dxtj - v.dx[j]);
-        ktn = wf * (2.f * ktdyt - v.ktdy[j]);
-        v.dx[j] = dxn;
-        v.ktdy[j] = ktn;
-      } else {
-        dxn = wf * dxtj;
-        ktn = wf * ktdyt;
-      }
-      const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
-      v.dxt[j] = nt;
-      const float ddx = dxn - nt;
-      df_acc(A.d[0], ddx, ddx);
-      df_acc(A.d[1], nt, nt);
-    };
     auto epi = [&](int j, float ktdyt, bool lg) {
-      if (lg) body(j, ktdyt, al);
-      else body(j, ktdyt, a);
+      if (lg) col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, al, a, fl, tl);
+      else col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, a, a, fa, tl);
     };
     auto gB = [&](int i) { return dyt[i]; };
     auto pre = [&](int j) {
@@ -359,11 +213,12 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
     walk_tiles<float, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
                                                                        epi, gdone, pre);
     if (check) tel_flush(ctl, tl);
+    fa.flush(a);
   }
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[19];
-    grid_finish<11, 8, true, ND>(part, r, smask, mmask, (restart ? wa : wb).group_part,
-                                 lay.n_long_tiles);
+    grid_finish<11, 8, true, ND, DFS == 1>(part, r, smask, mmask,
+                                           (restart ? wa : wb).group_part, lay.n_long_tiles);
     if (threadIdx.x == 0) col_finalize(ctl, ic, r, t, check, rp, rp, move, phase, MODE == 0);
   }
 }
@@ -390,45 +245,57 @@ __global__ void k_zero_f32(int n, float *x) {
 
 // The restart-mode kernel (MODE 1) of each stage is launched first and returns at entry unless
 // the stage needs it; the ordinary kernel (MODE 0) follows, in the instantiation of the side's
-// walk (SideLayout::walk).
+// walk (SideLayout::walk) and of the solve's restart-norm sums (IterConsts::df_sums).
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+// f(IC<walk>) for the walks a side's ordinary kernel may take (the wide staging round is a row
+// side instantiation only)
+template <bool ROW, class F>
+void with_walk(int walk, F &&f) {
+  if (walk == kWalkGrouped) f(IC<kWalkGrouped>{});
+  else if (ROW && walk == kWalkWide) f(IC<ROW ? kWalkWide : kWalkPlain>{});
+  else f(IC<kWalkPlain>{});
+}
+
+template <class F>
+void with_rho_dfs(int rho2, int dfs, F &&f) {
+  auto g = [&](auto R) { dfs ? f(R, IC<1>{}) : f(R, IC<0>{}); };
+  rho2 ? g(IC<1>{}) : g(IC<0>{});
+}
+
+// grid: CTAs of the ordinary kernel; grid1: CTAs of the restart-mode kernel, at most one resident
+// wave (its walk and its grid reduction serve any grid), so that its launch, which returns at
+// entry in all but a few iterations, takes a single wave of CTAs.
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
-                        double *part, const IterConsts &ic, int grid, int smem) {
+                        double *part, const IterConsts &ic, int grid, int grid1, int smem) {
   const int threads = side.lay.cta_warps * kWarp;
-  auto go = [&](auto kern, int sm) {
-    kern<<<grid, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dxt,
-                                    dxt64, x0, ctl, part, ic);
+  auto go = [&](auto kern, int g, int sm) {
+    kern<<<g, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dxt, dxt64,
+                                 x0, ctl, part, ic);
   };
-  const int w = side.lay.walk;
-  if (ic.rho2) {
-    go(k_row_iter_mx<1, 1, kWalkGrouped>, smem);
-    if (w == kWalkGrouped) go(k_row_iter_mx<1, 0, kWalkGrouped>, smem / 2);
-    else if (w == kWalkWide) go(k_row_iter_mx<1, 0, kWalkWide>, smem / 2);
-    else go(k_row_iter_mx<1, 0, kWalkPlain>, smem / 2);
-  } else {
-    go(k_row_iter_mx<0, 1, kWalkGrouped>, smem);
-    if (w == kWalkGrouped) go(k_row_iter_mx<0, 0, kWalkGrouped>, smem / 2);
-    else if (w == kWalkWide) go(k_row_iter_mx<0, 0, kWalkWide>, smem / 2);
-    else go(k_row_iter_mx<0, 0, kWalkPlain>, smem / 2);
-  }
+  with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
+    go(k_row_iter_mx<R(), 1, kWalkGrouped, 0>, grid1, smem);
+    with_walk<true>(side.lay.walk,
+                    [&](auto W) { go(k_row_iter_mx<R(), 0, W(), D()>, grid, smem / 2); });
+  });
 }
 
 void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx &v,
                         const float *dyt, const double *dyt64, const double *y0, Ctl *ctl,
-                        double *part, const IterConsts &ic, int grid, int smem, int phase) {
+                        double *part, const IterConsts &ic, int grid, int grid1, int smem,
+                        int phase) {
   const int threads = side.lay.cta_warps * kWarp;
-  auto go = [&](auto kern, int sm) {
-    kern<<<grid, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dyt,
-                                    dyt64, y0, ctl, part, ic, phase);
+  auto go = [&](auto kern, int g, int sm) {
+    kern<<<g, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dyt, dyt64,
+                                 y0, ctl, part, ic, phase);
   };
-  const bool grp = side.lay.walk == kWalkGrouped;
-  if (ic.rho2) {
-    go(k_col_iter_mx<1, 1, kWalkGrouped>, smem);
-    grp ? go(k_col_iter_mx<1, 0, kWalkGrouped>, smem / 2) : go(k_col_iter_mx<1, 0, kWalkPlain>, smem / 2);
-  } else {
-    go(k_col_iter_mx<0, 1, kWalkGrouped>, smem);
-    grp ? go(k_col_iter_mx<0, 0, kWalkGrouped>, smem / 2) : go(k_col_iter_mx<0, 0, kWalkPlain>, smem / 2);
-  }
+  with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
+    go(k_col_iter_mx<R(), 1, kWalkGrouped, 0>, grid1, smem);
+    with_walk<false>(side.lay.walk,
+                     [&](auto W) { go(k_col_iter_mx<R(), 0, W(), D()>, grid, smem / 2); });
+  });
 }
 
 void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const double *xs,
@@ -444,39 +311,52 @@ void zero_f32(cudaStream_t st, int n, float *x) {
 }
 
 void allow_large_smem_mx(int bytes) {
-  const void *k[] = {
-      (const void *)k_row_iter_mx<0, 0, kWalkPlain>,   (const void *)k_row_iter_mx<1, 0, kWalkPlain>,
-      (const void *)k_row_iter_mx<0, 0, kWalkWide>,    (const void *)k_row_iter_mx<1, 0, kWalkWide>,
-      (const void *)k_row_iter_mx<0, 0, kWalkGrouped>, (const void *)k_row_iter_mx<1, 0, kWalkGrouped>,
-      (const void *)k_row_iter_mx<0, 1, kWalkGrouped>, (const void *)k_row_iter_mx<1, 1, kWalkGrouped>,
-      (const void *)k_col_iter_mx<0, 0, kWalkPlain>,   (const void *)k_col_iter_mx<1, 0, kWalkPlain>,
-      (const void *)k_col_iter_mx<0, 0, kWalkGrouped>, (const void *)k_col_iter_mx<1, 0, kWalkGrouped>,
-      (const void *)k_col_iter_mx<0, 1, kWalkGrouped>, (const void *)k_col_iter_mx<1, 1, kWalkGrouped>};
-  for (const void *f : k) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  auto set = [&](const void *f) {
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  };
+  for (int rho2 = 0; rho2 < 2; ++rho2)
+    for (int dfs = 0; dfs < 2; ++dfs)
+      with_rho_dfs(rho2, dfs, [&](auto R, auto D) {
+        set((const void *)k_row_iter_mx<R(), 1, kWalkGrouped, 0>);
+        set((const void *)k_col_iter_mx<R(), 1, kWalkGrouped, 0>);
+        for (int w : {kWalkPlain, kWalkWide, kWalkGrouped}) {
+          with_walk<true>(w, [&](auto W) { set((const void *)k_row_iter_mx<R(), 0, W(), D()>); });
+          with_walk<false>(w, [&](auto W) { set((const void *)k_col_iter_mx<R(), 0, W(), D()>); });
+        }
+      });
 }
 
-int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads) {
-  // the ordinary kernels of one side in one walk instantiation (both reflection settings)
-  const void *k[2];
-  if (row) {
-    k[0] = walk == kWalkGrouped ? (const void *)k_row_iter_mx<0, 0, kWalkGrouped>
-           : walk == kWalkWide  ? (const void *)k_row_iter_mx<0, 0, kWalkWide>
-                                : (const void *)k_row_iter_mx<0, 0, kWalkPlain>;
-    k[1] = walk == kWalkGrouped ? (const void *)k_row_iter_mx<1, 0, kWalkGrouped>
-           : walk == kWalkWide  ? (const void *)k_row_iter_mx<1, 0, kWalkWide>
-                                : (const void *)k_row_iter_mx<1, 0, kWalkPlain>;
-  } else {
-    k[0] = walk == kWalkGrouped ? (const void *)k_col_iter_mx<0, 0, kWalkGrouped>
-                                : (const void *)k_col_iter_mx<0, 0, kWalkPlain>;
-    k[1] = walk == kWalkGrouped ? (const void *)k_col_iter_mx<1, 0, kWalkGrouped>
-                                : (const void *)k_col_iter_mx<1, 0, kWalkPlain>;
-  }
+int iter_mx_restart_blocks_per_sm(int smem, bool row, int threads) {
   int mn = 1 << 30;
-  for (const void *f : k) {
+  auto occ = [&](const void *f) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, smem);
+    mn = b < mn ? b : mn;
+  };
+  if (row) {
+    occ((const void *)k_row_iter_mx<0, 1, kWalkGrouped, 0>);
+    occ((const void *)k_row_iter_mx<1, 1, kWalkGrouped, 0>);
+  } else {
+    occ((const void *)k_col_iter_mx<0, 1, kWalkGrouped, 0>);
+    occ((const void *)k_col_iter_mx<1, 1, kWalkGrouped, 0>);
+  }
+  return mn;
+}
+
+int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs) {
+  // the ordinary kernels of one side in one walk instantiation and one kind of restart-norm
+  // sums (both reflection settings)
+  int mn = 1 << 30;
+  auto occ = [&](const void *f) {
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, smem / 2);
     mn = b < mn ? b : mn;
-  }
+  };
+  for (int rho2 = 0; rho2 < 2; ++rho2)
+      with_rho_dfs(rho2, dfs, [&](auto R, auto D) {
+        if (row) with_walk<true>(walk, [&](auto W) { occ((const void *)k_row_iter_mx<R(), 0, W(), D()>); });
+        else with_walk<false>(walk, [&](auto W) { occ((const void *)k_col_iter_mx<R(), 0, W(), D()>); });
+      });
   return mn;
 }
 

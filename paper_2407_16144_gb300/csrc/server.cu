@@ -131,7 +131,7 @@ void worker_loop(rhpdhg_server *s) {
         const int64_t nnz = r.row_ptr.back();
         rhpdhg_problem p = r.problem();
         bool admitted = false;
-        if (nnz <= s->small_nnz && r.params.precision == 0 && !r.params.adaptive_step) {
+        if (nnz <= s->small_nnz && !r.params.adaptive_step) {
           int32_t slot = -1;
           const int rc = rhpdhg_batch_add(s->batch, &p, &r.params, &slot);
           if (rc == RHPDHG_OK) {
@@ -252,7 +252,7 @@ int rhpdhg_server_create(int64_t budget_bytes, int64_t small_nnz, int32_t max_sl
   probe.m_eq = (int32_t)std::min<int64_t>(small_nnz / 5 + 1, INT32_MAX / 2);
   probe.n = (int32_t)std::min<int64_t>(small_nnz / 5 * 2 + 1, INT32_MAX / 2);
   probe.nnz = small_nnz;
-  const int64_t per = rhpdhg_batch_bytes_needed(&probe);
+  const int64_t per = rhpdhg_batch_bytes_needed(&probe, 1);
   s->arena_bytes = std::max<int64_t>(std::min<int64_t>(budget_bytes / 4, per * max_slots), 1 << 20);
   const int rc = rhpdhg_batch_create(max_slots, s->arena_bytes, nullptr, &s->batch);
   if (rc != RHPDHG_OK) {

@@ -57,8 +57,8 @@ class rhpdhg_params(C.Structure):
                 ("use_graphs", C.c_int32), ("trace", C.c_int32), ("profile", C.c_int32),
                 ("trace_capacity", C.c_int64), ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("adaptive_step", C.c_int32), ("cta_warps", C.c_int32),
-                ("reserved", C.c_int32), ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
-                ("alloc_ctx", C.c_void_p)]
+                ("df_sums", C.c_int32), ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
+                ("alloc_ctx", C.c_void_p), ("autotune", C.c_int32), ("reserved", C.c_int32)]
 
 
 class rhpdhg_result(C.Structure):
@@ -135,7 +135,7 @@ def load(path: str = LIB_PATH):
         "rhpdhg_batch_remove": (C.c_int, [H, C.c_int32]),
         "rhpdhg_batch_slot_status": (C.c_int, [H, C.c_int32]),
         "rhpdhg_batch_free_bytes": (C.c_int64, [H]),
-        "rhpdhg_batch_bytes_needed": (C.c_int64, [C.POINTER(rhpdhg_problem)]),
+        "rhpdhg_batch_bytes_needed": (C.c_int64, [C.POINTER(rhpdhg_problem), C.c_int32]),
         "rhpdhg_batch_launch_count": (C.c_int64, [H]),
         "rhpdhg_batch_free": (None, [H]),
         "rhpdhg_server_create": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int32,
@@ -210,7 +210,8 @@ def rhpdhg_get_trace(h, capacity: int):
 
 LAYOUT_FIELDS = ("grid_row", "grid_col", "tile_mult_row", "tile_mult_col", "long_rows_row",
                  "long_rows_col", "chunks_row", "chunks_col", "seg_row", "seg_col", "walk_row",
-                 "walk_col", "cta_warps_row", "cta_warps_col")
+                 "walk_col", "cta_warps_row", "cta_warps_col", "tuned", "tune_ns_rule",
+                 "tune_ns_best")
 
 
 def rhpdhg_get_layout(h):
@@ -314,8 +315,8 @@ def rhpdhg_batch_free_bytes(b) -> int:
     return load().rhpdhg_batch_free_bytes(b)
 
 
-def rhpdhg_batch_bytes_needed(lp: rhpdhg_problem) -> int:
-    return load().rhpdhg_batch_bytes_needed(C.byref(lp))
+def rhpdhg_batch_bytes_needed(lp: rhpdhg_problem, precision: int = 0) -> int:
+    return load().rhpdhg_batch_bytes_needed(C.byref(lp), precision)
 
 
 def rhpdhg_batch_launch_count(b) -> int:

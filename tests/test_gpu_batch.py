@@ -144,3 +144,76 @@ def test_batch_capacity_limits(rh):
         assert b.add(lp) == -1                         # no free slot (BUSY)
         b.remove(0)
         assert b.add(lp) == 0 and b.free_bytes() >= 0
+
+
+# ---------------------------------------------------------------------------------------------
+# mixed-precision slots (FP32 values and offsets in ordinary iterations, FP64 restarts, restart
+# points and checks): accuracy parity with the FP64 oracle, as for the single-LP mixed path
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_batch_mixed_slots_reach_tolerance(rh, alg):
+    lps = mix(seed0=80)
+    tol = 1e-6
+    with rh.Batch(16, 256 << 20) as b:
+        slots = [b.add(lp, algorithm=alg, precision=1, eps_rel_kkt=tol, max_iters=400_000)
+                 for lp in lps]
+        res = b.run_all(slots, iters=64)
+    for lp, s in zip(lps, slots):
+        r = res[s]
+        o = O.solve(lp, O.OracleParams(algorithm=alg, eps_rel_kkt=tol, max_iters=400_000))
+        assert r.status == rh.STATUS_OPTIMAL, (lp.name, r.status_name)
+        k = O.rel_kkt(lp, O.csr_matrix(lp), r.x, r.y)
+        assert k["rel_kkt"] <= tol * 1.05, (lp.name, k)
+        assert abs(r.primal_obj - o.primal_obj) <= 20 * tol * (1 + abs(o.primal_obj))
+
+
+def test_batch_mixed_first_iterations_close_to_fp64(rh):
+    """Before any restart a mixed slot follows its FP64 twin to FP32 accuracy."""
+    lps = mix(seed0=90)
+    T = 40
+    common = dict(algorithm=1, eps_rel_kkt=1e-14, first_epoch_len=100, max_iters=T)
+    with rh.Batch(32, 512 << 20) as b:
+        s64 = [b.add(lp, precision=0, **common) for lp in lps]
+        s32 = [b.add(lp, precision=1, **common) for lp in lps]
+        res = b.run_all(s64 + s32, iters=16)
+    for lp, a, c in zip(lps, s64, s32):
+        ra, rc = res[a], res[c]
+        assert ra.iters == rc.iters == T
+        assert rel(rc.x, ra.x) < 1e-5 and rel(rc.y, ra.y) < 1e-5, (lp.name, rel(rc.x, ra.x))
+
+
+def test_batch_mixed_alone_equals_in_mix(rh):
+    target = lpgen.make_standard_planted(seed=78, m=300, n=750)
+    with rh.Batch(4, 64 << 20) as b:
+        s = b.add(target, precision=1, eps_rel_kkt=1e-7)
+        alone = b.run_all([s], iters=64)[s]
+    others = mix(seed0=45)
+    with rh.Batch(32, 512 << 20) as b:
+        first = [b.add(lp, precision=p % 2, eps_rel_kkt=1e-7) for p, lp in enumerate(others[:4])]
+        b.step(100)
+        s = b.add(target, precision=1, eps_rel_kkt=1e-7)
+        rest = [b.add(lp, precision=1, eps_rel_kkt=1e-7) for lp in others[4:]]
+        res = b.run_all(first + [s] + rest, iters=37)
+    inmix = res[s]
+    assert alone.status == inmix.status == rh.STATUS_OPTIMAL
+    assert alone.iters == inmix.iters
+    assert np.array_equal(alone.x, inmix.x) and np.array_equal(alone.y, inmix.y)
+
+
+def test_batch_mixed_certificates(rh):
+    """A mixed slot's near-certificate at a restart point moves the slot to FP64 inside the
+    launch, which then certifies at 1e-8 (verified on the host against the unscaled data)."""
+    lps = [lpgen.make_primal_infeasible(3, 500, 1000), lpgen.make_dual_infeasible_twin(3, 500, 1000)]
+    with rh.Batch(4, 256 << 20) as b:
+        slots = [b.add(lp, precision=1, max_iters=100_000, max_epoch_len=200) for lp in lps]
+        res = b.run_all(slots, iters=256)
+    K0 = O.csr_matrix(lps[0])
+    r = res[slots[0]]
+    assert r.status == rh.STATUS_PRIMAL_INFEASIBLE, r.status_name
+    by = lps[0].q @ r.cert_y
+    assert by > 0 and (K0.T @ r.cert_y).max() / by <= 1e-8
+    K1 = O.csr_matrix(lps[1])
+    r = res[slots[1]]
+    assert r.status == rh.STATUS_DUAL_INFEASIBLE, r.status_name
+    v, cd = O.dual_infeasibility_violation(lps[1], K1, r.cert_x)
+    assert cd < 0 and v <= 1e-8

@@ -676,3 +676,86 @@ def test_caller_allocator_supplies_device_memory(rh, precision):
     assert not alloc.live and torch.cuda.memory_allocated() == before
     assert (r.status, r.iters) == (ref.status, ref.iters)
     assert np.array_equal(r.x, ref.x) and np.array_equal(r.y, ref.y)
+
+
+@pytest.mark.parametrize("case,alg", [("c2_small", 0), ("c2_small", 1), ("c1", 0), ("c1", 1),
+                                      ("c3_small", 1)])
+def test_mixed_restart_decisions_fp32_vs_fp64_grade_sums(rh, case, alg):
+    """The mixed path sums the restart test's norms in FP32 (df_sums = 0, the default: lane,
+    warp, CTA and grid adds in FP32); df_sums = 1 carries double-float (FP64-grade) sums from the
+    row up.  Over a full solve to 1e-6 the traced restart iterations, iteration counts and status
+    are the same with both, and the traced residuals agree to FP32 summation accuracy.  (On the
+    small multicommodity-flow LP plain rHPDHG does not reach 1e-6 within 200k iterations in any
+    precision, FP64 included, so that case runs r2HPDHG only.)"""
+    lp = CASES[case]()
+    runs = {}
+    for dfs in (0, 1):
+        with rh.Solver(lp, algorithm=alg, precision=1, eps_rel_kkt=1e-6, df_sums=dfs,
+                       max_iters=200_000, trace=1, trace_capacity=1 << 17) as s:
+            r = s.run()
+            tr = s.trace(1 << 17)
+        assert r.status == rh.STATUS_OPTIMAL, (dfs, r.status_name)
+        runs[dfs] = (r, tr)
+    (r0, t0), (r1, t1) = runs[0], runs[1]
+    assert r0.iters == r1.iters and r0.restarts == r1.restarts
+    assert [a[0] for a in t0 if a[4]] == [a[0] for a in t1 if a[4]]
+    # the FP32 warp sums carry an absolute error of about 1e-7 of the sum of the terms'
+    # magnitudes, which the cross term's cancellation makes larger relative to a small residual
+    worst = max(abs(a[3] - b[3]) / max(abs(b[3]), 1e-300) for a, b in zip(t0, t1))
+    print(f"{case} alg={alg}: {r0.iters} iterations, {r0.restarts} restarts with both sums; "
+          f"largest relative difference of the traced residual {worst:.1e}")
+    assert worst < 1e-3
+
+
+@pytest.mark.parametrize("warps", [8, 16])
+@pytest.mark.parametrize("case", ["c2_small", "c3_small", "short_cols"])
+def test_cta_width_iterates_match_oracle(rh, case, warps):
+    """Every CTA width the autotuner may choose computes the same method: with 8- and 16-warp
+    CTAs the FP64 PDHG points after 200 iterations match the oracle's to 1e-10 and the restart
+    iterations are the oracle's."""
+    lp = CASES[case]()
+    T = 200
+    common = dict(algorithm=1, eps_rel_kkt=1e-14, first_epoch_len=20, check_every=16)
+    o = O.solve(lp, O.OracleParams(max_iters=T, **common), snapshot_iters=[T - 1], trace=True)
+    with rh.Solver(lp, max_iters=T, cta_warps=warps, trace=1, trace_capacity=256,
+                   **common) as s:
+        r = s.run()
+        xt, yt = s.state(1)
+        tr = s.trace()
+        lay = s.layout()
+    assert lay["cta_warps_row"] == warps and lay["cta_warps_col"] == warps
+    assert r.iters == T
+    stop = min(first_tie(o.trace), first_tie(tr))
+    assert [a[0] for a in tr[:stop] if a[4]] == [b[0] for b in o.trace[:stop] if b[4]]
+    if stop == len(tr):
+        sn = o.snapshots[T - 1]
+        assert rel(xt, sn["xt"]) < 1e-10 and rel(yt, sn["yt"]) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuner_choice_report_and_cache(rh, precision):
+    """The autotuner times the candidate geometries at create, reports the rule's and the chosen
+    candidate's iteration times (the choice is never slower than the rule, which is one of the
+    candidates), caches the choice by the LP's structure for the next handle of the same shape,
+    and the tuned handle solves to the same objective as the fixed rule."""
+    lp = lpgen.make_c2(1, scale=0.05)
+    with rh.Solver(lp, precision=precision, eps_rel_kkt=1e-7) as s:
+        ref = s.run()
+        rule = s.layout()
+    assert rule["tuned"] == 0
+    with rh.Solver(lp, precision=precision, eps_rel_kkt=1e-7, autotune=1) as s:
+        a = s.layout()
+        r = s.run()
+    assert a["tuned"] in (1, 2)
+    assert 0 < a["tune_ns_best"] <= a["tune_ns_rule"]
+    assert a["cta_warps_row"] in (4, 8) and a["cta_warps_col"] in (4, 8)
+    with rh.Solver(lp, precision=precision, eps_rel_kkt=1e-7, autotune=1) as s:
+        b = s.layout()
+    assert b["tuned"] == 2
+    for k in ("cta_warps_row", "cta_warps_col", "walk_row", "grid_row", "grid_col"):
+        assert a[k] == b[k], k
+    assert r.status == ref.status == rh.STATUS_OPTIMAL
+    assert abs(r.primal_obj - ref.primal_obj) <= 1e-6 * (1 + abs(ref.primal_obj))
+    print(f"precision={precision}: rule {a['tune_ns_rule'] / 1e3:.1f} us, chosen "
+          f"{a['tune_ns_best'] / 1e3:.1f} us per iteration (warps {a['cta_warps_row']}/"
+          f"{a['cta_warps_col']}, row walk {a['walk_row']})")
