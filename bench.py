@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 120M-nonzero multicommodity-flow section")
-    ap.add_argument("--serve-requests", type=int, default=200,
+    ap.add_argument("--serve-requests", type=int, default=60,
                     help="requests of the 50/s Poisson stream replayed through the serving loop "
                          "(0 = skip)")
     ap.add_argument("--serve-max-iters", type=int, default=1_000_000)
@@ -297,36 +297,41 @@ def run_serving(args, rhpdhg, lpgen):
 
 
 def run_large(args, rhpdhg, lpgen, peak, peak_kind):
-    """The 120M-nonzero multicommodity-flow LP to 1e-4, both precisions, plus one profiled
-    mixed-precision solve for the per-kernel roofline."""
+    """The 120M-nonzero multicommodity-flow LP to 1e-4 in three precisions (BF16 matrix values,
+    FP32 values, FP64), plus one profiled solve of each low-precision mode for the per-kernel
+    HBM roofline."""
     lp = lpgen.make_multicommodity_flow()
     out = {"workload": "multicommodity flow: 20 commodities on 250k nodes / 2M arcs "
                        "(7M rows, 40M columns, 120M nonzeros), arc costs U[1,100], "
                        "capacities U[5,50], planted feasible flow (seed 2)",
            "tol": 1e-4}
-    for prec, name in ((1, "fp32 iterates, fp64 restarts"), (0, "fp64")):
+    names = {2: "bf16 matrix, fp32 iterates, fp64 restarts", 1: "fp32 iterates, fp64 restarts",
+             0: "fp64"}
+    for prec in (2, 1, 0):
         t0 = time.perf_counter()
         s = rhpdhg.Solver(lp, algorithm=args.algorithm, precision=prec, eps_rel_kkt=1e-4,
                           time_limit_s=300.0)
         t1 = time.perf_counter()
         r = s.run()
         s.close()
-        out[name] = {"status": r.status_name, "iters": r.iters, "solve_s": r.solve_seconds,
-                     "create_s": t1 - t0, "iters_per_s": r.iters / r.solve_seconds,
-                     "rel_kkt": r.rel_kkt, "primal_obj": r.primal_obj}
-    s = rhpdhg.Solver(lp, algorithm=args.algorithm, precision=1, eps_rel_kkt=1e-4, profile=1)
-    s.run()
-    kt = s.kernel_times()
-    s.close()
-    ach_c = kt["bytes_col"] / (kt["ms_col"] / 1000.0) / 1e9
-    ach_r = kt["bytes_row"] / (kt["ms_row"] / 1000.0) / 1e9
-    out["roofline"] = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind,
-                       "column_kernel": {"achieved": ach_c, "frac": ach_c / peak,
-                                         "ms_per_launch": kt["ms_col"],
-                                         "bytes_per_launch": kt["bytes_col"]},
-                       "row_kernel": {"achieved": ach_r, "frac": ach_r / peak,
-                                      "ms_per_launch": kt["ms_row"],
-                                      "bytes_per_launch": kt["bytes_row"]}}
+        out[names[prec]] = {"status": r.status_name, "iters": r.iters, "solve_s": r.solve_seconds,
+                            "create_s": t1 - t0, "iters_per_s": r.iters / r.solve_seconds,
+                            "rel_kkt": r.rel_kkt, "primal_obj": r.primal_obj,
+                            "continued_in_fp64": bool(r.escalated)}
+    out["roofline"] = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind}
+    for prec in (1, 2):
+        s = rhpdhg.Solver(lp, algorithm=args.algorithm, precision=prec, eps_rel_kkt=1e-4,
+                          profile=1)
+        s.run()
+        kt = s.kernel_times()
+        s.close()
+        ach_c = kt["bytes_col"] / (kt["ms_col"] / 1000.0) / 1e9
+        ach_r = kt["bytes_row"] / (kt["ms_row"] / 1000.0) / 1e9
+        out["roofline"][names[prec]] = {
+            "column_kernel": {"achieved": ach_c, "frac": ach_c / peak,
+                              "ms_per_launch": kt["ms_col"], "bytes_per_launch": kt["bytes_col"]},
+            "row_kernel": {"achieved": ach_r, "frac": ach_r / peak,
+                           "ms_per_launch": kt["ms_row"], "bytes_per_launch": kt["bytes_row"]}}
     return out
 
 
@@ -481,6 +486,8 @@ def run_ours(args):
     rc2, fp64_tflops = rhpdhg.rhpdhg_probe_fp64_fma_rate(sh)
     if rc1 != rhpdhg.OK or rc2 != rhpdhg.OK:
         raise RuntimeError("rate probe failed: " + rhpdhg.rhpdhg_last_error(None))
+    read_gbs = {f"{b >> 20} MiB": rhpdhg.rhpdhg_probe_l2_read_bandwidth(b, sh)[1]
+                for b in (16 << 20, 64 << 20, 1 << 30)}
     # kernel timing (CUDA events around each launch of the two iteration kernels), for the
     # headline precision and the other one
     def profiled(prm):
@@ -553,6 +560,7 @@ def run_ours(args):
                      "l2_peak": l2_gbs, "l2_peak_kind": "probed read bandwidth of a 64 MiB "
                                                        "L2-resident buffer (this run)",
                      "l2_frac": achieved / l2_gbs,
+                     "read_bandwidth_by_buffer_size_gbs": read_gbs,
                      "traffic": (PROFILED_TRAFFIC.get(dom) if args.precision == 1 and
                                  kernel_digest() == PROFILED_TRAFFIC["digest"] else None),
                      "ms_per_launch_row": kt["ms_row"], "ms_per_launch_col": kt["ms_col"],

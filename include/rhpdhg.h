@@ -112,10 +112,16 @@ typedef struct {
   int32_t algorithm;            /* 0 = rHPDHG (Algorithm 1, eq. hpdhg); 1 = r2HPDHG
                                    (Algorithm 2, eq. hrpdhg).                        default 1 */
   int32_t precision;            /* 0 = FP64 throughout; 1 = FP32 matrix values and iterates with
-                                   FP64 anchors, restart norms, residuals and checks.  When a
-                                   certificate candidate at a restart point comes within 1e-3 of
-                                   eps_infeas's test, the solve continues in FP64 from that
-                                   restart point (iterations and epochs carry on). default 0 */
+                                   FP64 anchors, restarts, residuals and checks.  When a
+                                   certificate candidate comes within 1e-3 of the Farkas test at
+                                   two restart points in a row, the solve continues in FP64 from
+                                   the second (iterations and epochs carry on); 2 = as 1 with
+                                   BF16 matrix values: the scaling factors are rounded to powers
+                                   of two, so K^ = D K E is exact in BF16 when every value of K
+                                   has at most 8 significant bits (small integers such as the
+                                   +-1 of an incidence matrix); otherwise create fails with
+                                   RHPDHG_ERR_INVALID_ARG.  Precision 2 takes df_sums = 0.
+                                                                                  default 0 */
   double  eps_rel_kkt;          /* stop when max(rel_p, rel_d, rel_gap) <= eps.   default 1e-4  */
   double  eps_infeas;           /* certificate tolerance (normalised violation).  default 1e-8  */
   int64_t max_iters;            /* PDHG evaluations T(z).                         default 1e7   */
@@ -173,7 +179,9 @@ typedef struct {
                                    algorithm, row-length histograms), so handles of the same shape
                                    reuse it without timing.  Ignored when cta_warps is set.
                                                                                   default 0    */
-  int32_t reserved;
+  int32_t pow2_scaling;         /* 1 = the Ruiz and Pock-Chambolle factors of D and E rounded to
+                                   the nearest powers of two (a preconditioner that only shifts
+                                   exponents; implied by precision 2).            default 0    */
 } rhpdhg_params;
 
 /* Result of a finished solve, filled by rhpdhg_poll. */
@@ -181,7 +189,9 @@ typedef struct {
   int32_t status;               /* RHPDHG_STATUS_*                                             */
   int32_t out_memory;           /* memory kind of x, y, cert_x, cert_y below (input to poll)   */
   int32_t cert_source;          /* RHPDHG_CERT_*: candidate behind an infeasibility status     */
-  int32_t reserved;
+  int32_t escalated;            /* precision 1 or 2: 1 if the solve continued in FP64 from a
+                                   restart point (a near-certificate at two restart points in a
+                                   row), else 0                                                 */
   int64_t iters;                /* PDHG evaluations performed                                  */
   int64_t restarts;             /* outer iterations n (restarts performed)                     */
   double  rel_p, rel_d, rel_gap;/* relative KKT parts at the returned point (last check)       */

@@ -84,6 +84,8 @@ class OracleParams:
     restart_beta: float = math.exp(-1.0)
     check_every: int = 64
     adaptive_step: int = 0        # 1 = the adaptive step rule (Section 7, "as cuPDLP")
+    pow2_scaling: int = 0         # 1 = every factor of D and E rounded to the nearest power of
+    #                               two after Ruiz and Pock-Chambolle (a preconditioner variant)
     x0: Optional[np.ndarray] = None
     y0: Optional[np.ndarray] = None
 
@@ -131,6 +133,23 @@ def scale_problem(K: sp.csr_matrix, ruiz_iters: int, alpha: float):
         Kh = (sp.diags(dr) @ Kh @ sp.diags(dc)).tocsr()
         D *= dr
         E *= dc
+    return Kh, D, E
+
+
+def round_pow2(v: np.ndarray) -> np.ndarray:
+    """Each positive entry rounded to the power of two nearest to it on a log scale
+    (2^floor(log2 v + 1/2)): a scaling factor within a factor sqrt(2) of the original that only
+    shifts exponents, so K^ = D K E keeps the significant bits of K."""
+    m, e = np.frexp(v)                      # v = m 2^e with m in [0.5, 1)
+    return np.ldexp(1.0, np.where(m >= np.sqrt(0.5), e, e - 1))
+
+
+def scale_problem_pow2(K: sp.csr_matrix, ruiz_iters: int, alpha: float):
+    """scale_problem, then D and E rounded to powers of two (round_pow2) and K^ = D K E
+    recomputed from K with the rounded factors."""
+    _, D, E = scale_problem(K, ruiz_iters, alpha)
+    D, E = round_pow2(D), round_pow2(E)
+    Kh = (sp.diags(D) @ K @ sp.diags(E)).tocsr()
     return Kh, D, E
 
 
@@ -324,7 +343,8 @@ def solve(lp, params: OracleParams = OracleParams(), snapshot_iters=(),
     rho = 2.0 if params.algorithm == 1 else 1.0
     m_eq, m, n = lp.m_eq, lp.m, lp.n
     K = csr_matrix(lp)
-    Kh, D, E = scale_problem(K, params.ruiz_iters, params.pock_chambolle_alpha)
+    scale = scale_problem_pow2 if params.pow2_scaling else scale_problem
+    Kh, D, E = scale(K, params.ruiz_iters, params.pock_chambolle_alpha)
     KhT = Kh.T.tocsr()
     c = E * lp.c
     q = D * lp.q

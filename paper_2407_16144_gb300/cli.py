@@ -1,7 +1,8 @@
 """Command-line solve of a generated workload through the C ABI.
 
     python -m paper_2407_16144_gb300.cli --workload c2 --tol 1e-6 [--precision 1]
-        [--algorithm 0|1] [--max-iters N] [--scale S] [--repeat R]
+        [--algorithm 0|1] [--max-iters N] [--scale S] [--repeat R] [--autotune 1]
+        [--cta-warps 4|8|16] [--df-sums 0|1]
 
 Workloads (all from lpgen, seeded): c1 = 200 x 500 planted standard form; c2 = 100k x 250k
 general form with power-law columns (--scale shrinks it); c3 = multicommodity flow, 20
@@ -47,6 +48,9 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--profile", type=int, default=0)
     ap.add_argument("--time-limit", type=float, default=3600.0)
+    ap.add_argument("--autotune", type=int, default=0)
+    ap.add_argument("--cta-warps", type=int, default=0)
+    ap.add_argument("--df-sums", type=int, default=0)
     a = ap.parse_args(argv)
     from . import rhpdhg
     rhpdhg.load()
@@ -55,7 +59,8 @@ def main(argv=None):
         t0 = time.perf_counter()
         with rhpdhg.Solver(lp, algorithm=a.algorithm, precision=a.precision, eps_rel_kkt=a.tol,
                            max_iters=a.max_iters, max_epoch_len=a.max_epoch_len,
-                           profile=a.profile, time_limit_s=a.time_limit) as s:
+                           profile=a.profile, time_limit_s=a.time_limit,
+                           autotune=a.autotune, cta_warps=a.cta_warps, df_sums=a.df_sums) as s:
             t1 = time.perf_counter()
             r = s.run()
             kt = s.kernel_times() if a.profile else None

@@ -444,14 +444,16 @@ __device__ void batch_col_pass_mx(const BatchDesc &d, const IterConsts &ic, int 
   } else if (rp) {
     const double *dyt64 = d.rvm.dyt64;
     auto g = [&](int i) { return dyt64[i]; };
-    auto fn = [&](int j, double ktd) { col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, a, a); };
+    auto fn = [&](int j, double ktd) {
+      col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, ic.no_upper, a, a);
+    };
     rows_apply(d.n, d.cp, d.ri, d.cv, d.gc, g, fn);
   } else {
     FprSums<2, 0> f;
     const float *dyt = d.rvm.dyt;
     auto g = [&](int i) { return dyt[i]; };
     auto fn = [&](int j, float ktdyt) {
-      col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, a, a, f, tl);
+      col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, ic.no_upper, a, a, f, tl);
     };
     rows_apply(d.n, d.cp, d.ri, d.cv32, d.gc, g, fn);
     if (check) tel_flush(ctl, tl);
@@ -488,6 +490,7 @@ __device__ void batch_escalate(const BatchDesc &d, IterConsts &ic, double *sh) {
     ctl->k_next = 0;
     ctl->n_next = ctl->n;
     ctl->mv_ready = 0;
+    ctl->escalated = 1;
     d.ic->mixed = 0;
     ic.mixed = 0;
   }
@@ -733,10 +736,12 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
     if (!std::isfinite(lp->rhs[i])) return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: non-finite rhs");
   }
   rp32[m] = (int)nnz;
+  bool any_upper = false;
   for (int j = 0; j < n; ++j) {
     if (!std::isfinite(lp->c[j]) || std::isnan(lp->l[j]) || std::isnan(lp->u[j]) ||
         lp->l[j] > lp->u[j] || lp->l[j] == INFINITY || lp->u[j] == -INFINITY)
       return berr(b, RHPDHG_ERR_INVALID_ARG, "batch: invalid c or bounds");
+    any_upper = any_upper || std::isfinite(lp->u[j]);
   }
   for (int j = 0; j < n; ++j) cp[j + 2] += cp[j + 1];
   for (int i = 0; i < m; ++i)
@@ -855,6 +860,7 @@ int rhpdhg_batch_add(rhpdhg_batch *b, const rhpdhg_problem *lp, const rhpdhg_par
   ic0.trace_cap = 0;
   ic0.trace = nullptr;
   ic0.mixed = mixed ? 1 : 0;
+  ic0.no_upper = any_upper ? 0 : 1;
   // the host copies must outlive the async copies: stage through a synchronisation
   cudaMemcpyAsync(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(ic, &ic0, sizeof(ic0), cudaMemcpyHostToDevice, st);
@@ -910,6 +916,7 @@ int rhpdhg_batch_poll(rhpdhg_batch *b, int32_t slot, rhpdhg_result *r) {
   r->status = c.status;
   r->iters = c.t;
   r->restarts = c.n;
+  r->escalated = c.escalated;
   r->rel_p = c.rel_p;
   r->rel_d = c.rel_d;
   r->rel_gap = c.rel_gap;

@@ -158,13 +158,14 @@ void algorithmic_bytes(rhpdhg_handle *h) {
   const double nnz = (double)h->nnz;
   if (h->mixed) {
     // FP32 values; row kernel reads dyt, kdxt, r0, ylo (+ dy, kdx), writes dyt, kdxt (+ dy, kdx),
-    // gathers dxt; column kernel reads dxt, s0, xlo, xhi (+ dx, ktdy), writes dxt (+ dx, ktdy),
-    // gathers dyt.  (Restart iterations add the FP64 anchor products; not counted here.)
-    const double fb = 4.0;
-    h->bytes_row = nnz * (fb + ib) + (h->m + 1) * ib + h->n * fb +
+    // gathers dxt; column kernel reads dxt, s0, xlo, xhi (not when every u is +inf) (+ dx, ktdy),
+    // writes dxt (+ dx, ktdy), gathers dyt.  (Restart iterations add the FP64 anchor products;
+    // not counted here.)
+    const double fb = 4.0, vb = h->ic.bf16 ? 2.0 : 4.0;   // offsets FP32; values FP32 or BF16
+    h->bytes_row = nnz * (vb + ib) + (h->m + 1) * ib + h->n * fb +
                    h->m * fb * ((4 + 2 * rho2) + (2 + 2 * rho2));
-    h->bytes_col = nnz * (fb + ib) + (h->n + 1) * ib + h->m * fb +
-                   h->n * fb * ((4 + 2 * rho2) + (1 + 2 * rho2));
+    h->bytes_col = nnz * (vb + ib) + (h->n + 1) * ib + h->m * fb +
+                   h->n * fb * ((4 + 2 * rho2 - h->ic.no_upper) + (1 + 2 * rho2));
     return;
   }
   const double vb = 8.0;
@@ -197,7 +198,8 @@ void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
       if (wide_row < 0 &&
           h->rows.nnz_short > (long long)lr.n_short_tiles * kWarp * kStageUnroll * 4) {
         const int bw =
-            iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide, wr * kWarp, h->ic.df_sums);
+            iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide, wr * kWarp, h->ic.df_sums,
+                                  h->ic.bf16);
         const long long need = ((long long)lr.total_items() + wr - 1) / wr;
         wide = bw > 0 && need <= (long long)bw * h->sm_count;
       }
@@ -205,10 +207,10 @@ void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
     }
     h->grid_row = tile_grid(lr, h->sm_count,
                             iter_mx_blocks_per_sm(h->smem_row, true, lr.walk, wr * kWarp,
-                                                  h->ic.df_sums));
+                                                  h->ic.df_sums, h->ic.bf16));
     h->grid_col = tile_grid(lc, h->sm_count,
                             iter_mx_blocks_per_sm(h->smem_col, false, lc.walk, wc * kWarp,
-                                                  h->ic.df_sums));
+                                                  h->ic.df_sums, h->ic.bf16));
     const int br = iter_mx_restart_blocks_per_sm(h->smem_row, true, wr * kWarp);
     const int bc = iter_mx_restart_blocks_per_sm(h->smem_col, false, wc * kWarp);
     h->grid_row1 = std::max(1, std::min(h->grid_row, h->sm_count * std::max(br, 1)));
@@ -315,6 +317,7 @@ int escalate_to_fp64(rhpdhg_handle *h) {
   c.n_next = c.n;
   c.cnt_row = c.cnt_col = 0;
   c.mv_ready = 0;
+  c.escalated = 1;
   CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
   side_spmv(h->st, h->rows, h->xt, h->kxt, h->grid_row);
   launch_col(h, 1);
@@ -669,7 +672,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   if (!lp->row_ptr || !lp->c || !lp->l || !lp->u || (m > 0 && !lp->rhs) ||
       (lp->nnz > 0 && (!lp->col_idx || !lp->val)))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "missing problem array");
-  if (P.algorithm < 0 || P.algorithm > 1 || P.precision < 0 || P.precision > 1 || P.check_every < 1 ||
+  if (P.algorithm < 0 || P.algorithm > 1 || P.precision < 0 || P.precision > 2 || P.check_every < 1 ||
       P.max_iters < 1 || !(P.eps_rel_kkt > 0) || !(P.eps_infeas > 0) || P.ruiz_iters < 0 ||
       P.power_iters < 1 || P.step_size < 0 || !(P.step_safety > 0) || P.primal_weight < 0 ||
       P.first_epoch_len < 0 || P.max_epoch_len < 0 || P.restart_scheme < 0 ||
@@ -677,18 +680,20 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
       !(P.restart_beta > 0 && P.restart_beta < 1) || P.trace_capacity < 0 ||
       P.pock_chambolle_alpha > 2.0 || P.adaptive_step < 0 || P.adaptive_step > 1 ||
       (P.cta_warps != 0 && P.cta_warps != 4 && P.cta_warps != 8 && P.cta_warps != 16) ||
-      P.df_sums < 0 || P.df_sums > 1 || P.autotune < 0 || P.autotune > 1)
+      P.df_sums < 0 || P.df_sums > 1 || P.autotune < 0 || P.autotune > 1 ||
+      P.pow2_scaling < 0 || P.pow2_scaling > 1 || (P.precision == 2 && P.df_sums != 0))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "invalid parameter");
   if ((P.dev_alloc == nullptr) != (P.dev_free == nullptr))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG,
                    "invalid parameter: dev_alloc and dev_free are given together or not at all");
-  if (P.adaptive_step && P.precision == 1)
+  if (P.adaptive_step && P.precision != 0)
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG,
                    "the adaptive step rule runs with precision 0 (FP64) only");
 
   h = new rhpdhg_handle();
   h->p = P;
-  h->mixed = P.precision == 1;
+  h->mixed = P.precision >= 1;
+  h->ic.bf16 = P.precision == 2 ? 1 : 0;
   h->created_mixed = h->mixed;
   h->m = m;
   h->m_eq = lp->m_eq;
@@ -785,6 +790,8 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   unsigned int vf = validate_problem(st, m, n, h->nnz, rp64, col, val, c_in, q_in, l_in, u_in,
                                      flags);
   CKT(cudaGetLastError());
+  h->ic.no_upper = (vf & kHasFiniteUpper) ? 0 : 1;
+  vf &= ~kHasFiniteUpper;
   if (vf) {
     std::string msg = "invalid problem:";
     if (vf & 1u) msg += " malformed row_ptr;";
@@ -814,6 +821,10 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     CKT(dalloc(&tn, n));
     compute_scaling(st, m, n, rp, col, val, cp, ridx, cval, P.ruiz_iters, P.pock_chambolle_alpha,
                     h->D, h->E, tm, tn);
+    if (P.pow2_scaling || P.precision == 2) {
+      round_pow2(st, m, h->D);
+      round_pow2(st, n, h->E);
+    }
     cudaError_t e = cudaStreamSynchronize(st);
     buf_release(tm);
     buf_release(tn);
@@ -825,12 +836,20 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     std::vector<int> hrp(m + 1), hcp(n + 1);
     CKT(cudaMemcpy(hrp.data(), rp, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost));
     CKT(cudaMemcpy(hcp.data(), cp, (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
-    const bool with32 = P.precision == 1;
+    // precision 2 keeps BF16 values of K^, exact when every value of K has at most 8
+    // significant bits (the scaling factors are powers of two)
+    if (P.precision == 2 && !values_exact_in_bf16(st, h->nnz, val, flags)) {
+      free_tmp();
+      h->err = "precision 2 needs matrix values exactly representable in BF16 (at most 8 "
+               "significant bits, within the FP32 exponent range)";
+      return fail(RHPDHG_ERR_INVALID_ARG);
+    }
+    const int lowp = P.precision;
     h->ic.rho2 = P.algorithm == 1 ? 1 : 0;
     h->ic.df_sums = P.df_sums;
     if (P.autotune) h->tune_sig = shape_signature(h, hrp, hcp);
-    CKT(build_side(st, m, nnz, rp, col, val, h->D, h->E, with32, &h->rows));
-    CKT(build_side(st, n, nnz, cp, ridx, cval, h->E, h->D, with32, &h->cols));
+    CKT(build_side(st, m, nnz, rp, col, val, h->D, h->E, lowp, &h->rows));
+    CKT(build_side(st, n, nnz, cp, ridx, cval, h->E, h->D, lowp, &h->cols));
   }
   // ---- scaled vectors ----
   CKT(dalloc(&h->c, n));
@@ -1048,6 +1067,7 @@ int rhpdhg_poll(rhpdhg_handle *h, rhpdhg_result *r) {
   if (r->x) CK(cudaMemcpyAsync(r->x, h->xres, h->n * sizeof(double), kind, h->st));
   if (r->y && h->m) CK(cudaMemcpyAsync(r->y, h->yres, h->m * sizeof(double), kind, h->st));
   r->cert_source = c.cert_src;
+  r->escalated = h->escalated ? 1 : 0;
   const bool mv = c.cert_src == kCertAnchorMove;
   if (r->cert_x)
     CK(cudaMemcpyAsync(r->cert_x, mv ? h->certx2 : h->certx, h->n * sizeof(double), kind, h->st));

@@ -15,6 +15,7 @@
 //     kernel updates it, so the restart test and the termination test never leave the device.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,6 +46,9 @@ enum WalkKind : int { kWalkPlain = 0, kWalkWide = 1, kWalkGrouped = 2 };
 __host__ __device__ constexpr int walk_unroll(int walk) {
   return walk == kWalkWide ? 2 * kStageUnroll : kStageUnroll;
 }
+
+// Information bit of the problem validation: some upper bound u_j is finite.
+constexpr unsigned int kHasFiniteUpper = 0x100u;
 
 // Infeasibility certificate candidates (rhpdhg_result.cert_source).
 enum CertSource : int { kCertNone = 0, kCertRestartPoint = 1, kCertCheck = 2, kCertAnchorMove = 3 };
@@ -130,6 +134,9 @@ struct Ctl {
   double mv_cd, mv_u, mv_l, mv_dlb, mv_dub, mv_au, mv_al;
   int mv_ready;
   int cert_src;          // candidate that certified infeasibility (kCert*)
+  int near_cert;         // mixed precision: consecutive restart points whose candidate came
+                         // within 1e-3 of certifying (two move the solve to FP64)
+  int escalated;         // 1 once a mixed-precision solve continued in FP64
   // adaptive step rule: redo = 1 while iteration t is being recomputed with a smaller step
   // (the kernels then take z_t from the stored x, K^T y, y, K x); retries counts the attempts
   int redo, retries;
@@ -177,6 +184,9 @@ struct IterConsts {
   long long trace_cap;
   TraceRec *trace;
   int mixed;                  // 1 = FP32-offset iterates (certificates escalate to FP64)
+  int bf16;                   // mixed: 1 = BF16 matrix values in the ordinary kernels
+  int no_upper;               // 1 = every u_j is +inf: the mixed kernels do not read the
+                              // FP32 upper-bound offsets (all +inf)
   int df_sums;                // mixed: 1 = double-float restart-norm sums from the lane up,
                               // 0 = FP32 within each warp and FP64 above
   int adaptive;               // 1 = adaptive step rule (inadmissible steps are redone)
@@ -517,6 +527,19 @@ struct Vec4<float> {
   __device__ __forceinline__ void load(const float *p) {
     const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+};
+// BF16 values (exact images of a matrix whose entries have at most 8 significant bits, scaled by
+// powers of two), widened to FP32 as they are loaded: 8 bytes per 4 entries.
+template <>
+struct Vec4<__nv_bfloat16> {
+  float v[4];
+  __device__ __forceinline__ void load(const __nv_bfloat16 *p) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+    v[0] = __uint_as_float(t.x << 16);
+    v[1] = __uint_as_float(t.x & 0xFFFF0000u);
+    v[2] = __uint_as_float(t.y << 16);
+    v[3] = __uint_as_float(t.y & 0xFFFF0000u);
   }
 };
 template <>

@@ -17,6 +17,7 @@ struct SideStore {
   SideLayout lay;
   SideVals<double> v64;
   SideVals<float> v32;
+  SideVals<__nv_bfloat16> v16;
   WalkScratch wa, wb;
   int *ptr_s = nullptr, *tile_end = nullptr, *idx_s = nullptr, *long_rows = nullptr,
       *beg_l = nullptr, *end_l = nullptr, *idx_l = nullptr;
@@ -24,6 +25,7 @@ struct SideStore {
   int *chunk_ptr = nullptr, *chunk_row = nullptr;
   double *val64_s = nullptr, *val64_l = nullptr;
   float *val32_s = nullptr, *val32_l = nullptr;
+  __nv_bfloat16 *val16_s = nullptr, *val16_l = nullptr;
   double *part_a = nullptr, *part_b = nullptr;
   unsigned int *done_a = nullptr, *done_b = nullptr;
   double *gpart_a = nullptr, *gpart_b = nullptr;
@@ -79,7 +81,8 @@ void count_launches(long long n);
 long long launches_so_far();
 
 // ---- setup (setup.cu) ------------------------------------------------------------------------
-// Validation of a device-resident problem: returns a bit mask of problems found (0 = valid).
+// Validation of a device-resident problem: returns a bit mask of problems found (0 = valid),
+// plus the information bit kHasFiniteUpper (not an error) when some u_j is finite.
 unsigned int validate_problem(cudaStream_t st, int m, int n, long long nnz, const long long *row_ptr,
                               const int *col, const double *val, const double *c, const double *q,
                               const double *l, const double *u, unsigned int *d_flags);
@@ -96,12 +99,18 @@ void compute_scaling(cudaStream_t st, int m, int n, const int *rp, const int *co
                      int ruiz_iters, double alpha, double *D, double *E, double *tmp_m,
                      double *tmp_n);
 // Build a split-CSR side from a CSR (nrows rows) with values scaled as
-// val * rscale[row] * cscale[col] (FP64, plus an FP32 copy when with32).  Rows longer than
-// kShortMax, and the longest rows of any tile whose short segment would exceed kSegBudget,
-// go to the long CSR.  Allocates device buffers (cudaMalloc).
+// val * rscale[row] * cscale[col] (FP64, plus an FP32 copy for lowp 1 or a BF16 copy for lowp 2).
+// Rows longer than kShortMax, and the longest rows of any tile whose short segment would exceed
+// kSegBudget, go to the long CSR.  Device buffers come from buf_alloc.
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
                        const double *val, const double *rscale, const double *cscale,
-                       bool with32, SideStore *out);
+                       int lowp, SideStore *out);
+// Each entry of v (n positive factors) rounded to the nearest power of two on a log scale.
+void round_pow2(cudaStream_t st, int n, double *v);
+// True when every value has at most 8 significant bits and fits the FP32 exponent range (is
+// exact in BF16); d_flag is a device word of scratch.  Synchronises the stream.
+unsigned int values_exact_in_bf16(cudaStream_t st, long long nnz, const double *val,
+                                  unsigned int *d_flag);
 void free_side(SideStore *s);
 // Launch geometry of the tile kernels for a side with L: enough CTAs of lay.cta_warps warps for
 // one work item per warp, at most blocks_per_sm resident CTAs per SM.
@@ -163,9 +172,9 @@ void launch_unscale_mx(cudaStream_t st, int n, int m, const double *e, const dou
 void zero_f32(cudaStream_t st, int n, float *x);
 void allow_large_smem_mx(int bytes);
 // Resident CTAs per SM of the ordinary mixed kernels of one side (row: K^, else K^T) in one
-// walk instantiation (kWalk*) and one kind of restart-norm sums (IterConsts::df_sums), for
-// CTAs of `threads` threads.
-int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs);
+// walk instantiation (kWalk*), one kind of restart-norm sums (IterConsts::df_sums) and one value
+// type (lp: 0 = FP32, 1 = BF16), for CTAs of `threads` threads.
+int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs, int lp);
 // opt in to dynamic shared memory above 48 KB for the tile kernels
 void allow_large_smem(int bytes);
 void allow_large_smem_setup(int bytes);

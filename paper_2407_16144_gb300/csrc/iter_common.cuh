@@ -76,7 +76,7 @@ __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, con
       return;
     }
   }
-  const double tau = ctl->tau, omega = ctl->omega;
+  const double omega = ctl->omega;
   if (ic.adaptive) {
     // the step eta is admissible while eta <= eta_bar = ||dz||_w^2 / (2 |dy^T K dx|),
     // ||dz||_w^2 = omega ||dx||^2 + ||dy||^2 / omega; the next step is
@@ -179,12 +179,14 @@ __device__ __forceinline__ void col_finalize(Ctl *ctl, const IterConsts &ic, con
     st = farkas_status(ctl->inf_qv, r[6], r[7], vy, r[5], vx, ic.eps_infeas);
     if (st != kRunning) {
       ctl->cert_src = rp ? kCertRestartPoint : kCertCheck;
-    } else if (ic.mixed && rp &&
-               farkas_status(ctl->inf_qv, r[6], r[7], vy, r[5], vx, 1e-3) != kRunning) {
+    } else if (ic.mixed && rp) {
       // With FP32 offsets a diverging iterate carries about 1e-5 relative rounding, so this
-      // candidate cannot reach eps_infeas; once it comes within 1e-3 of certifying, the solve
-      // continues in FP64 from this restart point.
-      st = kEscalate;
+      // candidate cannot reach eps_infeas; once it comes within 1e-3 of certifying at two
+      // restart points in a row, the solve continues in FP64 from this restart point.  (One
+      // restart point alone can pass the loose test on a feasible LP, early in its solve.)
+      const bool near = farkas_status(ctl->inf_qv, r[6], r[7], vy, r[5], vx, 1e-3) != kRunning;
+      ctl->near_cert = near ? ctl->near_cert + 1 : 0;
+      if (ctl->near_cert >= 2) st = kEscalate;
     }
   }
   if (move) {

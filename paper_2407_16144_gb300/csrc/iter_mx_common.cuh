@@ -183,9 +183,11 @@ __device__ __forceinline__ void col_mx_restart(int j, double kty, const ColVecsM
 
 // First iteration of an epoch (restart point), column j, with ktd = (K^T (y~ - y0))_j in FP64
 // from the exact dyt64: the checks at the restart point, then the blend and primal step in FP32.
+// no_upper: every u is +inf, so the upper-bound offset (+inf) is not read.
 template <int RHO2, class AS, class AM>
 __device__ __forceinline__ void col_mx_first(int j, double ktd, const ColVecsMx &v, float wf,
-                                             float tauf, bool check, bool rp, AS &A, AM &M) {
+                                             float tauf, bool check, bool rp, bool no_upper,
+                                             AS &A, AM &M) {
   const double xo = v.dxt64[j];
   const double x0j = check ? v.x0[j] : 0.0;
   const double kty = check ? v.kty0[j] + ktd : 0.0;
@@ -201,7 +203,8 @@ __device__ __forceinline__ void col_mx_first(int j, double ktd, const ColVecsMx 
     dxn = wf * dxtj;
     ktn = wf * ktdyt;
   }
-  const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
+  const float hi = no_upper ? INFINITY : v.xhi[j];
+  const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), hi);
   v.dxt[j] = nt;
   const float ddx = dxn - nt;
   A.s[0] += (double)ddx * (double)ddx;
@@ -210,13 +213,15 @@ __device__ __forceinline__ void col_mx_first(int j, double ktd, const ColVecsMx 
 
 // Ordinary iteration, column j, in FP32 with ktdyt = (K^T dyt)_j: checks and active-set
 // telemetry on check iterations, then the pending blend and the primal step of eq. pdhg.
+// no_upper: every u is +inf, so the upper-bound offset (+inf) is not read.
 template <int RHO2, class AS, class AM, class F>
 __device__ __forceinline__ void col_mx_ordinary(int j, float ktdyt, const ColVecsMx &v, float wf,
-                                                float tauf, bool check, AS &A, AM &M, F &Fs,
-                                                Tel &tl) {
+                                                float tauf, bool check, bool no_upper, AS &A,
+                                                AM &M, F &Fs, Tel &tl) {
   const float dxtj = v.dxt[j];
+  const float hi = no_upper ? INFINITY : v.xhi[j];
   if (check) {
-    tel_column(j, dxtj == v.xlo[j] || dxtj == v.xhi[j], v.act, tl);
+    tel_column(j, dxtj == v.xlo[j] || dxtj == hi, v.act, tl);
     const double x0j = v.x0[j];
     col_mx_checks(j, x0j, (double)dxtj, v.kty0[j] + (double)ktdyt, (double)ktdyt, v, check,
                   false, A, M);
@@ -231,7 +236,7 @@ __device__ __forceinline__ void col_mx_ordinary(int j, float ktdyt, const ColVec
     dxn = wf * dxtj;
     ktn = wf * ktdyt;
   }
-  const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), v.xhi[j]);
+  const float nt = fminf(fmaxf(dxn + v.s0[j] + tauf * ktn, v.xlo[j]), hi);
   v.dxt[j] = nt;
   const float ddx = dxn - nt;
   Fs.add(0, ddx, ddx);

@@ -36,6 +36,11 @@ namespace rh {
 
 namespace {
 
+// Matrix values of the ordinary kernels: FP32 (LP = 0) or BF16 (LP = 1, precision 2: exact
+// values of a matrix of at most 8 significant bits under power-of-two scaling).
+template <int LP>
+using LowT = std::conditional_t<LP == 1, __nv_bfloat16, float>;
+
 // packed slots of the CTA accumulators: the restart-norm sums of the ordinary kernels
 template <int MODE>
 constexpr int row_df_slots() { return MODE == 0 ? 3 : 0; }
@@ -52,9 +57,9 @@ __host__ __device__ constexpr int mx_max_regs(int mode, int walk, int dfs) {
 // MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
 // MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
 // launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
-template <int RHO2, int MODE, int WALK, int DFS>
+template <int RHO2, int MODE, int WALK, int DFS, int LP>
 __global__ void __maxnreg__(mx_max_regs(MODE, WALK, DFS))
-k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
+k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
               const double *__restrict__ dxt64, const double *__restrict__ x0, Ctl *ctl,
               double *part, IterConsts ic) {
@@ -126,7 +131,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       prefetch_l1(v.r0 + i);
       if (i >= m_eq) prefetch_l1(v.ylo + i);
     };
-    walk_tiles<float, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
+    walk_tiles<LowT<LP>, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
                                                                        epi, gdone, pre);
     fa.flush(a);
   }
@@ -139,9 +144,9 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
 }
 
 // MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
-template <int RHO2, int MODE, int WALK, int DFS>
+template <int RHO2, int MODE, int WALK, int DFS, int LP>
 __global__ void __maxnreg__(mx_max_regs(MODE, WALK, DFS))
-k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScratch wa,
+k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
               const double *__restrict__ dyt64, const double *__restrict__ y0, Ctl *ctl,
               double *part, IterConsts ic, int phase) {
@@ -155,6 +160,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
   const double w = ctl->w, tau = ctl->tau;
   const float wf = (float)w, tauf = (float)tau;
   const bool check = phase == 0 && (((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters));
+  const bool no_upper = ic.no_upper;
   // staging: FP64 walks use (32 L + 4) doubles per warp, FP32 walks (32 L + 4) floats (the
   // FP32-only kernels are launched with half the shared memory)
   double *my64 = smem + (threadIdx.x >> 5) * lay.seg;
@@ -188,16 +194,16 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
    } else {
     // first iteration of an epoch: K^T (y~ - y0) in FP64 from the exact dyt64 of the row kernel
     auto epi = [&](int j, double ktd, bool lg) {
-      if (lg) col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, al, a);
-      else col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, a, a);
+      if (lg) col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, no_upper, al, a);
+      else col_mx_first<RHO2>(j, ktd, v, wf, tauf, check, rp, no_upper, a, a);
     };
     auto gA = [&](int i) { return dyt64[i]; };
     walk_tiles<double, double>(lay, v64, gA, my64, wb, epi, gdone);
    }
   } else {
     auto epi = [&](int j, float ktdyt, bool lg) {
-      if (lg) col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, al, a, fl, tl);
-      else col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, a, a, fa, tl);
+      if (lg) col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, no_upper, al, a, fl, tl);
+      else col_mx_ordinary<RHO2>(j, ktdyt, v, wf, tauf, check, no_upper, a, a, fa, tl);
     };
     auto gB = [&](int i) { return dyt[i]; };
     auto pre = [&](int j) {
@@ -208,9 +214,9 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<float> v32, WalkScr
       }
       prefetch_l1(v.s0 + j);
       prefetch_l1(v.xlo + j);
-      prefetch_l1(v.xhi + j);
+      if (!no_upper) prefetch_l1(v.xhi + j);
     };
-    walk_tiles<float, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
+    walk_tiles<LowT<LP>, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
                                                                        epi, gdone, pre);
     if (check) tel_flush(ctl, tl);
     fa.flush(a);
@@ -271,14 +277,16 @@ void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx 
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int grid1, int smem) {
   const int threads = side.lay.cta_warps * kWarp;
-  auto go = [&](auto kern, int g, int sm) {
-    kern<<<g, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dxt, dxt64,
-                                 x0, ctl, part, ic);
+  auto go = [&](auto kern, int g, int sm, auto vals) {
+    kern<<<g, threads, sm, st>>>(side.lay, side.v64, vals, side.wa, side.wb, v, dxt, dxt64, x0,
+                                 ctl, part, ic);
   };
   with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
-    go(k_row_iter_mx<R(), 1, kWalkGrouped, 0>, grid1, smem);
-    with_walk<true>(side.lay.walk,
-                    [&](auto W) { go(k_row_iter_mx<R(), 0, W(), D()>, grid, smem / 2); });
+    go(k_row_iter_mx<R(), 1, kWalkGrouped, 0, 0>, grid1, smem, side.v32);
+    with_walk<true>(side.lay.walk, [&](auto W) {
+      if (ic.bf16) go(k_row_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      else go(k_row_iter_mx<R(), 0, W(), D(), 0>, grid, smem / 2, side.v32);
+    });
   });
 }
 
@@ -287,14 +295,16 @@ void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx 
                         double *part, const IterConsts &ic, int grid, int grid1, int smem,
                         int phase) {
   const int threads = side.lay.cta_warps * kWarp;
-  auto go = [&](auto kern, int g, int sm) {
-    kern<<<g, threads, sm, st>>>(side.lay, side.v64, side.v32, side.wa, side.wb, v, dyt, dyt64,
-                                 y0, ctl, part, ic, phase);
+  auto go = [&](auto kern, int g, int sm, auto vals) {
+    kern<<<g, threads, sm, st>>>(side.lay, side.v64, vals, side.wa, side.wb, v, dyt, dyt64, y0,
+                                 ctl, part, ic, phase);
   };
   with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
-    go(k_col_iter_mx<R(), 1, kWalkGrouped, 0>, grid1, smem);
-    with_walk<false>(side.lay.walk,
-                     [&](auto W) { go(k_col_iter_mx<R(), 0, W(), D()>, grid, smem / 2); });
+    go(k_col_iter_mx<R(), 1, kWalkGrouped, 0, 0>, grid1, smem, side.v32);
+    with_walk<false>(side.lay.walk, [&](auto W) {
+      if (ic.bf16) go(k_col_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      else go(k_col_iter_mx<R(), 0, W(), D(), 0>, grid, smem / 2, side.v32);
+    });
   });
 }
 
@@ -317,11 +327,17 @@ void allow_large_smem_mx(int bytes) {
   for (int rho2 = 0; rho2 < 2; ++rho2)
     for (int dfs = 0; dfs < 2; ++dfs)
       with_rho_dfs(rho2, dfs, [&](auto R, auto D) {
-        set((const void *)k_row_iter_mx<R(), 1, kWalkGrouped, 0>);
-        set((const void *)k_col_iter_mx<R(), 1, kWalkGrouped, 0>);
+        set((const void *)k_row_iter_mx<R(), 1, kWalkGrouped, 0, 0>);
+        set((const void *)k_col_iter_mx<R(), 1, kWalkGrouped, 0, 0>);
         for (int w : {kWalkPlain, kWalkWide, kWalkGrouped}) {
-          with_walk<true>(w, [&](auto W) { set((const void *)k_row_iter_mx<R(), 0, W(), D()>); });
-          with_walk<false>(w, [&](auto W) { set((const void *)k_col_iter_mx<R(), 0, W(), D()>); });
+          with_walk<true>(w, [&](auto W) {
+            set((const void *)k_row_iter_mx<R(), 0, W(), D(), 0>);
+            set((const void *)k_row_iter_mx<R(), 0, W(), 0, 1>);
+          });
+          with_walk<false>(w, [&](auto W) {
+            set((const void *)k_col_iter_mx<R(), 0, W(), D(), 0>);
+            set((const void *)k_col_iter_mx<R(), 0, W(), 0, 1>);
+          });
         }
       });
 }
@@ -334,18 +350,18 @@ int iter_mx_restart_blocks_per_sm(int smem, bool row, int threads) {
     mn = b < mn ? b : mn;
   };
   if (row) {
-    occ((const void *)k_row_iter_mx<0, 1, kWalkGrouped, 0>);
-    occ((const void *)k_row_iter_mx<1, 1, kWalkGrouped, 0>);
+    occ((const void *)k_row_iter_mx<0, 1, kWalkGrouped, 0, 0>);
+    occ((const void *)k_row_iter_mx<1, 1, kWalkGrouped, 0, 0>);
   } else {
-    occ((const void *)k_col_iter_mx<0, 1, kWalkGrouped, 0>);
-    occ((const void *)k_col_iter_mx<1, 1, kWalkGrouped, 0>);
+    occ((const void *)k_col_iter_mx<0, 1, kWalkGrouped, 0, 0>);
+    occ((const void *)k_col_iter_mx<1, 1, kWalkGrouped, 0, 0>);
   }
   return mn;
 }
 
-int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs) {
-  // the ordinary kernels of one side in one walk instantiation and one kind of restart-norm
-  // sums (both reflection settings)
+int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs, int lp) {
+  // the ordinary kernels of one side in one walk instantiation, one kind of restart-norm sums
+  // and one value type (both reflection settings)
   int mn = 1 << 30;
   auto occ = [&](const void *f) {
     int b = 0;
@@ -353,10 +369,18 @@ int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs) {
     mn = b < mn ? b : mn;
   };
   for (int rho2 = 0; rho2 < 2; ++rho2)
-      with_rho_dfs(rho2, dfs, [&](auto R, auto D) {
-        if (row) with_walk<true>(walk, [&](auto W) { occ((const void *)k_row_iter_mx<R(), 0, W(), D()>); });
-        else with_walk<false>(walk, [&](auto W) { occ((const void *)k_col_iter_mx<R(), 0, W(), D()>); });
-      });
+    with_rho_dfs(rho2, dfs, [&](auto R, auto D) {
+      if (row)
+        with_walk<true>(walk, [&](auto W) {
+          occ(lp ? (const void *)k_row_iter_mx<R(), 0, W(), 0, 1>
+                 : (const void *)k_row_iter_mx<R(), 0, W(), D(), 0>);
+        });
+      else
+        with_walk<false>(walk, [&](auto W) {
+          occ(lp ? (const void *)k_col_iter_mx<R(), 0, W(), 0, 1>
+                 : (const void *)k_col_iter_mx<R(), 0, W(), D(), 0>);
+        });
+    });
   return mn;
 }
 

@@ -131,7 +131,7 @@ void worker_loop(rhpdhg_server *s) {
         const int64_t nnz = r.row_ptr.back();
         rhpdhg_problem p = r.problem();
         bool admitted = false;
-        if (nnz <= s->small_nnz && !r.params.adaptive_step) {
+        if (nnz <= s->small_nnz && !r.params.adaptive_step && r.params.precision != 2) {
           int32_t slot = -1;
           const int rc = rhpdhg_batch_add(s->batch, &p, &r.params, &slot);
           if (rc == RHPDHG_OK) {

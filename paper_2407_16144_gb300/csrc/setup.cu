@@ -57,6 +57,7 @@ __global__ void k_validate_cols(int n, const double *c, const double *l, const d
   double lj = l[j], uj = u[j];
   if (isnan(lj) || isnan(uj) || lj > uj) f |= 16u;
   if (lj == INFINITY || uj == -INFINITY) f |= 32u;
+  if (isfinite(uj)) f |= kHasFiniteUpper;
   if (f) atomicOr(flags, f);
 }
 
@@ -126,12 +127,14 @@ __global__ void k_scale_update(int n, const double *stat, double *scale) {
   if (s > 0.0) scale[i] = scale[i] / sqrt(s);
 }
 
-// copy each row's entries, scaled, to its place in the short or long arrays (warp per row)
-template <bool W32>
+// copy each row's entries, scaled, to its place in the short or long arrays (warp per row),
+// with an FP32 (LOWP 1) or BF16 (LOWP 2) copy of the scaled values
+template <int LOWP>
 __global__ void k_copy_rows(int nrows, const int *ptr, const int *idx, const double *val,
                             const double *rs, const double *cs, const int *dst,
                             const uint32_t *long_mask, int *idx_s, double *val_s, float *val32_s,
-                            int *idx_l, double *val_l, float *val32_l) {
+                            __nv_bfloat16 *val16_s, int *idx_l, double *val_l, float *val32_l,
+                            __nv_bfloat16 *val16_l) {
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= nrows) return;
@@ -140,6 +143,7 @@ __global__ void k_copy_rows(int nrows, const int *ptr, const int *idx, const dou
   int *ix = lg ? idx_l : idx_s;
   double *vx = lg ? val_l : val_s;
   float *vf = lg ? val32_l : val32_s;
+  __nv_bfloat16 *vh = lg ? val16_l : val16_s;
   const int b = ptr[r], e = ptr[r + 1], o = dst[r];
   const double sr = rs[r];
   for (int p = b + lane; p < e; p += 32) {
@@ -147,7 +151,29 @@ __global__ void k_copy_rows(int nrows, const int *ptr, const int *idx, const dou
     const double v = sr * val[p] * cs[j];
     ix[o + (p - b)] = j;
     vx[o + (p - b)] = v;
-    if (W32) vf[o + (p - b)] = (float)v;
+    if (LOWP == 1) vf[o + (p - b)] = (float)v;
+    if (LOWP == 2) vh[o + (p - b)] = __float2bfloat16_rn((float)v);
+  }
+}
+
+// each factor rounded to the power of two nearest to it on a log scale
+__global__ void k_round_pow2(int n, double *v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int e = 0;
+  const double f = frexp(v[i], &e);           // v = f 2^e, f in [0.5, 1)
+  v[i] = ldexp(1.0, f >= 0.70710678118654752440 ? e : e - 1);
+}
+
+// flag = 1 if some value has more than 8 significant bits (not exact in BF16) or lies outside
+// the FP32 exponent range
+__global__ void k_check_bf16(long long nnz, const double *val, unsigned int *flag) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nnz;
+       p += (long long)gridDim.x * blockDim.x) {
+    const double v = val[p];
+    const float f = (float)v;
+    const float h = __bfloat162float(__float2bfloat16_rn(f));
+    if ((double)h != v) atomicOr(flag, 1u);
   }
 }
 
@@ -563,7 +589,7 @@ bool plan_side(const int *hp, int nrows, SidePlan *p) {
 
 cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, const int *idx,
                        const double *val, const double *rscale, const double *cscale,
-                       bool with32, SideStore *out) {
+                       int lowp, SideStore *out) {
   (void)nnz;
   SideStore s;
   cudaError_t err = cudaSuccess;
@@ -622,22 +648,27 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   TRY(cudaMemsetAsync(s.val64_s, 0, nnz_s * sizeof(double), st));
   TRY(cudaMemsetAsync(s.idx_l, 0, nnz_l * sizeof(int), st));
   TRY(cudaMemsetAsync(s.val64_l, 0, nnz_l * sizeof(double), st));
-  if (with32) {
+  if (lowp == 1) {
     TRY(buf_alloc((void **)&s.val32_s, nnz_s * sizeof(float)));
     TRY(buf_alloc((void **)&s.val32_l, nnz_l * sizeof(float)));
     TRY(cudaMemsetAsync(s.val32_s, 0, nnz_s * sizeof(float), st));
     TRY(cudaMemsetAsync(s.val32_l, 0, nnz_l * sizeof(float), st));
+  } else if (lowp == 2) {
+    TRY(buf_alloc((void **)&s.val16_s, nnz_s * sizeof(__nv_bfloat16)));
+    TRY(buf_alloc((void **)&s.val16_l, nnz_l * sizeof(__nv_bfloat16)));
+    TRY(cudaMemsetAsync(s.val16_s, 0, nnz_s * sizeof(__nv_bfloat16), st));
+    TRY(cudaMemsetAsync(s.val16_l, 0, nnz_l * sizeof(__nv_bfloat16), st));
   }
   if (nrows > 0) {
     const int nb = nblocks((long long)nrows * 32, 256);
-    if (with32)
-      k_copy_rows<true><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rscale, cscale, d_dst,
-                                            s.long_mask, s.idx_s, s.val64_s, s.val32_s, s.idx_l,
-                                            s.val64_l, s.val32_l);
-    else
-      k_copy_rows<false><<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rscale, cscale, d_dst,
-                                             s.long_mask, s.idx_s, s.val64_s, s.val32_s, s.idx_l,
-                                             s.val64_l, s.val32_l);
+    auto copy = [&](auto kern) {
+      kern<<<nb, 256, 0, st>>>(nrows, ptr, idx, val, rscale, cscale, d_dst, s.long_mask,
+                               s.idx_s, s.val64_s, s.val32_s, s.val16_s, s.idx_l, s.val64_l,
+                               s.val32_l, s.val16_l);
+    };
+    if (lowp == 1) copy(k_copy_rows<1>);
+    else if (lowp == 2) copy(k_copy_rows<2>);
+    else copy(k_copy_rows<0>);
     count_launches(1);
   }
   // ---- walk scratch ------------------------------------------------------------------------
@@ -667,6 +698,8 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   s.v64.l = s.val64_l;
   s.v32.s = s.val32_s;
   s.v32.l = s.val32_l;
+  s.v16.s = s.val16_s;
+  s.v16.l = s.val16_l;
   s.wa.chunk_part = s.part_a;
   s.wa.group_done = s.done_a;
   s.wa.group_part = s.gpart_a;
@@ -682,10 +715,30 @@ fail:
   return err;
 }
 
+void round_pow2(cudaStream_t st, int n, double *v) {
+  if (n <= 0) return;
+  k_round_pow2<<<nblocks(n, 256), 256, 0, st>>>(n, v);
+  count_launches(1);
+}
+
+unsigned int values_exact_in_bf16(cudaStream_t st, long long nnz, const double *val,
+                                  unsigned int *d_flag) {
+  cudaMemsetAsync(d_flag, 0, sizeof(unsigned int), st);
+  if (nnz > 0) {
+    k_check_bf16<<<std::min<long long>(nblocks(nnz, 256), 4096), 256, 0, st>>>(nnz, val, d_flag);
+    count_launches(1);
+  }
+  unsigned int h = 0;
+  cudaMemcpyAsync(&h, d_flag, sizeof(h), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return h == 0;
+}
+
 void free_side(SideStore *s) {
   void *bufs[] = {s->ptr_s, s->tile_end, s->idx_s, s->long_mask, s->long_rows, s->beg_l,
                   s->end_l, s->idx_l,
                   s->chunk_ptr, s->chunk_row, s->val64_s, s->val64_l, s->val32_s, s->val32_l,
+                  s->val16_s, s->val16_l,
                   s->part_a, s->part_b, s->done_a, s->done_b, s->gpart_a, s->gpart_b};
   for (void *b : bufs) buf_release(b);
   *s = SideStore();

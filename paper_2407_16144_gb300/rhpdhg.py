@@ -58,12 +58,12 @@ class rhpdhg_params(C.Structure):
                 ("trace_capacity", C.c_int64), ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("adaptive_step", C.c_int32), ("cta_warps", C.c_int32),
                 ("df_sums", C.c_int32), ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("autotune", C.c_int32), ("reserved", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("autotune", C.c_int32), ("pow2_scaling", C.c_int32)]
 
 
 class rhpdhg_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("out_memory", C.c_int32), ("cert_source", C.c_int32),
-                ("reserved", C.c_int32), ("iters", C.c_int64),
+                ("escalated", C.c_int32), ("iters", C.c_int64),
                 ("restarts", C.c_int64), ("rel_p", C.c_double), ("rel_d", C.c_double),
                 ("rel_gap", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("solve_seconds", C.c_double), ("eta", C.c_double), ("omega", C.c_double),
@@ -394,7 +394,7 @@ class Server:
             return None
         _check(rc, None, "rhpdhg_server_poll")
         self._shape.pop(ticket)
-        res = Result(status=r.status, cert_source=r.cert_source,
+        res = Result(status=r.status, cert_source=r.cert_source, escalated=r.escalated,
                      iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
                      rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
                      dual_obj=r.dual_obj, solve_seconds=r.solve_seconds, eta=r.eta,
@@ -485,7 +485,7 @@ class Batch:
         if rc == BUSY:
             return None
         _check(rc, None, "rhpdhg_batch_poll")
-        res = Result(status=r.status, cert_source=r.cert_source,
+        res = Result(status=r.status, cert_source=r.cert_source, escalated=r.escalated,
                      iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
                      rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
                      dual_obj=r.dual_obj, solve_seconds=0.0, eta=r.eta, omega=r.omega,
@@ -638,6 +638,7 @@ class Result:
     cert_x: np.ndarray
     cert_y: np.ndarray
     cert_source: int = 0     # CERT_* of an infeasibility status
+    escalated: int = 0       # 1 if a mixed-precision solve continued in FP64
 
     @property
     def status_name(self) -> str:
@@ -718,7 +719,7 @@ class Solver:
         if rc == BUSY:
             return None
         _check(rc, self.h, "rhpdhg_poll")
-        return Result(status=r.status, cert_source=r.cert_source,
+        return Result(status=r.status, cert_source=r.cert_source, escalated=r.escalated,
                       iters=r.iters, restarts=r.restarts, rel_p=r.rel_p,
                       rel_d=r.rel_d, rel_gap=r.rel_gap, primal_obj=r.primal_obj,
                       dual_obj=r.dual_obj, solve_seconds=r.solve_seconds, eta=r.eta,

@@ -5,8 +5,9 @@ the FP64 oracle and its independent rel-KKT checker (oracle.rel_kkt on the unsca
     FP64 with the objective within 1e-8 relative of the oracle's own full solve (stored in
     tests/golden/oracle_solves.json by tests/golden/make_oracle_solves.py, which calls only the
     oracle), and in mixed precision with the checker's rel-KKT at 1e-8; to 1e-4 in both.
-  * Multicommodity flow (20 commodities, 250k nodes, 2M arcs, 120M nonzeros): to 1e-6 in both
-    precisions, checked by the checker, objectives agreeing to the tolerance's duality gap.
+  * Multicommodity flow (20 commodities, 250k nodes, 2M arcs, 120M nonzeros): to 1e-6 in FP64,
+    in mixed precision and with BF16 matrix values, checked by the checker, objectives agreeing
+    to the tolerance's duality gap.
   * 50k x 100k primal-infeasible LP: certified at 1e-8 under the two-phase restart schedule of
     the remark after Theorem infeas, with the iteration count reported beside the adaptive rule's.
 
@@ -83,7 +84,7 @@ def test_multicommodity_flow_full_size_to_1e6(rh):
     lp = lpgen.make_multicommodity_flow()
     K = O.csr_matrix(lp)
     res = {}
-    for prec in (1, 0):
+    for prec in (2, 1, 0):
         with rh.Solver(lp, algorithm=1, precision=prec, eps_rel_kkt=1e-6,
                        time_limit_s=600.0) as s:
             r = s.run()
@@ -93,6 +94,7 @@ def test_multicommodity_flow_full_size_to_1e6(rh):
               f"checker rel-KKT {k['rel_kkt']:.2e}, objective {r.primal_obj:.10e}")
         assert k["rel_kkt"] <= 1.05e-6, (prec, k)
         assert r.x.min() >= 0.0
+        assert r.escalated == 0        # a feasible LP stays in its precision
         res[prec] = r
     a, b = res[1].primal_obj, res[0].primal_obj
     print(f"C3 objectives: |mixed - fp64| / (1 + |mixed| + |fp64|) = "

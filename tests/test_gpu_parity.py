@@ -449,6 +449,7 @@ def test_mixed_precision_certificates(rh, alg):
             r2 = s.run()
         assert (r2.status, r2.iters, r2.restarts) == (r.status, r.iters, r.restarts)
         assert np.array_equal(r2.cert_x, r.cert_x) and np.array_equal(r2.cert_y, r.cert_y)
+        assert r.escalated == r2.escalated == 1      # the certificate comes from FP64
         _check_certificate(rh, lp, r, kind)
         print(f"mixed {name} alg={alg}: detected at {r.iters} iterations")
 
@@ -759,3 +760,52 @@ def test_autotuner_choice_report_and_cache(rh, precision):
     print(f"precision={precision}: rule {a['tune_ns_rule'] / 1e3:.1f} us, chosen "
           f"{a['tune_ns_best'] / 1e3:.1f} us per iteration (warps {a['cta_warps_row']}/"
           f"{a['cta_warps_col']}, row walk {a['walk_row']})")
+
+
+# ---------------------------------------------------------------------------------------------
+# BF16 matrix values (precision 2): power-of-two scaling keeps K^ exact in BF16 when K has at
+# most 8 significant bits per value
+
+def test_pow2_scaling_fp64_matches_oracle(rh):
+    """The power-of-two scaling option in FP64: the same D and E as the oracle's rounding and
+    the same PDHG points over 200 iterations (to 1e-10)."""
+    lp = CASES["c3_small"]()
+    Kh, Do, Eo = O.scale_problem_pow2(O.csr_matrix(lp), 10, 1.0)
+    T = 200
+    common = dict(algorithm=1, eps_rel_kkt=1e-14, first_epoch_len=20, check_every=16,
+                  pow2_scaling=1)
+    o = O.solve(lp, O.OracleParams(max_iters=T, **common), snapshot_iters=[T - 1])
+    with rh.Solver(lp, max_iters=T, **common) as s:
+        D, E, eta, om0, smax = s.scaling()
+        r = s.run()
+        xt, yt = s.state(1)
+    assert np.array_equal(D, Do) and np.array_equal(E, Eo)
+    sn = o.snapshots[T - 1]
+    assert r.iters == T and rel(xt, sn["xt"]) < 1e-10 and rel(yt, sn["yt"]) < 1e-10
+
+
+@pytest.mark.parametrize("alg", [0, 1])
+def test_bf16_values_equal_fp32_values_under_pow2_scaling(rh, alg):
+    """On an LP of +-1 coefficients the BF16 values of precision 2 are exactly the FP32 values
+    of precision 1 with power-of-two scaling, so the two runs are bit-identical: same trace,
+    iterations, restarts and point."""
+    lp = CASES["c3_small"]()
+    common = dict(algorithm=alg, eps_rel_kkt=1e-6, max_iters=30_000, trace=1,
+                  trace_capacity=1 << 15)
+    with rh.Solver(lp, precision=2, **common) as s:
+        a = s.run()
+        ta = s.trace(1 << 15)
+    with rh.Solver(lp, precision=1, pow2_scaling=1, **common) as s:
+        b = s.run()
+        tb = s.trace(1 << 15)
+    assert (a.status, a.iters, a.restarts) == (b.status, b.iters, b.restarts)
+    assert ta == tb
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.y, b.y)
+
+
+def test_bf16_rejects_values_that_are_not_exact(rh):
+    lp = CASES["c2_small"]()           # lognormal values: more than 8 significant bits
+    with pytest.raises(rh.RHPDHGError, match="BF16"):
+        rh.Solver(lp, precision=2)
+    with pytest.raises(rh.RHPDHGError, match="parameter"):
+        rh.Solver(CASES["c3_small"](), precision=2, df_sums=1)

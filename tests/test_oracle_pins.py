@@ -543,3 +543,26 @@ def test_primal_weight_covariance_catches_a_wrong_update(monkeypatch):
         monkeypatch.setattr(O, "primal_weight_update", fn)
         same, om, fp, it, nr = _covariance_gaps(lp, 2.0, 1.0)
         assert not (same and om < 1e-6 and it < 1e-6), name
+
+
+def test_power_of_two_scaling_keeps_the_significant_bits():
+    """round_pow2 gives powers of two within a factor sqrt(2) of the unrounded scaling, and with
+    them every entry of K^ = D K E of a matrix of small integers has exactly the significant bits
+    of the integer (it is the integer times a power of two), which is what makes such a K^ exact
+    in a short floating-point format."""
+    lp = lpgen.make_multicommodity_flow(2, 300, 2000, 3)
+    K = O.csr_matrix(lp)
+    _, D0, E0 = O.scale_problem(K, 10, 1.0)
+    Kh, D, E = O.scale_problem_pow2(K, 10, 1.0)
+    for v, v0 in ((D, D0), (E, E0)):
+        mant, _ = np.frexp(v)
+        assert np.all(mant == 0.5)                         # powers of two
+        assert np.all(v / v0 <= np.sqrt(2) * (1 + 1e-15)) and np.all(v0 / v <= np.sqrt(2) * (1 + 1e-15))
+    assert np.allclose(Kh.toarray(), D[:, None] * K.toarray() * E[None, :], rtol=0, atol=0)
+    mant, _ = np.frexp(np.abs(Kh.data))
+    assert np.all(mant == 0.5)                             # +-1 entries stay +-2^k
+    # the rounded scaling is still a valid preconditioner: the oracle solves with it
+    r = O.solve(lp, O.OracleParams(algorithm=1, eps_rel_kkt=1e-6, pow2_scaling=1,
+                                   max_iters=200_000))
+    assert r.status == O.OPTIMAL
+    assert O.rel_kkt(lp, K, r.x, r.y)["rel_kkt"] <= 1e-6 * 1.0001
