@@ -377,7 +377,7 @@ void candidate_grids(rhpdhg_handle *h, int *max_row, int *max_col) {
 // count, and the histograms (log2 buckets) of the row lengths of K and of K^T.
 std::string shape_signature(const rhpdhg_handle *h, const std::vector<int> &rp,
                             const std::vector<int> &cp) {
-  std::string sig = std::to_string(h->mixed) + "/" + std::to_string(h->ic.rho2) + "/" +
+  std::string sig = std::to_string(h->mixed + h->ic.bf16) + "/" + std::to_string(h->ic.rho2) + "/" +
                     std::to_string(h->ic.df_sums) + "/" + std::to_string(h->m_eq) + "/" +
                     std::to_string(h->m_ineq) + "/" + std::to_string(h->n) + "/" +
                     std::to_string(h->nnz) + "/" + std::to_string(h->sm_count);
@@ -894,9 +894,11 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   {
     double *v = nullptr, *w = nullptr, *um = nullptr, *pp = nullptr, *ss = nullptr;
     unsigned int *tk = nullptr;
-    const bool f32 = false;              // FP64 values (the FP32 copy measured no faster)
-    const int gr = side_spmv_pw_grid(h->rows, f32, h->sm_count);
-    const int gc = side_spmv_pw_grid(h->cols, f32, h->sm_count);
+    // FP64 handles in FP64; mixed-precision handles in their own value precision with FP32
+    // products and row sums (the step keeps its 10% margin: eta sigma_max = 0.9 (1 + O(1e-6)))
+    const int lowp = P.precision;
+    const int gr = side_spmv_pw_grid(h->rows, lowp, h->sm_count);
+    const int gc = side_spmv_pw_grid(h->cols, lowp, h->sm_count);
     const int gmax = std::max(gr, gc);
     CKT(dalloc(&v, n));
     CKT(dalloc(&w, n));
@@ -908,12 +910,12 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     fill(st, n, 1.0 / std::sqrt((double)n), v);
     const double *scale = nullptr;       // v is already normalised
     for (int it = 0; it < P.power_iters; ++it) {
-      side_spmv_pw(st, h->rows, f32, v, scale, um, pp, tk, ss + 2, gr);
-      side_spmv_pw(st, h->cols, f32, um, nullptr, w, pp, tk, ss + 4, gc);
+      side_spmv_pw(st, h->rows, lowp, v, scale, um, pp, tk, ss + 2, gr);
+      side_spmv_pw(st, h->cols, lowp, um, nullptr, w, pp, tk, ss + 4, gc);
       std::swap(v, w);
       scale = ss + 5;                    // 1 / ||K^T K^ v||
     }
-    side_spmv_pw(st, h->rows, f32, v, scale, um, pp, tk, ss + 6, gr);
+    side_spmv_pw(st, h->rows, lowp, v, scale, um, pp, tk, ss + 6, gr);
     double s2 = 0;
     CKT(cudaMemcpyAsync(&s2, ss + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
     CKT(cudaStreamSynchronize(st));
@@ -1014,6 +1016,13 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   h->cvm = ColVecsMx{h->dxt, h->dx, h->ktdy, h->s0, h->xlo, h->xhi, h->x0, h->kty0, h->xout,
                      h->certx, h->dxt64, h->c, h->l, h->u, h->E, h->Einv, h->certx2, h->act};
   algorithmic_bytes(h);
+  {
+    // the ordinary mixed kernels read the matrix stream evict-first where one iteration's
+    // bytes exceed L2 (see Vec4 in common.cuh)
+    int l2 = 0;
+    CKC(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->dev));
+    h->ic.l2_first = h->mixed && h->bytes_row + h->bytes_col > (double)l2 ? 1 : 0;
+  }
   h->launches = launches_so_far() - launches0;
   CKC(cudaStreamSynchronize(st));
   CKC(cudaGetLastError());

@@ -188,8 +188,10 @@ struct IterConsts {
   int no_upper;               // 1 = every u_j is +inf: the mixed kernels do not read the
                               // FP32 upper-bound offsets (all +inf)
   int df_sums;                // mixed: 1 = double-float restart-norm sums from the lane up,
-                              // 0 = FP32 within each warp and FP64 above
+                              // 0 = FP32 sums at every level
   int adaptive;               // 1 = adaptive step rule (inadmissible steps are redone)
+  int l2_first;               // mixed: 1 = the ordinary kernels read the matrix stream with the
+                              // L2 evict-first policy (one iteration's bytes exceed L2)
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -519,14 +521,33 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 // VT is the value type, PT the product/accumulator type; src(j) returns the gathered vector
 // entry; smem is this warp's staging area of 32 * L + 4 PTs.
 
+// Cache policy of the matrix stream (template parameter CP of the walk).  CP = 1 reads the
+// entries with an L2 evict-first policy: where one iteration's bytes exceed L2 they stream through
+// once per product, and the policy leaves L2 to the gathered vectors and the reduction partials.
+// Where the problem fits L2 the plain loads (CP = 0) are kept: there the evict-first lines were
+// measured to cost re-reads.  The policy is created next to each load from an immediate, which
+// the compiler keeps a constant (a policy selected at run time measured slower).
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 template <typename VT>
 struct Vec4;
 template <>
 struct Vec4<float> {
   float v[4];
+  template <int CP = 0>
   __device__ __forceinline__ void load(const float *p) {
-    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    if constexpr (CP == 1) {
+      asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+          : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+          : "l"(p), "l"(l2_evict_first()));
+    } else {
+      const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
   }
 };
 // BF16 values (exact images of a matrix whose entries have at most 8 significant bits, scaled by
@@ -534,8 +555,16 @@ struct Vec4<float> {
 template <>
 struct Vec4<__nv_bfloat16> {
   float v[4];
+  template <int CP = 0>
   __device__ __forceinline__ void load(const __nv_bfloat16 *p) {
-    const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+    uint2 t;
+    if constexpr (CP == 1) {
+      asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+          : "=r"(t.x), "=r"(t.y)
+          : "l"(p), "l"(l2_evict_first()));
+    } else {
+      t = __ldg(reinterpret_cast<const uint2 *>(p));
+    }
     v[0] = __uint_as_float(t.x << 16);
     v[1] = __uint_as_float(t.x & 0xFFFF0000u);
     v[2] = __uint_as_float(t.y << 16);
@@ -545,6 +574,7 @@ struct Vec4<__nv_bfloat16> {
 template <>
 struct Vec4<double> {
   double v[4];
+  template <int CP = 0>
   __device__ __forceinline__ void load(const double *p) {
     const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
     const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
@@ -552,13 +582,20 @@ struct Vec4<double> {
   }
 };
 
+template <int CP = 0>
 __device__ __forceinline__ void load_idx4(const int *p, int *j) {
-  const int4 t = __ldg(reinterpret_cast<const int4 *>(p));
-  j[0] = t.x; j[1] = t.y; j[2] = t.z; j[3] = t.w;
+  if constexpr (CP == 1) {
+    asm("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(j[0]), "=r"(j[1]), "=r"(j[2]), "=r"(j[3])
+        : "l"(p), "l"(l2_evict_first()));
+  } else {
+    const int4 t = __ldg(reinterpret_cast<const int4 *>(p));
+    j[0] = t.x; j[1] = t.y; j[2] = t.z; j[3] = t.w;
+  }
 }
 
 // One long-row chunk (work item `item` < lay.n_chunks) of walk_tiles, by the whole warp.
-template <typename VT, typename PT, typename Src, typename Epi, typename GroupDone>
+template <typename VT, typename PT, int CP, typename Src, typename Epi, typename GroupDone>
 __device__ __forceinline__ void walk_chunk(const SideLayout &lay, const SideVals<VT> vals,
                                            const Src &src, const WalkScratch ws, Epi &epi,
                                            GroupDone &gdone, int item) {
@@ -574,10 +611,10 @@ __device__ __forceinline__ void walk_chunk(const SideLayout &lay, const SideVals
   if (p0 < ce) {
     int j[8];
     Vec4<VT> va, vb;
-    load_idx4(lay.idx_l + p0, j);
-    load_idx4(lay.idx_l + p0 + 4, j + 4);
-    va.load(vals.l + p0);
-    vb.load(vals.l + p0 + 4);
+    load_idx4<CP>(lay.idx_l + p0, j);
+    load_idx4<CP>(lay.idx_l + p0 + 4, j + 4);
+    va.template load<CP>(vals.l + p0);
+    vb.template load<CP>(vals.l + p0 + 4);
     PT x[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) x[u] = (p0 + u < ce) ? PT(src(j[u])) : PT(0);
@@ -652,7 +689,7 @@ struct NoPrefetch {
 // Stage the products of the segment [seg_b, seg_e) (seg_b 4-aligned) in smem[0, ...): lane
 // handles 4-entry groups g = lane, lane + 32, ..., U at a time (more loads in flight per round,
 // more registers).
-template <typename VT, typename PT, int U, typename Src>
+template <typename VT, typename PT, int U, int CP, typename Src>
 __device__ __forceinline__ void stage_segment(const SideLayout &lay, const SideVals<VT> vals,
                                               const Src &src, PT *smem, int seg_b, int seg_e) {
   const int lane = threadIdx.x & 31;
@@ -665,8 +702,8 @@ __device__ __forceinline__ void stage_segment(const SideLayout &lay, const SideV
     for (int u = 0; u < kU; ++u) {
       const int g = g0 + u * kWarp + lane;
       if (g < nvec) {
-        load_idx4(lay.idx_s + seg_b + 4 * g, j[u]);
-        vv[u].load(vals.s + seg_b + 4 * g);
+        load_idx4<CP>(lay.idx_s + seg_b + 4 * g, j[u]);
+        vv[u].template load<CP>(vals.s + seg_b + 4 * g);
       }
     }
     PT x[kU][4];
@@ -690,7 +727,7 @@ __device__ __forceinline__ void stage_segment(const SideLayout &lay, const SideV
 
 // One short tile st of walk_tiles (tile_mult == 1): stage its segment, then lane r sums row r
 // and runs its epilogue.
-template <typename VT, typename PT, int U, typename Src, typename Epi, typename Pre>
+template <typename VT, typename PT, int U, int CP, typename Src, typename Epi, typename Pre>
 __device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<VT> vals,
                                           const Src &src, PT *smem, Epi &epi, const Pre &pre,
                                           int st) {
@@ -703,7 +740,7 @@ __device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<
   const int seg_b = __shfl_sync(0xffffffffu, rb, 0);     // 4-aligned
   int re = __shfl_down_sync(0xffffffffu, rb, 1);
   if (lane >= nr - 1) re = seg_e;
-  stage_segment<VT, PT, U>(lay, vals, src, smem, seg_b, seg_e);
+  stage_segment<VT, PT, U, CP>(lay, vals, src, smem, seg_b, seg_e);
   __syncwarp();
   tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lay.long_mask[st], epi);
   __syncwarp();
@@ -713,8 +750,8 @@ __device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<
 // registers); GROUPED = true walks any layout.
 // pre(row) is called by the lane of each short-tile row before the tile's entries are staged,
 // so that what the row's epilogue will read can be requested while the staging round trips run.
-template <typename VT, typename PT, bool GROUPED = true, int U = kStageUnroll, typename Src,
-          typename Epi, typename GroupDone, typename Pre = NoPrefetch>
+template <typename VT, typename PT, bool GROUPED = true, int U = kStageUnroll, int CP = 0,
+          typename Src, typename Epi, typename GroupDone, typename Pre = NoPrefetch>
 __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals<VT> vals,
                                            const Src &src, PT *smem, const WalkScratch ws,
                                            Epi &epi, GroupDone &gdone,
@@ -725,9 +762,9 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
   const int total = lay.total_items();
   for (int item = gwarp; item < total; item += nwarps) {
     if (item < lay.n_chunks) {
-      walk_chunk<VT, PT>(lay, vals, src, ws, epi, gdone, item);
+      walk_chunk<VT, PT, CP>(lay, vals, src, ws, epi, gdone, item);
     } else if constexpr (!GROUPED) {
-      walk_tile<VT, PT, U>(lay, vals, src, smem, epi, pre, item - lay.n_chunks);
+      walk_tile<VT, PT, U, CP>(lay, vals, src, smem, epi, pre, item - lay.n_chunks);
     } else {
       // a group of nt <= tile_mult consecutive short tiles, staged as one segment
       const int t0 = (item - lay.n_chunks) * lay.tile_mult;
@@ -748,7 +785,7 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
       const int rb0 = lay.ptr_s[t0 * kTileRows + min(lane, lay.nrows - 1 - t0 * kTileRows)];
       const int seg_b = __shfl_sync(0xffffffffu, rb0, 0);     // 4-aligned
       const int seg_e = __shfl_sync(0xffffffffu, te, nt - 1);
-      stage_segment<VT, PT, U>(lay, vals, src, smem, seg_b, seg_e);
+      stage_segment<VT, PT, U, CP>(lay, vals, src, smem, seg_b, seg_e);
       __syncwarp();
 #pragma unroll 1
       for (int m = 0; m < nt; ++m) {

@@ -118,13 +118,13 @@ int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm);
 // out = side * src   (plain product, FP64)
 void side_spmv(cudaStream_t st, const SideStore &side, const double *src, double *out, int grid);
 // Power-iteration product: out = side * (src * in_scale[0]) and ss = (||out||^2, 1/||out||);
-// fp32 selects the FP32 values (mixed precision);
+// lowp 0: FP64 values, products and sums; 1 / 2: the side's FP32 / BF16 values with FP32 products
+// and row sums (mixed-precision handles); the norm is an FP64 sum in every case.
 // part holds grid * kMaxPartials doubles, ticket a zeroed counter.
-// fp32: use the side's FP32 values (products and sums in FP64; mixed-precision handles).
-void side_spmv_pw(cudaStream_t st, const SideStore &side, bool fp32, const double *src,
+void side_spmv_pw(cudaStream_t st, const SideStore &side, int lowp, const double *src,
                   const double *in_scale, double *out, double *part, unsigned int *ticket,
                   double *ss, int grid);
-int side_spmv_pw_grid(const SideStore &side, bool fp32, int sm_count);
+int side_spmv_pw_grid(const SideStore &side, int lowp, int sm_count);
 // deterministic sum of squares -> *out (device scalar); tmp holds >= 1024 doubles
 void sumsq(cudaStream_t st, int n, const double *x, double *out, double *tmp);
 // v = w / sqrt(*ss)

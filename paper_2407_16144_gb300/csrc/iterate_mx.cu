@@ -57,7 +57,8 @@ __host__ __device__ constexpr int mx_max_regs(int mode, int walk, int dfs) {
 // MODE 0 runs the ordinary (FP32) iterations and returns at once when a restart is pending;
 // MODE 1 runs only the restart iterations (FP64 walks) and returns at once otherwise.  Both are
 // launched every iteration; splitting them keeps the register footprint of the FP32 kernel small.
-template <int RHO2, int MODE, int WALK, int DFS, int LP>
+// CP: the matrix stream's cache policy of the ordinary kernels' walk (see Vec4 in common.cuh).
+template <int RHO2, int MODE, int WALK, int DFS, int LP, int CP = 0>
 __global__ void __maxnreg__(mx_max_regs(MODE, WALK, DFS))
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
@@ -131,7 +132,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, Walk
       prefetch_l1(v.r0 + i);
       if (i >= m_eq) prefetch_l1(v.ylo + i);
     };
-    walk_tiles<LowT<LP>, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
+    walk_tiles<LowT<LP>, float, WALK == kWalkGrouped, walk_unroll(WALK), CP>(lay, v32, gB, my32, wb,
                                                                        epi, gdone, pre);
     fa.flush(a);
   }
@@ -144,7 +145,7 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, Walk
 }
 
 // MODE 0: ordinary iterations (no pending restart, not a restart point); MODE 1: the rest.
-template <int RHO2, int MODE, int WALK, int DFS, int LP>
+template <int RHO2, int MODE, int WALK, int DFS, int LP, int CP = 0>
 __global__ void __maxnreg__(mx_max_regs(MODE, WALK, DFS))
 k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, WalkScratch wa,
               WalkScratch wb, ColVecsMx v, const float *__restrict__ dyt,
@@ -216,7 +217,7 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, Walk
       prefetch_l1(v.xlo + j);
       if (!no_upper) prefetch_l1(v.xhi + j);
     };
-    walk_tiles<LowT<LP>, float, WALK == kWalkGrouped, walk_unroll(WALK)>(lay, v32, gB, my32, wb,
+    walk_tiles<LowT<LP>, float, WALK == kWalkGrouped, walk_unroll(WALK), CP>(lay, v32, gB, my32, wb,
                                                                        epi, gdone, pre);
     if (check) tel_flush(ctl, tl);
     fa.flush(a);
@@ -284,7 +285,11 @@ void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx 
   with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
     go(k_row_iter_mx<R(), 1, kWalkGrouped, 0, 0>, grid1, smem, side.v32);
     with_walk<true>(side.lay.walk, [&](auto W) {
-      if (ic.bf16) go(k_row_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      // evict-first matrix stream only with the FP32 restart-norm sums (the default)
+      const bool cp = ic.l2_first && ic.df_sums == 0;
+      if (ic.bf16 && cp) go(k_row_iter_mx<R(), 0, W(), 0, 1, 1>, grid, smem / 2, side.v16);
+      else if (ic.bf16) go(k_row_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      else if (cp) go(k_row_iter_mx<R(), 0, W(), 0, 0, 1>, grid, smem / 2, side.v32);
       else go(k_row_iter_mx<R(), 0, W(), D(), 0>, grid, smem / 2, side.v32);
     });
   });
@@ -302,7 +307,10 @@ void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx 
   with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
     go(k_col_iter_mx<R(), 1, kWalkGrouped, 0, 0>, grid1, smem, side.v32);
     with_walk<false>(side.lay.walk, [&](auto W) {
-      if (ic.bf16) go(k_col_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      const bool cp = ic.l2_first && ic.df_sums == 0;
+      if (ic.bf16 && cp) go(k_col_iter_mx<R(), 0, W(), 0, 1, 1>, grid, smem / 2, side.v16);
+      else if (ic.bf16) go(k_col_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      else if (cp) go(k_col_iter_mx<R(), 0, W(), 0, 0, 1>, grid, smem / 2, side.v32);
       else go(k_col_iter_mx<R(), 0, W(), D(), 0>, grid, smem / 2, side.v32);
     });
   });
@@ -333,10 +341,14 @@ void allow_large_smem_mx(int bytes) {
           with_walk<true>(w, [&](auto W) {
             set((const void *)k_row_iter_mx<R(), 0, W(), D(), 0>);
             set((const void *)k_row_iter_mx<R(), 0, W(), 0, 1>);
+            set((const void *)k_row_iter_mx<R(), 0, W(), 0, 0, 1>);
+            set((const void *)k_row_iter_mx<R(), 0, W(), 0, 1, 1>);
           });
           with_walk<false>(w, [&](auto W) {
             set((const void *)k_col_iter_mx<R(), 0, W(), D(), 0>);
             set((const void *)k_col_iter_mx<R(), 0, W(), 0, 1>);
+            set((const void *)k_col_iter_mx<R(), 0, W(), 0, 0, 1>);
+            set((const void *)k_col_iter_mx<R(), 0, W(), 0, 1, 1>);
           });
         }
       });
@@ -370,15 +382,20 @@ int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs, in
   };
   for (int rho2 = 0; rho2 < 2; ++rho2)
     with_rho_dfs(rho2, dfs, [&](auto R, auto D) {
+      // both cache-policy instantiations (the choice is made after the geometry)
       if (row)
         with_walk<true>(walk, [&](auto W) {
           occ(lp ? (const void *)k_row_iter_mx<R(), 0, W(), 0, 1>
                  : (const void *)k_row_iter_mx<R(), 0, W(), D(), 0>);
+          occ(lp ? (const void *)k_row_iter_mx<R(), 0, W(), 0, 1, 1>
+                 : (const void *)k_row_iter_mx<R(), 0, W(), 0, 0, 1>);
         });
       else
         with_walk<false>(walk, [&](auto W) {
           occ(lp ? (const void *)k_col_iter_mx<R(), 0, W(), 0, 1>
                  : (const void *)k_col_iter_mx<R(), 0, W(), D(), 0>);
+          occ(lp ? (const void *)k_col_iter_mx<R(), 0, W(), 0, 1, 1>
+                 : (const void *)k_col_iter_mx<R(), 0, W(), 0, 0, 1>);
         });
     });
   return mn;

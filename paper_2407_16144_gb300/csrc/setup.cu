@@ -236,26 +236,32 @@ k_side_spmv(SideLayout lay, SideVals<double> vals, WalkScratch ws,
 // One product of the power iteration on K^T K^: out = side * (src * in_scale[0]) (in_scale NULL:
 // 1), plus ss[0] = ||out||^2 and ss[1] = 1 / ||out|| (0 for a zero vector) from the grid's
 // deterministic ticket reduction.  The next product reads ss + 1 as its input scale, so the
-// normalisation v = w / ||w|| costs no launch of its own.
-template <typename VT>
+// normalisation v = w / ||w|| costs no launch of its own.  PT is the product and row-sum type:
+// FP64 with the FP64 values; FP32 with the FP32 or BF16 values of a mixed-precision handle, where
+// the input scale is applied to each row's sum (in FP64) instead of to every gathered entry and
+// the norm is still an FP64 sum.
+template <typename VT, typename PT>
 __global__ void __launch_bounds__(kBlockThreads)
 k_side_spmv_pw(SideLayout lay, SideVals<VT> vals, WalkScratch ws,
                const double *__restrict__ src, const double *in_scale, double *out, double *part,
                unsigned int *ticket, double *ss) {
   extern __shared__ double smem[];
-  double *my = smem + (threadIdx.x >> 5) * lay.seg;
+  PT *my = reinterpret_cast<PT *>(smem) + (threadIdx.x >> 5) * lay.seg;
+  constexpr bool kF64 = sizeof(PT) == sizeof(double);
   const double sc = in_scale ? *in_scale : 1.0;
+  const double post = kF64 ? 1.0 : sc;
   Acc<1, 0> a, al;
   a.zero();
   al.zero();
-  auto epi = [&](int row, double dot, bool lg) {
-    out[row] = dot;
-    if (lg) al.s[0] += dot * dot;
-    else a.s[0] += dot * dot;
+  auto epi = [&](int row, PT dot, bool lg) {
+    const double o = (double)dot * post;
+    out[row] = o;
+    if (lg) al.s[0] += o * o;
+    else a.s[0] += o * o;
   };
-  auto gather = [&](int j) { return src[j] * sc; };
+  auto gather = [&](int j) { return kF64 ? PT(src[j] * sc) : PT(src[j]); };
   auto gdone = [&](int grp) { store_group(al, 0x1u, ws.group_part, grp); };
-  walk_tiles<VT, double>(lay, vals, gather, my, ws, epi, gdone);
+  walk_tiles<VT, PT>(lay, vals, gather, my, ws, epi, gdone);
   if (cta_reduce_and_ticket(a, 0x1u, 0u, 0u, part, ticket)) {
     double r[1];
     grid_finish<1, 0>(part, r, 0x1u, 0u, ws.group_part, lay.n_long_tiles);
@@ -754,31 +760,47 @@ int tile_grid(const SideLayout &lay, int sm_count, int blocks_per_sm) {
 
 void allow_large_smem_setup(int bytes) {
   cudaFuncSetAttribute(k_side_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_side_spmv_pw<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k_side_spmv_pw<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_side_spmv_pw<double, double>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_side_spmv_pw<float, float>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_side_spmv_pw<__nv_bfloat16, float>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-void side_spmv_pw(cudaStream_t st, const SideStore &side, bool fp32, const double *src,
+static int pw_smem(const SideStore &side, int lowp) {
+  return kBlockWarps * side.lay.seg * (lowp ? (int)sizeof(float) : (int)sizeof(double));
+}
+
+void side_spmv_pw(cudaStream_t st, const SideStore &side, int lowp, const double *src,
                   const double *in_scale, double *out, double *part, unsigned int *ticket,
                   double *ss, int grid) {
-  int smem = kBlockWarps * side.lay.seg * (int)sizeof(double);
-  if (fp32)
-    k_side_spmv_pw<float><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v32, side.wa, src,
-                                                             in_scale, out, part, ticket, ss);
+  const int smem = pw_smem(side, lowp);
+  if (lowp == 2)
+    k_side_spmv_pw<__nv_bfloat16, float><<<grid, kBlockThreads, smem, st>>>(
+        side.lay, side.v16, side.wa, src, in_scale, out, part, ticket, ss);
+  else if (lowp == 1)
+    k_side_spmv_pw<float, float><<<grid, kBlockThreads, smem, st>>>(
+        side.lay, side.v32, side.wa, src, in_scale, out, part, ticket, ss);
   else
-    k_side_spmv_pw<double><<<grid, kBlockThreads, smem, st>>>(side.lay, side.v64, side.wa, src,
-                                                              in_scale, out, part, ticket, ss);
+    k_side_spmv_pw<double, double><<<grid, kBlockThreads, smem, st>>>(
+        side.lay, side.v64, side.wa, src, in_scale, out, part, ticket, ss);
   count_launches(1);
 }
 
 // grid of the power-iteration product on `side`: whole resident waves, at most the work items
-int side_spmv_pw_grid(const SideStore &side, bool fp32, int sm_count) {
-  int smem = kBlockWarps * side.lay.seg * (int)sizeof(double);
+int side_spmv_pw_grid(const SideStore &side, int lowp, int sm_count) {
+  const int smem = pw_smem(side, lowp);
   int b = 0;
-  if (fp32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_side_spmv_pw<float>, kBlockThreads, smem);
+  if (lowp == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_side_spmv_pw<__nv_bfloat16, float>,
+                                                  kBlockThreads, smem);
+  else if (lowp == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_side_spmv_pw<float, float>,
+                                                  kBlockThreads, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_side_spmv_pw<double>, kBlockThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_side_spmv_pw<double, double>,
+                                                  kBlockThreads, smem);
   return tile_grid(side.lay, sm_count, b);
 }
 

@@ -700,11 +700,13 @@ def test_mixed_restart_decisions_fp32_vs_fp64_grade_sums(rh, case, alg):
     (r0, t0), (r1, t1) = runs[0], runs[1]
     assert r0.iters == r1.iters and r0.restarts == r1.restarts
     assert [a[0] for a in t0 if a[4]] == [a[0] for a in t1 if a[4]]
-    # the FP32 warp sums carry an absolute error of about 1e-7 of the sum of the terms'
-    # magnitudes, which the cross term's cancellation makes larger relative to a small residual
-    worst = max(abs(a[3] - b[3]) / max(abs(b[3]), 1e-300) for a, b in zip(t0, t1))
+    # the FP32 sums carry an absolute error of about 1e-7 of the sum of the terms' magnitudes,
+    # which the cross term's cancellation makes larger relative to a small residual: the
+    # difference is bounded relative to the residual plus 1e-6 of the largest traced residual
+    big = max(abs(b[3]) for b in t1)
+    worst = max(abs(a[3] - b[3]) / (abs(b[3]) + 1e-6 * big) for a, b in zip(t0, t1))
     print(f"{case} alg={alg}: {r0.iters} iterations, {r0.restarts} restarts with both sums; "
-          f"largest relative difference of the traced residual {worst:.1e}")
+          f"largest difference of the traced residual {worst:.1e} (relative, floored)")
     assert worst < 1e-3
 
 
