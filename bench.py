@@ -299,7 +299,8 @@ def run_serving(args, rhpdhg, lpgen):
 def run_large(args, rhpdhg, lpgen, peak, peak_kind):
     """The 120M-nonzero multicommodity-flow LP to 1e-4 in three precisions (BF16 matrix values,
     FP32 values, FP64), plus one profiled solve of each low-precision mode for the per-kernel
-    HBM roofline."""
+    HBM roofline.  Every handle is created with the autotuner on (its launch-shape choice is
+    reported; the profiled handles reuse it from the tuner's cache)."""
     lp = lpgen.make_multicommodity_flow()
     out = {"workload": "multicommodity flow: 20 commodities on 250k nodes / 2M arcs "
                        "(7M rows, 40M columns, 120M nonzeros), arc costs U[1,100], "
@@ -310,18 +311,20 @@ def run_large(args, rhpdhg, lpgen, peak, peak_kind):
     for prec in (2, 1, 0):
         t0 = time.perf_counter()
         s = rhpdhg.Solver(lp, algorithm=args.algorithm, precision=prec, eps_rel_kkt=1e-4,
-                          time_limit_s=300.0)
+                          time_limit_s=300.0, autotune=1)
         t1 = time.perf_counter()
         r = s.run()
+        lay = s.layout()
         s.close()
         out[names[prec]] = {"status": r.status_name, "iters": r.iters, "solve_s": r.solve_seconds,
                             "create_s": t1 - t0, "iters_per_s": r.iters / r.solve_seconds,
                             "rel_kkt": r.rel_kkt, "primal_obj": r.primal_obj,
-                            "continued_in_fp64": bool(r.escalated)}
+                            "continued_in_fp64": bool(r.escalated),
+                            "autotune": {k: lay.get(k) for k in TUNE_KEYS}}
     out["roofline"] = {"bound": "hbm", "unit": "GB/s", "peak": peak, "peak_kind": peak_kind}
     for prec in (1, 2):
         s = rhpdhg.Solver(lp, algorithm=args.algorithm, precision=prec, eps_rel_kkt=1e-4,
-                          profile=1)
+                          profile=1, autotune=1)
         s.run()
         kt = s.kernel_times()
         s.close()

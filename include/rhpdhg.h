@@ -285,10 +285,11 @@ int rhpdhg_get_trace(const rhpdhg_handle *h, rhpdhg_trace_rec *recs, int64_t cap
  * FP64 handles); warps per CTA of the row kernels and of the column kernels; the autotuner's
  * outcome (0 = the fixed rule, 1 = timed at create, 2 = taken from the cache), and the time of
  * one iteration (row plus column stage, median, nanoseconds) with the rule's geometry and with
- * the chosen one (0 when not tuned).
+ * the chosen one (0 when not tuned); whether the FP64 walks of K^ and of K^T sum a tile's longest
+ * rows warp-wide (1) or every row in one lane (0), decided at create from the row lengths.
  * capacity: entries available at out.  Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG for a NULL
  * handle or out, or capacity < RHPDHG_LAYOUT_FIELDS. */
-#define RHPDHG_LAYOUT_FIELDS 17
+#define RHPDHG_LAYOUT_FIELDS 19
 int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity);
 
 /* Handles take their device buffers from a process-wide cache of buffers freed by earlier
@@ -302,10 +303,13 @@ int64_t rhpdhg_release_cached_memory(void);
  * with nrows rows and row pointers row_ptr (host memory, nrows + 1 entries, row_ptr[0] = 0); no
  * device is used.  out receives RHPDHG_PLAN_FIELDS values: 32-row tiles; short tiles per work
  * item (1, 2 or 4); long rows; long-row chunks; staging stride (entries per warp); padded
- * short-array entries; padded long-array entries.  capacity: entries available at out.
+ * short-array entries; padded long-array entries; 1 if the FP64 walks sum each tile's longest
+ * rows warp-wide (when that saves at least 15% of the FP64 adds of the row sums by the tile cost
+ * model: lane-per-row sums cost the longest short row rounded up to 4, a threshold c of 8, 16 or
+ * 32 costs c plus ceil(len / 32) + 5 per longer row), else 0.  capacity: entries available at out.
  * Returns RHPDHG_OK, or RHPDHG_ERR_INVALID_ARG for a NULL pointer, nrows < 0, row pointers that
  * do not start at 0 or decrease, offsets beyond int32, or capacity < RHPDHG_PLAN_FIELDS. */
-#define RHPDHG_PLAN_FIELDS 7
+#define RHPDHG_PLAN_FIELDS 8
 int rhpdhg_plan_layout(const int64_t *row_ptr, int32_t nrows, int64_t *out, int32_t capacity);
 
 /* With params.profile = 1: average device time (ms) per launch of the row-side kernel

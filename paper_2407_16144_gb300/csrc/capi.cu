@@ -1135,7 +1135,8 @@ int rhpdhg_get_layout(const rhpdhg_handle *h, int64_t *out, int32_t capacity) {
                                            r.seg,        c.seg,        r.walk,      c.walk,
                                            r.cta_warps,  c.cta_warps,  h->tuned,
                                            (int64_t)std::llround(1e3 * h->tune_us_rule),
-                                           (int64_t)std::llround(1e3 * h->tune_us_best)};
+                                           (int64_t)std::llround(1e3 * h->tune_us_best),
+                                           r.wide_rows,  c.wide_rows};
   for (int i = 0; i < RHPDHG_LAYOUT_FIELDS; ++i) out[i] = v[i];
   return RHPDHG_OK;
 }
@@ -1159,7 +1160,8 @@ int rhpdhg_plan_layout(const int64_t *row_ptr, int32_t nrows, int64_t *out, int3
                                          (int64_t)P.chunk_row.size(),
                                          ((P.maxseg + 3) & ~3LL) + 4,
                                          P.nnz_s,
-                                         P.nnz_l};
+                                         P.nnz_l,
+                                         P.wide_rows};
   for (int i = 0; i < RHPDHG_PLAN_FIELDS; ++i) out[i] = v[i];
   return RHPDHG_OK;
 }

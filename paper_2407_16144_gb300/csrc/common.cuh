@@ -85,6 +85,7 @@ struct SideLayout {
   int tile_mult = 1;         // consecutive short tiles per work item (1 .. kMaxTileMult)
   int walk = 0;              // instantiation of the ordinary mixed kernels' walk (kWalk*)
   int cta_warps = kBlockWarps;  // warps per CTA of this side's iteration kernels (host only)
+  int wide_rows = 0;         // FP64 walks sum a tile's longest rows warp-wide (tile_rows_fp64)
   int n_tile_groups = 0;     // ceil(n_short_tiles / tile_mult)
   __host__ __device__ int total_items() const { return n_chunks + n_tile_groups; }
 };
@@ -525,7 +526,7 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 // entries with an L2 evict-first policy: where one iteration's bytes exceed L2 they stream through
 // once per product, and the policy leaves L2 to the gathered vectors and the reduction partials.
 // Where the problem fits L2 the plain loads (CP = 0) are kept: there the evict-first lines were
-// measured to cost re-reads.  The policy is created next to each load from an immediate, which
+// measured to cost re-reads; BF16 values keep them too (the hinted 8-byte loads measured slower).  The policy is created next to each load from an immediate, which
 // the compiler keeps a constant (a policy selected at run time measured slower).
 __device__ __forceinline__ unsigned long long l2_evict_first() {
   unsigned long long p;
@@ -557,14 +558,8 @@ struct Vec4<__nv_bfloat16> {
   float v[4];
   template <int CP = 0>
   __device__ __forceinline__ void load(const __nv_bfloat16 *p) {
-    uint2 t;
-    if constexpr (CP == 1) {
-      asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
-          : "=r"(t.x), "=r"(t.y)
-          : "l"(p), "l"(l2_evict_first()));
-    } else {
-      t = __ldg(reinterpret_cast<const uint2 *>(p));
-    }
+    static_assert(CP == 0, "BF16 values are read with plain loads");
+    const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
     v[0] = __uint_as_float(t.x << 16);
     v[1] = __uint_as_float(t.x & 0xFFFF0000u);
     v[2] = __uint_as_float(t.y << 16);
@@ -652,14 +647,40 @@ __device__ __forceinline__ void walk_chunk(const SideLayout &lay, const SideVals
   }
 }
 
-// Lane r of a short tile sums row r's staged products smem[rb - seg_b, re - seg_b) with four
-// interleaved accumulators and runs its epilogue (rows marked long in lm are skipped).
-template <typename PT, typename Epi>
-__device__ __forceinline__ void tile_rows(const PT *smem, int row0, int nr, int rb, int re,
-                                          int seg_b, uint32_t lm, Epi &epi) {
+// FP64 tiles: the FP64 pipe is narrow, and lane-per-row sums issue as many FP64 adds per warp as
+// the tile's longest row has entries, with the other lanes masked.  Rows longer than a threshold
+// T are therefore summed by the whole warp (lane-strided partial sums and a shuffle tree, about
+// len/32 + 5 adds per row), the rest lane per row as in tile_rows.  T is the candidate among 8,
+// 16, 32 and the longest row that minimises the warp's FP64 adds, 4 ceil(T / 4) + the sum over
+// rows longer than T of (ceil(len / 32) + 5) (one warp reduction per candidate); a tile whose rows
+// have at most 16 entries keeps T = its longest row.  Rows at or below T are summed exactly as
+// tile_rows sums them.  Used only on sides where the same cost model, evaluated over all tiles at
+// set-up, saves FP64 adds (SideLayout::wide_rows); elsewhere tile_rows keeps lane-per-row sums.
+template <typename Epi>
+__device__ __forceinline__ void tile_rows_fp64(const double *smem, int row0, int nr, int rb,
+                                               int re, int seg_b, uint32_t lm, Epi &epi) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  if (lane < nr && !((lm >> lane) & 1u)) {
-    PT s0 = PT(0), s1 = PT(0), s2 = PT(0), s3 = PT(0);
+  const bool act = lane < nr && !((lm >> lane) & 1u);
+  const int len = act ? re - rb : 0;           // at most kShortMax
+  const int mx = (int)__reduce_max_sync(full, (unsigned)len);
+  int T = mx;
+  if (mx > 16) {
+    int best = (mx + 3) & ~3;
+    const int wadds = ((len + 31) >> 5) + 5;   // this row's adds when summed by the warp
+#pragma unroll
+    for (int c = 8; c <= 32; c *= 2) {
+      if (c >= mx) break;
+      const int cost = c + (int)__reduce_add_sync(full, len > c ? (unsigned)wadds : 0u);
+      if (cost < best) {
+        best = cost;
+        T = c;
+      }
+    }
+  }
+  double dot = 0.0;
+  if (act && len <= T) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int p = rb - seg_b;
     const int pe = re - seg_b;
     for (; p + 4 <= pe; p += 4) {
@@ -671,7 +692,53 @@ __device__ __forceinline__ void tile_rows(const PT *smem, int row0, int nr, int 
     if (p < pe) s0 += smem[p];
     if (p + 1 < pe) s1 += smem[p + 1];
     if (p + 2 < pe) s2 += smem[p + 2];
+    // the lane's epilogue loads go out while the warp sums the long rows
     epi(row0 + lane, (s0 + s1) + (s2 + s3), false);
+  }
+  unsigned big = __ballot_sync(full, act && len > T);
+  while (big) {
+    const int r = __ffs(big) - 1;
+    big &= big - 1;
+    const int b = __shfl_sync(full, rb, r) - seg_b, e = __shfl_sync(full, re, r) - seg_b;
+    double s = 0.0;
+    for (int p = b + lane; p < e; p += 32) s += smem[p];
+    s = warp_sum(s);
+    if (lane == r) dot = s;
+  }
+  if (act && len > T) epi(row0 + lane, dot, false);
+}
+
+// Lane r of a short tile sums row r's staged products smem[rb - seg_b, re - seg_b) with four
+// interleaved accumulators and runs its epilogue (rows marked long in lm are skipped).  FP64
+// tiles go to tile_rows_fp64.
+template <typename PT, typename Epi>
+__device__ __forceinline__ void tile_rows(const PT *smem, int row0, int nr, int rb, int re,
+                                          int seg_b, uint32_t lm, bool wide, Epi &epi) {
+  // (without the warp-wide sums each lane goes on to its epilogue as soon as its row is summed,
+  // so its loads overlap the other lanes' sums)
+  if constexpr (sizeof(PT) == sizeof(double)) {
+    if (wide) {
+      tile_rows_fp64(smem, row0, nr, rb, re, seg_b, lm, epi);
+      return;
+    }
+  }
+  {
+    const int lane = threadIdx.x & 31;
+    if (lane < nr && !((lm >> lane) & 1u)) {
+      PT s0 = PT(0), s1 = PT(0), s2 = PT(0), s3 = PT(0);
+      int p = rb - seg_b;
+      const int pe = re - seg_b;
+      for (; p + 4 <= pe; p += 4) {
+        s0 += smem[p];
+        s1 += smem[p + 1];
+        s2 += smem[p + 2];
+        s3 += smem[p + 3];
+      }
+      if (p < pe) s0 += smem[p];
+      if (p + 1 < pe) s1 += smem[p + 1];
+      if (p + 2 < pe) s2 += smem[p + 2];
+      epi(row0 + lane, (s0 + s1) + (s2 + s3), false);
+    }
   }
 }
 
@@ -742,7 +809,7 @@ __device__ __forceinline__ void walk_tile(const SideLayout &lay, const SideVals<
   if (lane >= nr - 1) re = seg_e;
   stage_segment<VT, PT, U, CP>(lay, vals, src, smem, seg_b, seg_e);
   __syncwarp();
-  tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lay.long_mask[st], epi);
+  tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lay.long_mask[st], lay.wide_rows != 0, epi);
   __syncwarp();
 }
 
@@ -796,7 +863,7 @@ __device__ __forceinline__ void walk_tiles(const SideLayout &lay, const SideVals
         const uint32_t lm_m = __shfl_sync(0xffffffffu, lmk, m);
         int re = __shfl_down_sync(0xffffffffu, rb, 1);
         if (lane >= nr - 1) re = te_m;
-        tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lm_m, epi);
+        tile_rows<PT>(smem, row0, nr, rb, re, seg_b, lm_m, lay.wide_rows != 0, epi);
       }
       __syncwarp();
     }

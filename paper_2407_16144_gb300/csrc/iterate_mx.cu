@@ -285,10 +285,10 @@ void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx 
   with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
     go(k_row_iter_mx<R(), 1, kWalkGrouped, 0, 0>, grid1, smem, side.v32);
     with_walk<true>(side.lay.walk, [&](auto W) {
-      // evict-first matrix stream only with the FP32 restart-norm sums (the default)
+      // evict-first matrix stream only for FP32 values with FP32 restart-norm sums (the
+      // default); with BF16 values it measured slower
       const bool cp = ic.l2_first && ic.df_sums == 0;
-      if (ic.bf16 && cp) go(k_row_iter_mx<R(), 0, W(), 0, 1, 1>, grid, smem / 2, side.v16);
-      else if (ic.bf16) go(k_row_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      if (ic.bf16) go(k_row_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
       else if (cp) go(k_row_iter_mx<R(), 0, W(), 0, 0, 1>, grid, smem / 2, side.v32);
       else go(k_row_iter_mx<R(), 0, W(), D(), 0>, grid, smem / 2, side.v32);
     });
@@ -308,8 +308,7 @@ void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx 
     go(k_col_iter_mx<R(), 1, kWalkGrouped, 0, 0>, grid1, smem, side.v32);
     with_walk<false>(side.lay.walk, [&](auto W) {
       const bool cp = ic.l2_first && ic.df_sums == 0;
-      if (ic.bf16 && cp) go(k_col_iter_mx<R(), 0, W(), 0, 1, 1>, grid, smem / 2, side.v16);
-      else if (ic.bf16) go(k_col_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
+      if (ic.bf16) go(k_col_iter_mx<R(), 0, W(), 0, 1>, grid, smem / 2, side.v16);
       else if (cp) go(k_col_iter_mx<R(), 0, W(), 0, 0, 1>, grid, smem / 2, side.v32);
       else go(k_col_iter_mx<R(), 0, W(), D(), 0>, grid, smem / 2, side.v32);
     });
@@ -342,13 +341,11 @@ void allow_large_smem_mx(int bytes) {
             set((const void *)k_row_iter_mx<R(), 0, W(), D(), 0>);
             set((const void *)k_row_iter_mx<R(), 0, W(), 0, 1>);
             set((const void *)k_row_iter_mx<R(), 0, W(), 0, 0, 1>);
-            set((const void *)k_row_iter_mx<R(), 0, W(), 0, 1, 1>);
           });
           with_walk<false>(w, [&](auto W) {
             set((const void *)k_col_iter_mx<R(), 0, W(), D(), 0>);
             set((const void *)k_col_iter_mx<R(), 0, W(), 0, 1>);
             set((const void *)k_col_iter_mx<R(), 0, W(), 0, 0, 1>);
-            set((const void *)k_col_iter_mx<R(), 0, W(), 0, 1, 1>);
           });
         }
       });
@@ -382,20 +379,18 @@ int iter_mx_blocks_per_sm(int smem, bool row, int walk, int threads, int dfs, in
   };
   for (int rho2 = 0; rho2 < 2; ++rho2)
     with_rho_dfs(rho2, dfs, [&](auto R, auto D) {
-      // both cache-policy instantiations (the choice is made after the geometry)
+      // both cache-policy instantiations of FP32 values (the choice is made after the geometry)
       if (row)
         with_walk<true>(walk, [&](auto W) {
           occ(lp ? (const void *)k_row_iter_mx<R(), 0, W(), 0, 1>
                  : (const void *)k_row_iter_mx<R(), 0, W(), D(), 0>);
-          occ(lp ? (const void *)k_row_iter_mx<R(), 0, W(), 0, 1, 1>
-                 : (const void *)k_row_iter_mx<R(), 0, W(), 0, 0, 1>);
+          if (!lp) occ((const void *)k_row_iter_mx<R(), 0, W(), 0, 0, 1>);
         });
       else
         with_walk<false>(walk, [&](auto W) {
           occ(lp ? (const void *)k_col_iter_mx<R(), 0, W(), 0, 1>
                  : (const void *)k_col_iter_mx<R(), 0, W(), D(), 0>);
-          occ(lp ? (const void *)k_col_iter_mx<R(), 0, W(), 0, 1, 1>
-                 : (const void *)k_col_iter_mx<R(), 0, W(), 0, 0, 1>);
+          if (!lp) occ((const void *)k_col_iter_mx<R(), 0, W(), 0, 0, 1>);
         });
     });
   return mn;

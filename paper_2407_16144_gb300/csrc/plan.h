@@ -1,6 +1,7 @@
 // Host plan of one side's tiled split-CSR layout, computed from the row pointers alone: which
 // rows are long, where every row's entries go, the chunks of the long rows, the staging stride,
-// and how many consecutive short tiles one walk item covers.  build_side uploads it; the C ABI
+// how many consecutive short tiles one walk item covers, and whether the FP64 walks sum a tile's
+// longest rows warp-wide.  build_side uploads it; the C ABI
 // exposes its summary (rhpdhg_plan_layout) so the rule can be checked without a GPU.
 #pragma once
 
@@ -19,6 +20,7 @@ struct SidePlan {
   long long nnz_s = 0, nnz_l = 0;   // padded lengths of the short and long arrays
   long long maxseg = 0;             // longest segment of one work item's tile group
   int mult = 1;                     // short tiles per work item
+  int wide_rows = 0;                // FP64 walks sum a tile's longest rows warp-wide
 };
 
 // Plans the layout of a side with nrows rows and row pointers hp[0..nrows] (hp[0] = 0).

@@ -510,6 +510,37 @@ size_t buf_drop_cache() {
   return freed;
 }
 
+// The cost model of tile_rows_fp64 over all short tiles of a side: FP64 adds per warp of the
+// lane-per-row sums (4 ceil(longest / 4) per tile) against the best threshold's (c + the sum over
+// rows longer than c of ceil(len / 32) + 5, c in 8, 16, 32).  The warp-wide sums are enabled
+// when they save at least 15% of those adds (power-law sides; not sides of even row lengths,
+// where the search would only cost time).
+static bool wide_rows_pay(const int *hp, const std::vector<uint32_t> &mask, int nrows) {
+  long long plain = 0, best = 0;
+  for (int t = 0; t * kTileRows < nrows; ++t) {
+    int len[kTileRows];
+    int mx = 0;
+    for (int r = 0; r < kTileRows; ++r) {
+      const int row = t * kTileRows + r;
+      len[r] = (row < nrows && !((mask[t] >> r) & 1u)) ? hp[row + 1] - hp[row] : 0;
+      mx = std::max(mx, len[r]);
+    }
+    const int p = (mx + 3) & ~3;
+    int b = p;
+    if (mx > 16) {
+      for (int c = 8; c <= 32 && c < mx; c *= 2) {
+        int cost = c;
+        for (int r = 0; r < kTileRows; ++r)
+          if (len[r] > c) cost += ((len[r] + 31) >> 5) + 5;
+        b = std::min(b, cost);
+      }
+    }
+    plain += p;
+    best += b;
+  }
+  return plain > 0 && (double)best <= 0.85 * (double)plain;
+}
+
 bool plan_side(const int *hp, int nrows, SidePlan *p) {
   SidePlan &P = *p;
   const int ntiles = (nrows + kTileRows - 1) / kTileRows;
@@ -590,6 +621,7 @@ bool plan_side(const int *hp, int nrows, SidePlan *p) {
   }
   P.mult = mult;
   P.maxseg = maxseg;
+  P.wide_rows = wide_rows_pay(hp, P.mask, nrows) ? 1 : 0;
   return true;
 }
 
@@ -621,6 +653,7 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   s.lay.n_long = nlong;
   s.lay.n_long_tiles = (nlong + kTileRows - 1) / kTileRows;
   s.lay.n_chunks = nch;
+  s.lay.wide_rows = P.wide_rows;
   s.nnz_short = nnz_s;
   s.nnz_long = nnz_l;
   const size_t ng = (size_t)std::max(s.lay.n_long_tiles, 1);

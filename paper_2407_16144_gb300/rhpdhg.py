@@ -211,7 +211,7 @@ def rhpdhg_get_trace(h, capacity: int):
 LAYOUT_FIELDS = ("grid_row", "grid_col", "tile_mult_row", "tile_mult_col", "long_rows_row",
                  "long_rows_col", "chunks_row", "chunks_col", "seg_row", "seg_col", "walk_row",
                  "walk_col", "cta_warps_row", "cta_warps_col", "tuned", "tune_ns_rule",
-                 "tune_ns_best")
+                 "tune_ns_best", "wide_rows_row", "wide_rows_col")
 
 
 def rhpdhg_get_layout(h):
@@ -225,7 +225,8 @@ def release_cached_memory() -> int:
     return int(load().rhpdhg_release_cached_memory())
 
 
-PLAN_FIELDS = ("tiles", "tile_mult", "long_rows", "chunks", "seg", "nnz_short", "nnz_long")
+PLAN_FIELDS = ("tiles", "tile_mult", "long_rows", "chunks", "seg", "nnz_short", "nnz_long",
+               "wide_rows")
 
 
 def rhpdhg_plan_layout(row_ptr):

@@ -8,6 +8,12 @@ into chunks of 256 entries.  M short tiles are walked per work item: the largest
 at least 2M tiles, a mean group segment of at most 256 entries (aligned short length times M
 over the tile count) and a longest group segment of at most 1024 entries; else 1.  The staging
 stride is the longest segment of a work item's group, rounded up to 4, plus 4.
+
+FP64 walks sum a tile's longest short rows warp-wide when that saves work over the whole side:
+per tile, lane-per-row sums cost the longest short row rounded up to 4 (FP64 adds per warp);
+with a threshold c of 8, 16 or 32 (below the longest row, tried only when the longest exceeds
+16) they cost c plus, for every short row longer than c, ceil(len / 32) + 5.  The side takes
+warp-wide sums when the tiles' best costs add up to at most 85% of the lane-per-row costs.
 """
 import numpy as np
 
@@ -23,6 +29,7 @@ def plan(row_ptr) -> dict:
     cur = cl = 0
     n_long = chunks = 0
     seg_b, seg_e = [], []
+    cost_plain = cost_best = 0
     for t in range(nt):
         L = lens[32 * t:32 * (t + 1)]
         short = L <= 128
@@ -41,6 +48,16 @@ def plan(row_ptr) -> dict:
                 n_long += 1
                 chunks += -(-int(L[r]) // 256)
         seg_e.append(cur)
+        sl = [int(L[r]) if short[r] else 0 for r in range(len(L))]
+        mx = max(sl, default=0)
+        plain = _align4(mx)
+        best = plain
+        if mx > 16:
+            for c in (8, 16, 32):
+                if c < mx:
+                    best = min(best, c + sum(-(-x // 32) + 5 for x in sl if x > c))
+        cost_plain += plain
+        cost_best += best
     maxseg = max((e - b for b, e in zip(seg_b, seg_e)), default=0)
     mult = 1
     for m in (4, 2):
@@ -51,7 +68,8 @@ def plan(row_ptr) -> dict:
             mult, maxseg = m, mx
             break
     return dict(tiles=nt, tile_mult=mult, long_rows=n_long, chunks=chunks,
-                seg=_align4(maxseg) + 4, nnz_short=_align4(cur) + 4, nnz_long=_align4(cl) + 256)
+                seg=_align4(maxseg) + 4, nnz_short=_align4(cur) + 4, nnz_long=_align4(cl) + 256,
+                wide_rows=int(cost_plain > 0 and cost_best <= 0.85 * cost_plain))
 
 
 def expected_tile_mult(row_ptr) -> int:

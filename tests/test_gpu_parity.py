@@ -80,6 +80,8 @@ def test_walk_layout(rh, case):
         assert rc == 0 and pl["tile_mult"] == lay[f"tile_mult_{side}"]
         assert pl["long_rows"] == lay[f"long_rows_{side}"] and pl["chunks"] == lay[f"chunks_{side}"]
         assert pl["seg"] == lay[f"seg_{side}"]
+        # warp-wide FP64 row sums where the tile cost model says they pay
+        assert lay[f"wide_rows_{side}"] == pl["wide_rows"]
     if case == "short_cols":
         assert lay["tile_mult_col"] == 4
     if case == "c3_small":

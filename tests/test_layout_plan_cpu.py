@@ -53,6 +53,18 @@ def test_plan_matches_rule(rh_lib, name, lengths):
     assert got == layout_rule.plan(rp), name
 
 
+def test_wide_row_sums_only_where_rows_are_skewed(rh_lib):
+    """The warp-wide FP64 row sums are chosen for skewed tiles (one long row among short ones,
+    a power law) and not for even row lengths, where they would save nothing."""
+    rng = np.random.default_rng(11)
+    skewed = ([2] * 31 + [100]) * 64
+    even = [25] * 32 * 64
+    power = list(np.minimum(rng.zipf(2.1, size=32 * 200), 128))
+    for lengths, want in ((skewed, 1), (even, 0), (power, 1), ([40] * 32 * 8, 0)):
+        rc, got = rh.rhpdhg_plan_layout(_rp(lengths))
+        assert rc == 0 and got["wide_rows"] == want == layout_rule.plan(_rp(lengths))["wide_rows"]
+
+
 def test_plan_rejects_bad_row_pointers(rh_lib):
     assert rh.rhpdhg_plan_layout(np.array([1, 2, 3]))[0] == rh.ERR_INVALID_ARG
     assert rh.rhpdhg_plan_layout(np.array([0, 3, 2]))[0] == rh.ERR_INVALID_ARG
