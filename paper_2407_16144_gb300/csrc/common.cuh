@@ -692,8 +692,7 @@ __device__ __forceinline__ void tile_rows_fp64(const double *smem, int row0, int
     if (p < pe) s0 += smem[p];
     if (p + 1 < pe) s1 += smem[p + 1];
     if (p + 2 < pe) s2 += smem[p + 2];
-    // the lane's epilogue loads go out while the warp sums the long rows
-    epi(row0 + lane, (s0 + s1) + (s2 + s3), false);
+    dot = (s0 + s1) + (s2 + s3);
   }
   unsigned big = __ballot_sync(full, act && len > T);
   while (big) {
@@ -705,7 +704,9 @@ __device__ __forceinline__ void tile_rows_fp64(const double *smem, int row0, int
     s = warp_sum(s);
     if (lane == r) dot = s;
   }
-  if (act && len > T) epi(row0 + lane, dot, false);
+  // one converged epilogue pass (split into the short rows' and the long rows' lanes, the FP64
+  // epilogue issued twice and measured slower)
+  if (act) epi(row0 + lane, dot, false);
 }
 
 // Lane r of a short tile sums row r's staged products smem[rb - seg_b, re - seg_b) with four
