@@ -159,29 +159,36 @@ typedef struct {
   int32_t cta_warps;            /* warps per CTA of the iteration kernels: 4, 8 or 16; 0 = the
                                    library's choice.                              default 0    */
   int32_t df_sums;              /* precision 1: sums of the restart test's norms (Section 3,
-                                   eq. adaptive-restart).  0 = each warp adds its rows' FP32
-                                   products in FP32 (fused multiply-adds, a fixed shuffle tree;
-                                   relative error below 1e-6), FP64 above the warp; 1 = double-
-                                   float (two FP32 numbers, error-free transformations) from the
-                                   row up: FP64-grade sums, slower on GPUs with a narrow FP64
-                                   pipe.                                          default 0    */
+                                   eq. adaptive-restart) in ordinary iterations.  0 = FP32 sums of
+                                   the FP32 products at every level (lane, warp, CTA, grid; fixed
+                                   trees and orders); 1 = double-float (two FP32 numbers,
+                                   error-free transformations) from the row up: FP64-grade sums,
+                                   slower on GPUs with a narrow FP64 pipe.  Restart points always
+                                   sum in FP64.                                   default 0    */
   /* Caller's allocator for the handle's device memory (both functions or neither; NULL = the
    * library's own cache of device buffers), with its context pointer.  Used by rhpdhg_create
    * only; the batched solver and the server ignore it.                          default NULL */
   rhpdhg_dev_alloc_fn dev_alloc;
   rhpdhg_dev_free_fn  dev_free;
   void *alloc_ctx;
-  int32_t autotune;             /* 1 = rhpdhg_create times candidate launch geometries of the
-                                   iteration kernels (warps per CTA of each side; plain or wide
-                                   staging walk of the mixed row kernel) on the handle's stream
-                                   and keeps the fastest per side; the choice is cached for the
-                                   process by a signature of the LP's structure (sizes, precision,
-                                   algorithm, row-length histograms), so handles of the same shape
-                                   reuse it without timing.  Ignored when cta_warps is set.
+  int32_t autotune;             /* 1 = rhpdhg_create times candidate launch shapes of the
+                                   iteration kernels on the handle's stream and keeps the fastest
+                                   per side: 4- or 8-warp CTAs; 1, 2 or 4 short tiles per work
+                                   item where the group fits the staging area; plain or wide
+                                   staging walk of the mixed row kernel; the full resident grid or
+                                   three quarters of it.  The choice is cached for the process by
+                                   a signature of the LP's structure (sizes, precision, algorithm,
+                                   sum mode, row-length histograms), so handles of the same shape
+                                   reuse it without timing.  Ignored when cta_warps or tile_mult
+                                   is set.                                        default 0    */
+  int32_t pow2_scaling;         /* 1 = the diagonal scalings D and E (Ruiz, then Pock-Chambolle)
+                                   rounded to the nearest powers of two (a preconditioner that
+                                   only shifts exponents; implied by precision 2). default 0   */
+  int32_t tile_mult;            /* 0 = short tiles per work item by the layout rule (or the
+                                   autotuner); 1, 2 or 4 = that many on each side whose longest
+                                   group of tiles fits the staging area (other sides keep the
+                                   rule).  rhpdhg_get_layout reports what each side walks.
                                                                                   default 0    */
-  int32_t pow2_scaling;         /* 1 = the Ruiz and Pock-Chambolle factors of D and E rounded to
-                                   the nearest powers of two (a preconditioner that only shifts
-                                   exponents; implied by precision 2).            default 0    */
 } rhpdhg_params;
 
 /* Result of a finished solve, filled by rhpdhg_poll. */

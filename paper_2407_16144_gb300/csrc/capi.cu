@@ -177,16 +177,30 @@ void algorithmic_bytes(rhpdhg_handle *h) {
   h->bytes_col = nnz * (vb + ib) + (h->n + 1) * ib + h->m * vb + h->n * vb * col_vec;
 }
 
-// Launch geometry of the iteration kernels for CTAs of wr warps (row side) and wc warps (column
-// side): dynamic shared memory for each warp's staging area, the walk instantiation of the
-// ordinary mixed row kernel (wide_row: 1 = the wide staging round, 0 = the plain walk, -1 = the
-// rule below) and grids of one work item per warp within the resident CTAs.
-void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
+// Launch shape of one side's iteration kernels: warps per CTA, short tiles per work item (0 = the
+// layout rule's), the ordinary mixed row kernel's wide staging round (1 = on, 0 = off, -1 = the
+// rule below), and the grid as a percentage of the resident CTAs (100 = all).
+struct SideShape {
+  int warps = kBlockWarps;
+  int mult = 0;
+  int wide = -1;
+  int cap = 100;
+};
+
+// Launch geometry of the iteration kernels for the row-side shape r and the column-side shape c:
+// tiles per work item, dynamic shared memory for each warp's staging area, the walk
+// instantiation of the ordinary mixed kernels, and grids of one work item per warp within the
+// resident CTAs (times the shape's cap).
+void set_geometry(rhpdhg_handle *h, const SideShape &r, const SideShape &c) {
+  apply_mult(h->rows, r.mult > 0 && mult_ok(h->rows, r.mult) ? r.mult : h->rows.rule_mult);
+  apply_mult(h->cols, c.mult > 0 && mult_ok(h->cols, c.mult) ? c.mult : h->cols.rule_mult);
   SideLayout &lr = h->rows.lay, &lc = h->cols.lay;
+  const int wr = r.warps, wc = c.warps;
   lr.cta_warps = wr;
   lc.cta_warps = wc;
   h->smem_row = wr * lr.seg * (int)sizeof(double);
   h->smem_col = wc * lc.seg * (int)sizeof(double);
+  auto capped = [](int b, int cap) { return std::max(1, b * cap / 100); };
   if (h->mixed) {
     lr.walk = lr.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
     lc.walk = lc.tile_mult > 1 ? kWalkGrouped : kWalkPlain;
@@ -194,8 +208,8 @@ void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
     // registers) when their tiles are long and the grid stays set by the tile count at the
     // wider kernel's residency, so that the registers cost no CTAs.
     if (lr.walk == kWalkPlain && lr.n_short_tiles > 0) {
-      bool wide = wide_row == 1;
-      if (wide_row < 0 &&
+      bool wide = r.wide == 1;
+      if (r.wide < 0 &&
           h->rows.nnz_short > (long long)lr.n_short_tiles * kWarp * kStageUnroll * 4) {
         const int bw =
             iter_mx_blocks_per_sm(h->smem_row, true, kWalkWide, wr * kWarp, h->ic.df_sums,
@@ -206,19 +220,34 @@ void set_geometry(rhpdhg_handle *h, int wr, int wc, int wide_row) {
       if (wide) lr.walk = kWalkWide;
     }
     h->grid_row = tile_grid(lr, h->sm_count,
-                            iter_mx_blocks_per_sm(h->smem_row, true, lr.walk, wr * kWarp,
-                                                  h->ic.df_sums, h->ic.bf16));
+                            capped(iter_mx_blocks_per_sm(h->smem_row, true, lr.walk, wr * kWarp,
+                                                         h->ic.df_sums, h->ic.bf16),
+                                   r.cap));
     h->grid_col = tile_grid(lc, h->sm_count,
-                            iter_mx_blocks_per_sm(h->smem_col, false, lc.walk, wc * kWarp,
-                                                  h->ic.df_sums, h->ic.bf16));
+                            capped(iter_mx_blocks_per_sm(h->smem_col, false, lc.walk, wc * kWarp,
+                                                         h->ic.df_sums, h->ic.bf16),
+                                   c.cap));
     const int br = iter_mx_restart_blocks_per_sm(h->smem_row, true, wr * kWarp);
     const int bc = iter_mx_restart_blocks_per_sm(h->smem_col, false, wc * kWarp);
     h->grid_row1 = std::max(1, std::min(h->grid_row, h->sm_count * std::max(br, 1)));
     h->grid_col1 = std::max(1, std::min(h->grid_col, h->sm_count * std::max(bc, 1)));
   } else {
-    h->grid_row = tile_grid(lr, h->sm_count, row_iter_blocks_per_sm(h->smem_row, wr * kWarp));
-    h->grid_col = tile_grid(lc, h->sm_count, col_iter_blocks_per_sm(h->smem_col, wc * kWarp));
+    h->grid_row = tile_grid(lr, h->sm_count,
+                            capped(row_iter_blocks_per_sm(h->smem_row, wr * kWarp), r.cap));
+    h->grid_col = tile_grid(lc, h->sm_count,
+                            capped(col_iter_blocks_per_sm(h->smem_col, wc * kWarp), c.cap));
   }
+}
+
+// The shape set_geometry applied last, as a candidate (wide as resolved by the rule).
+SideShape current_shape(const rhpdhg_handle *h, bool row) {
+  const SideLayout &l = row ? h->rows.lay : h->cols.lay;
+  SideShape s;
+  s.warps = l.cta_warps;
+  s.mult = l.tile_mult;
+  s.wide = (row && l.walk == kWalkWide) ? 1 : 0;
+  s.cap = 100;
+  return s;
 }
 
 void launch_row(rhpdhg_handle *h) {
@@ -337,40 +366,45 @@ int escalate_to_fp64(rhpdhg_handle *h) {
 // later handles of the same shape take it without timing.
 
 struct TuneChoice {
-  int wr = kBlockWarps, wc = kBlockWarps, wide = 0;
+  SideShape r, c;
   double us_rule = 0.0, us_best = 0.0;
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune_cache;
 
-struct RowCand {
-  int warps, wide;
-};
-
-std::vector<RowCand> row_candidates(const rhpdhg_handle *h) {
-  std::vector<RowCand> c;
-  const bool can_widen = h->mixed && h->rows.lay.tile_mult == 1 && h->rows.lay.n_short_tiles > 0;
-  for (int w : {4, 8}) {
-    c.push_back({w, 0});
-    if (can_widen) c.push_back({w, 1});
-  }
+// Candidate shapes of one side: 4- or 8-warp CTAs; 1, 2 or 4 tiles per work item where the
+// group fits the staging area; on the mixed row side with one tile per item, the plain or the
+// wide staging walk; the full resident grid or three quarters of it.
+std::vector<SideShape> side_candidates(const rhpdhg_handle *h, bool row) {
+  const SideStore &sd = row ? h->rows : h->cols;
+  std::vector<SideShape> c;
+  for (int w : {4, 8})
+    for (int m : {1, 2, 4}) {
+      if (!mult_ok(sd, m)) continue;
+      const bool can_widen = row && h->mixed && m == 1 && sd.lay.n_short_tiles > 0;
+      for (int wide = 0; wide <= (can_widen ? 1 : 0); ++wide)
+        for (int cap : {100, 75}) c.push_back(SideShape{w, m, wide, cap});
+    }
   return c;
 }
-const int kColCands[] = {4, 8};
+
+bool same_shape(const SideShape &a, const SideShape &b) {
+  return a.warps == b.warps && a.mult == b.mult && a.wide == b.wide && a.cap == b.cap;
+}
 
 // Largest grid of each side over all candidates (the partial buffers are sized for it).
 void candidate_grids(rhpdhg_handle *h, int *max_row, int *max_col) {
-  const int wr = h->rows.lay.cta_warps, wc = h->cols.lay.cta_warps;
-  const int wide = h->rows.lay.walk == kWalkWide ? 1 : 0;
+  const SideShape r0 = current_shape(h, true), c0 = current_shape(h, false);
   *max_row = h->grid_row;
   *max_col = h->grid_col;
-  for (const RowCand &r : row_candidates(h))
-    for (int c : kColCands) {
-      set_geometry(h, r.warps, c, r.wide);
-      *max_row = std::max(*max_row, h->grid_row);
-      *max_col = std::max(*max_col, h->grid_col);
-    }
-  set_geometry(h, wr, wc, wide);
+  const std::vector<SideShape> rs = side_candidates(h, true), cs = side_candidates(h, false);
+  const size_t k = std::max(rs.size(), cs.size());
+  for (size_t i = 0; i < k; ++i) {
+    set_geometry(h, rs[i % rs.size()], cs[i % cs.size()]);
+    *max_row = std::max(*max_row, h->grid_row);
+    *max_col = std::max(*max_col, h->grid_col);
+  }
+  set_geometry(h, r0, c0);
 }
 
 // Signature of the LP's structure for the cache: precision, algorithm, sum mode, sizes, SM
@@ -408,17 +442,16 @@ int autotune(rhpdhg_handle *h) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(h->tune_sig);
     if (it != g_tune_cache.end()) {
-      set_geometry(h, it->second.wr, it->second.wc, it->second.wide);
+      set_geometry(h, it->second.r, it->second.c);
       h->tuned = 2;
       h->tune_us_rule = it->second.us_rule;
       h->tune_us_best = it->second.us_best;
       return RHPDHG_OK;
     }
   }
-  const std::vector<RowCand> rows = row_candidates(h);
-  const int nr = (int)rows.size(), nc = 2;
-  const RowCand rule_r{h->rows.lay.cta_warps, h->rows.lay.walk == kWalkWide ? 1 : 0};
-  const int rule_c = h->cols.lay.cta_warps;
+  const std::vector<SideShape> rows = side_candidates(h, true), cols = side_candidates(h, false);
+  const int nr = (int)rows.size(), nc = (int)cols.size();
+  const SideShape rule_r = current_shape(h, true), rule_c = current_shape(h, false);
   // ordinary iterations only: no check, no restart, no trace while timing
   const IterConsts saved = h->ic;
   h->ic.check_every = INT_MAX;
@@ -428,13 +461,14 @@ int autotune(rhpdhg_handle *h) {
   h->ic.max_epoch_len = 0;
   h->ic.trace_cap = 0;
   int rc = reset_state(h);
+  // iteration i runs row candidate i mod nr and column candidate i mod nc; each stage is timed
+  // on its own, so every candidate of either side gets at least `reps` samples
   const int warm = 2, reps = 3;
-  const int K = warm + reps * nr * nc;
+  const int K = warm + reps * std::max(nr, nc);
   std::vector<cudaEvent_t> ev(3 * K);
   for (auto &e : ev) cudaEventCreate(&e);
   for (int i = 0; i < K && rc == RHPDHG_OK; ++i) {
-    const RowCand &r = rows[i % nr];
-    set_geometry(h, r.warps, kColCands[(i / nr) % nc], r.wide);
+    set_geometry(h, rows[i % nr], cols[i % nc]);
     cudaEventRecord(ev[3 * i], h->st);
     launch_row(h);
     cudaEventRecord(ev[3 * i + 1], h->st);
@@ -450,29 +484,29 @@ int autotune(rhpdhg_handle *h) {
     cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]);
     cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]);
     tr[i % nr].push_back(a);
-    tc[(i / nr) % nc].push_back(b);
+    tc[i % nc].push_back(b);
   }
   for (auto &ev_ : ev) cudaEventDestroy(ev_);
   h->ic = saved;
   if (rc != RHPDHG_OK) return rc;
   if (e != cudaSuccess)
     return set_err(h, RHPDHG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-  int br = 0, bc = 0, ir = 0, icr = 0;
+  int br = 0, bc = 0, ir = -1, icr = -1;
   for (int i = 0; i < nr; ++i) {
     if (median(tr[i]) < median(tr[br])) br = i;
-    if (rows[i].warps == rule_r.warps && rows[i].wide == rule_r.wide) ir = i;
+    if (same_shape(rows[i], rule_r)) ir = i;
   }
   for (int i = 0; i < nc; ++i) {
     if (median(tc[i]) < median(tc[bc])) bc = i;
-    if (kColCands[i] == rule_c) icr = i;
+    if (same_shape(cols[i], rule_c)) icr = i;
   }
   TuneChoice ch;
-  ch.wr = rows[br].warps;
-  ch.wide = rows[br].wide;
-  ch.wc = kColCands[bc];
-  ch.us_rule = 1e3 * (median(tr[ir]) + median(tc[icr]));
+  ch.r = rows[br];
+  ch.c = cols[bc];
+  // the rule's shape is a candidate whenever the CTA width is 4 or 8 (the default is 4)
+  ch.us_rule = 1e3 * ((ir >= 0 ? median(tr[ir]) : 0.0) + (icr >= 0 ? median(tc[icr]) : 0.0));
   ch.us_best = 1e3 * (median(tr[br]) + median(tc[bc]));
-  set_geometry(h, ch.wr, ch.wc, ch.wide);
+  set_geometry(h, ch.r, ch.c);
   h->tuned = 1;
   h->tune_us_rule = ch.us_rule;
   h->tune_us_best = ch.us_best;
@@ -681,7 +715,8 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
       P.pock_chambolle_alpha > 2.0 || P.adaptive_step < 0 || P.adaptive_step > 1 ||
       (P.cta_warps != 0 && P.cta_warps != 4 && P.cta_warps != 8 && P.cta_warps != 16) ||
       P.df_sums < 0 || P.df_sums > 1 || P.autotune < 0 || P.autotune > 1 ||
-      P.pow2_scaling < 0 || P.pow2_scaling > 1 || (P.precision == 2 && P.df_sums != 0))
+      P.pow2_scaling < 0 || P.pow2_scaling > 1 || (P.precision == 2 && P.df_sums != 0) ||
+      (P.tile_mult != 0 && P.tile_mult != 1 && P.tile_mult != 2 && P.tile_mult != 4))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG, "invalid parameter");
   if ((P.dev_alloc == nullptr) != (P.dev_free == nullptr))
     return set_err(nullptr, RHPDHG_ERR_INVALID_ARG,
@@ -882,11 +917,9 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   allow_large_smem(kMaxTileSmem);
   allow_large_smem_setup(kMaxTileSmem);
   allow_large_smem_mx(kMaxTileSmem);
-  {
-    const int wr = P.cta_warps > 0 ? P.cta_warps : kBlockWarps;
-    const int wc = P.cta_warps > 0 ? P.cta_warps : kBlockWarps;
-    set_geometry(h, wr, wc, -1);
-  }
+  // the rule's geometry for the power iteration, so that the step size does not depend on the
+  // launch shape asked for (which is applied after it)
+  set_geometry(h, SideShape{}, SideShape{});
 
   // ---- power iteration for sigma_max(K^) ----
   // v <- K^T K^ v / ||K^T K^ v|| from v = 1/sqrt(n); each step is two fused products (the
@@ -929,6 +962,12 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
     h->sigma_max = (m > 0 && h->nnz > 0) ? std::sqrt(s2) : 0.0;
   }
   buf_release(dn);
+  {
+    SideShape r, c;
+    r.warps = c.warps = P.cta_warps > 0 ? P.cta_warps : kBlockWarps;
+    r.mult = c.mult = P.tile_mult;   // 0 = the rule; a side whose group does not fit keeps it
+    set_geometry(h, r, c);
+  }
   if (P.step_size > 0) h->eta = P.step_size;
   else if (h->sigma_max > 1e-12) h->eta = P.step_safety / h->sigma_max;
   else h->eta = 1.0;
@@ -962,7 +1001,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   std::memset(h->h_mirror, 0, 2 * sizeof(Ctl));
   {
     int gr = h->grid_row, gc = h->grid_col;
-    if (P.autotune && P.cta_warps == 0) candidate_grids(h, &gr, &gc);
+    if (P.autotune && P.cta_warps == 0 && P.tile_mult == 0) candidate_grids(h, &gr, &gc);
     CKC(dalloc(&h->part_row, (size_t)gr * kMaxPartials));
     CKC(dalloc(&h->part_col, (size_t)gc * kMaxPartials));
   }
@@ -1026,7 +1065,7 @@ int rhpdhg_create(const rhpdhg_problem *lp, const rhpdhg_params *params, void *c
   h->launches = launches_so_far() - launches0;
   CKC(cudaStreamSynchronize(st));
   CKC(cudaGetLastError());
-  if (P.autotune && P.cta_warps == 0) {
+  if (P.autotune && P.cta_warps == 0 && P.tile_mult == 0) {
     const int rc = autotune(h);
     if (rc != RHPDHG_OK) return fail(rc);
   }

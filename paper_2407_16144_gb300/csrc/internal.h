@@ -30,7 +30,23 @@ struct SideStore {
   unsigned int *done_a = nullptr, *done_b = nullptr;
   double *gpart_a = nullptr, *gpart_b = nullptr;
   long long nnz_short = 0, nnz_long = 0;
+  int rule_mult = 1;                    // tiles per work item by the layout rule
+  long long maxseg_mult[3] = {0, -1, -1};  // longest group segment with 1, 2, 4 tiles per item
+                                           // (-1: over the staging budget)
 };
+
+// Tiles per work item m usable on a side (its longest group of m tiles fits the staging area).
+inline bool mult_ok(const SideStore &sd, int m) {
+  const int k = m == 4 ? 2 : (m == 2 ? 1 : 0);
+  return (m == 1 || m == 2 || m == 4) && sd.maxseg_mult[k] >= 0;
+}
+// Sets the side's walk to m tiles per work item (mult_ok): item count and staging stride.
+inline void apply_mult(SideStore &sd, int m) {
+  const int k = m == 4 ? 2 : (m == 2 ? 1 : 0);
+  sd.lay.tile_mult = m;
+  sd.lay.n_tile_groups = (sd.lay.n_short_tiles + m - 1) / m;
+  sd.lay.seg = (int)((sd.maxseg_mult[k] + 3) & ~3LL) + 4;
+}
 
 struct RowVecs {      // m-vectors used by the row kernel (K^ x~ and the dual step)
   double *y, *yt, *y0, *kx, *kxt, *kx0, *certy;

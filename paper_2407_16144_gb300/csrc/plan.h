@@ -21,6 +21,9 @@ struct SidePlan {
   long long maxseg = 0;             // longest segment of one work item's tile group
   int mult = 1;                     // short tiles per work item
   int wide_rows = 0;                // FP64 walks sum a tile's longest rows warp-wide
+  // longest segment of a work item's tile group with 1, 2 and 4 tiles per item (-1 where it
+  // exceeds the staging budget): the walks the autotuner may choose instead of the rule's
+  long long maxseg_mult[3] = {0, -1, -1};
 };
 
 // Plans the layout of a side with nrows rows and row pointers hp[0..nrows] (hp[0] = 0).

@@ -605,18 +605,22 @@ bool plan_side(const int *hp, int nrows, SidePlan *p) {
   // staged as one segment, so that each warp's chain of dependent loads carries M tiles' bytes.
   // M is the largest of kMaxTileMult, ..., 2 whose mean group segment fits one staging round
   // (128 * kStageUnroll entries) and whose longest fits the staging budget; else 1.
-  int mult = 1;
-  for (int cand = kMaxTileMult; cand >= 2 && mult == 1; cand /= 2) {
-    if (ntiles < 2 * cand) continue;
-    if (align4(cur) * cand > (long long)ntiles * kWarp * kStageUnroll * 4) continue;
+  P.maxseg_mult[0] = maxseg;
+  for (int k = 1, cand = 2; cand <= kMaxTileMult; ++k, cand *= 2) {
     long long mx = 0;
     for (int t0 = 0; t0 < ntiles; t0 += cand) {
       const int t1 = std::min(ntiles, t0 + cand) - 1;
       mx = std::max(mx, (long long)P.tile_end[t1] - P.ptr_s[(size_t)t0 * kTileRows]);
     }
-    if (mx <= kSegBudget) {
+    P.maxseg_mult[k] = (ntiles > 0 && mx <= kSegBudget) ? mx : -1;
+  }
+  int mult = 1;
+  for (int k = 2, cand = kMaxTileMult; cand >= 2 && mult == 1; --k, cand /= 2) {
+    if (ntiles < 2 * cand) continue;
+    if (align4(cur) * cand > (long long)ntiles * kWarp * kStageUnroll * 4) continue;
+    if (P.maxseg_mult[k] >= 0) {
       mult = cand;
-      maxseg = mx;
+      maxseg = P.maxseg_mult[k];
     }
   }
   P.mult = mult;
@@ -654,6 +658,8 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   s.lay.n_long_tiles = (nlong + kTileRows - 1) / kTileRows;
   s.lay.n_chunks = nch;
   s.lay.wide_rows = P.wide_rows;
+  s.rule_mult = mult;
+  for (int k = 0; k < 3; ++k) s.maxseg_mult[k] = P.maxseg_mult[k];
   s.nnz_short = nnz_s;
   s.nnz_long = nnz_l;
   const size_t ng = (size_t)std::max(s.lay.n_long_tiles, 1);

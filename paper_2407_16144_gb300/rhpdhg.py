@@ -58,7 +58,8 @@ class rhpdhg_params(C.Structure):
                 ("trace_capacity", C.c_int64), ("x0", C.c_void_p), ("y0", C.c_void_p),
                 ("adaptive_step", C.c_int32), ("cta_warps", C.c_int32),
                 ("df_sums", C.c_int32), ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN),
-                ("alloc_ctx", C.c_void_p), ("autotune", C.c_int32), ("pow2_scaling", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("autotune", C.c_int32), ("pow2_scaling", C.c_int32),
+                ("tile_mult", C.c_int32)]
 
 
 class rhpdhg_result(C.Structure):

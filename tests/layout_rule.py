@@ -23,6 +23,16 @@ def _align4(v: int) -> int:
 
 
 def plan(row_ptr) -> dict:
+    return _plan(row_ptr)[0]
+
+
+def group_fits(row_ptr, m: int) -> bool:
+    """Whether walking m consecutive short tiles per work item fits the staging area: the longest
+    group segment has at most 1024 entries (always true for m = 1)."""
+    return m == 1 or _plan(row_ptr)[1](m) <= 1024
+
+
+def _plan(row_ptr):
     lens = np.diff(np.asarray(row_ptr, dtype=np.int64))
     n = len(lens)
     nt = (n + 31) // 32
@@ -59,17 +69,23 @@ def plan(row_ptr) -> dict:
         cost_plain += plain
         cost_best += best
     maxseg = max((e - b for b, e in zip(seg_b, seg_e)), default=0)
+
+    def longest_group(m):
+        if nt == 0:
+            return 1 << 30
+        return max(seg_e[min(nt, t + m) - 1] - seg_b[t] for t in range(0, nt, m))
+
     mult = 1
     for m in (4, 2):
         if nt < 2 * m or _align4(cur) * m > nt * 256:
             continue
-        mx = max(seg_e[min(nt, t + m) - 1] - seg_b[t] for t in range(0, nt, m))
+        mx = longest_group(m)
         if mx <= 1024:
             mult, maxseg = m, mx
             break
     return dict(tiles=nt, tile_mult=mult, long_rows=n_long, chunks=chunks,
                 seg=_align4(maxseg) + 4, nnz_short=_align4(cur) + 4, nnz_long=_align4(cl) + 256,
-                wide_rows=int(cost_plain > 0 and cost_best <= 0.85 * cost_plain))
+                wide_rows=int(cost_plain > 0 and cost_best <= 0.85 * cost_plain)), longest_group
 
 
 def expected_tile_mult(row_ptr) -> int:

@@ -737,6 +737,46 @@ def test_cta_width_iterates_match_oracle(rh, case, warps):
         assert rel(xt, sn["xt"]) < 1e-10 and rel(yt, sn["yt"]) < 1e-10
 
 
+@pytest.mark.parametrize("case", ["c2_small", "c3_small", "short_cols"])
+def test_tile_groups_iterates_match_oracle_and_each_other(rh, case):
+    """Every tiles-per-item choice the autotuner may make computes the same method.  A forced
+    tile_mult of 1, 2 or 4 is taken on each side whose longest group fits the staging area (the
+    rule restated in Python decides which), and otherwise the side keeps the rule.  Before the
+    first restart no reduction reaches the iterates, and the FP64 PDHG points of all choices
+    are then bit-identical.  After 200 iterations they match the oracle's to 1e-10, with its
+    restart iterations."""
+    lp = CASES[case]()
+    A = O.csr_matrix(lp)
+    rps = {"row": A.indptr, "col": A.T.tocsr().indptr}
+    common = dict(algorithm=1, eps_rel_kkt=1e-14, first_epoch_len=20, check_every=16)
+    T = 200
+    o = O.solve(lp, O.OracleParams(max_iters=T, **common), snapshot_iters=[T - 1], trace=True)
+    early = None
+    for m in (1, 2, 4):
+        with rh.Solver(lp, max_iters=15, tile_mult=m, **common) as s:
+            s.run()
+            pts = s.state(1)
+            lay = s.layout()
+        for side, rp in rps.items():
+            want = m if layout_rule.group_fits(rp, m) else layout_rule.expected_tile_mult(rp)
+            assert lay[f"tile_mult_{side}"] == want, (side, m)
+        if early is None:
+            early = pts
+        else:
+            assert np.array_equal(pts[0], early[0]) and np.array_equal(pts[1], early[1]), m
+        with rh.Solver(lp, max_iters=T, tile_mult=m, trace=1, trace_capacity=256,
+                       **common) as s:
+            r = s.run()
+            xt, yt = s.state(1)
+            tr = s.trace()
+        assert r.iters == T
+        stop = min(first_tie(o.trace), first_tie(tr))
+        assert [a[0] for a in tr[:stop] if a[4]] == [b[0] for b in o.trace[:stop] if b[4]]
+        if stop == len(tr):
+            sn = o.snapshots[T - 1]
+            assert rel(xt, sn["xt"]) < 1e-10 and rel(yt, sn["yt"]) < 1e-10
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_autotuner_choice_report_and_cache(rh, precision):
     """The autotuner times the candidate geometries at create, reports the rule's and the chosen
