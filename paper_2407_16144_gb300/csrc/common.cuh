@@ -82,6 +82,8 @@ struct SideLayout {
   const int *idx_l = nullptr;       // long entries (padded, plus kChunk slack at the end)
   const int *chunk_ptr = nullptr;   // n_long + 1: chunks of long row i are [chunk_ptr[i], ..[i+1])
   const int *chunk_row = nullptr;   // n_chunks: long-row index of each chunk
+  const int4 *chunk_desc = nullptr; // n_chunks: (long-row index, first entry, end entry, chunks
+                                    // of its group of 32 long rows): one load per chunk item
   int tile_mult = 1;         // consecutive short tiles per work item (1 .. kMaxTileMult)
   int walk = 0;              // instantiation of the ordinary mixed kernels' walk (kWalk*)
   int cta_warps = kBlockWarps;  // warps per CTA of this side's iteration kernels (host only)
@@ -595,11 +597,10 @@ __device__ __forceinline__ void walk_chunk(const SideLayout &lay, const SideVals
                                            const Src &src, const WalkScratch ws, Epi &epi,
                                            GroupDone &gdone, int item) {
   const int lane = threadIdx.x & 31;
-  const int li = lay.chunk_row[item];
-  const int c0 = lay.chunk_ptr[li];
-  const int re = lay.end_l[li];
-  const int cb = lay.beg_l[li] + (item - c0) * kChunk;   // 4-aligned
-  const int ce = min(cb + kChunk, re);
+  const int4 dsc = __ldg(lay.chunk_desc + item);
+  const int li = dsc.x;
+  const int cb = dsc.y;                                   // 4-aligned
+  const int ce = dsc.z;
   // lane reads entries [p0, p0 + 8): two 16-byte index loads, 16 or 32 bytes of values
   const int p0 = cb + 8 * lane;
   PT s = PT(0);
@@ -626,7 +627,7 @@ __device__ __forceinline__ void walk_chunk(const SideLayout &lay, const SideVals
   if (lane == 0) {
     ws.chunk_part[item] = (double)s;
     __threadfence();
-    const unsigned int need = (unsigned int)(lay.chunk_ptr[g1] - lay.chunk_ptr[g0]);
+    const unsigned int need = (unsigned int)dsc.w;
     const unsigned int old = atomicAdd(ws.group_done + grp, 1u);
     fin = (old == need - 1) ? 1 : 0;
   }
@@ -635,9 +636,18 @@ __device__ __forceinline__ void walk_chunk(const SideLayout &lay, const SideVals
     __threadfence();
     const int lr = g0 + lane;
     if (lr < g1) {
+      // the row's chunk partials, added in chunk order; loaded eight at a time so that a long
+      // row's loads are in flight together (a row has up to 5000 / 256 chunks)
       PT d = PT(0);
-      for (int c = lay.chunk_ptr[lr]; c < lay.chunk_ptr[lr + 1]; ++c)
-        d += PT(__ldcg(ws.chunk_part + c));
+      const int c1 = lay.chunk_ptr[lr + 1];
+      for (int c = lay.chunk_ptr[lr]; c < c1; c += 8) {
+        double p[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) p[u] = c + u < c1 ? __ldcg(ws.chunk_part + c + u) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (c + u < c1) d += PT(p[u]);
+      }
       epi(lay.long_rows[lr], d, true);
     }
     // the finishing warp varies from run to run: the group's reduction contributions go to the

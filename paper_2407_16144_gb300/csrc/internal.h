@@ -23,6 +23,7 @@ struct SideStore {
       *beg_l = nullptr, *end_l = nullptr, *idx_l = nullptr;
   uint32_t *long_mask = nullptr;
   int *chunk_ptr = nullptr, *chunk_row = nullptr;
+  int4 *chunk_desc = nullptr;
   double *val64_s = nullptr, *val64_l = nullptr;
   float *val32_s = nullptr, *val32_l = nullptr;
   __nv_bfloat16 *val16_s = nullptr, *val16_l = nullptr;

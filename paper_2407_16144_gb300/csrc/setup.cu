@@ -681,6 +681,18 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   TRY(up(&s.end_l, end_l));
   TRY(up(&s.chunk_ptr, chunk_ptr));
   TRY(up(&s.chunk_row, chunk_row));
+  {
+    // per chunk: its long row, entry range, and the chunk count of its group of 32 long rows
+    std::vector<int4> desc((size_t)std::max(nch, 1));
+    for (int c = 0; c < nch; ++c) {
+      const int li = chunk_row[c];
+      const int cb = beg_l[li] + (c - chunk_ptr[li]) * kChunk;
+      const int g0 = (li / kTileRows) * kTileRows, g1 = std::min(g0 + kTileRows, nlong);
+      desc[c] = make_int4(li, cb, std::min(cb + kChunk, end_l[li]), chunk_ptr[g1] - chunk_ptr[g0]);
+    }
+    TRY(buf_alloc((void **)&s.chunk_desc, desc.size() * sizeof(int4)));
+    TRY(cudaMemcpy(s.chunk_desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  }
   TRY(up(&d_dst, dst));
   TRY(buf_alloc((void **)&s.long_mask, mask.size() * sizeof(uint32_t)));
   TRY(cudaMemcpy(s.long_mask, mask.data(), mask.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
@@ -739,6 +751,7 @@ cudaError_t build_side(cudaStream_t st, int nrows, int nnz, const int *ptr, cons
   s.lay.idx_l = s.idx_l;
   s.lay.chunk_ptr = s.chunk_ptr;
   s.lay.chunk_row = s.chunk_row;
+  s.lay.chunk_desc = s.chunk_desc;
   s.v64.s = s.val64_s;
   s.v64.l = s.val64_l;
   s.v32.s = s.val32_s;
@@ -782,7 +795,8 @@ unsigned int values_exact_in_bf16(cudaStream_t st, long long nnz, const double *
 void free_side(SideStore *s) {
   void *bufs[] = {s->ptr_s, s->tile_end, s->idx_s, s->long_mask, s->long_rows, s->beg_l,
                   s->end_l, s->idx_l,
-                  s->chunk_ptr, s->chunk_row, s->val64_s, s->val64_l, s->val32_s, s->val32_l,
+                  s->chunk_ptr, s->chunk_row, s->chunk_desc, s->val64_s, s->val64_l,
+                  s->val32_s, s->val32_l,
                   s->val16_s, s->val16_l,
                   s->part_a, s->part_b, s->done_a, s->done_b, s->gpart_a, s->gpart_b};
   for (void *b : bufs) buf_release(b);
