@@ -489,7 +489,7 @@ def run_ours(args):
     step_other()
     o_outs, o_ms = timed(step_other, 3)
     ro = o_outs[-1]
-    # rate probes for the roofline denominators that the driver's peaks do not give: the read
+    # rate probes for the roofline denominators that MEASURED_PEAKS.json does not hold: the read
     # bandwidth of a 64 MiB buffer held in L2, and the FP64 FMA rate
     rc1, l2_gbs = rhpdhg.rhpdhg_probe_l2_read_bandwidth(64 << 20, sh)
     rc2, fp64_tflops = rhpdhg.rhpdhg_probe_fp64_fma_rate(sh)
