@@ -501,6 +501,39 @@ def make_tiny_general(seed: int, m_eq: int = 2, m_ineq: int = 2, n: int = 5) -> 
               q=q, l=l, u=u, name=f"tiny_general_s{seed}")
 
 
+def make_long_lines(seed: int, m: int = 2400, n: int = 3000, dense_rows: int = 2,
+                    dense_cols: int = 2, col_nnz: int = 3) -> LP:
+    """Iterate-parity case for the long-row paths: an m x n general-form LP (half equality rows)
+    whose first `dense_rows` rows hold every column and whose first `dense_cols` columns appear in
+    every row (with the defaults, rows of 3000 and columns of 2400 entries, more than 8 chunks of
+    256 each), the other columns holding col_nnz random entries; N(0,1) values, finite boxes on
+    most columns, some free; c and q random (feasibility is not needed for iterate parity)."""
+    rng = np.random.default_rng(40_000 + seed)
+    rows, cols = [], []
+    for i in range(dense_rows):
+        rows.append(np.full(n, i))
+        cols.append(np.arange(n))
+    for j in range(dense_cols):
+        rows.append(np.arange(dense_rows, m))
+        cols.append(np.full(m - dense_rows, j))
+    for j in range(dense_cols, n):
+        r = rng.choice(np.arange(dense_rows, m), size=col_nnz, replace=False)
+        rows.append(r)
+        cols.append(np.full(col_nnz, j))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = rng.standard_normal(len(rows))
+    row_ptr, col_idx, val = coo_to_csr(m, n, rows, cols, vals)
+    l = rng.uniform(-2.0, 0.0, size=n)
+    u = l + rng.uniform(0.5, 3.0, size=n)
+    free = rng.random(n) < 0.1
+    l[free], u[free] = -INF, INF
+    m_eq = m // 2
+    return LP(m_eq=m_eq, m_ineq=m - m_eq, n=n, row_ptr=row_ptr, col_idx=col_idx, val=val,
+              c=rng.standard_normal(n), q=rng.standard_normal(m), l=l, u=u,
+              name=f"long_lines_s{seed}")
+
+
 def make_box_lp(seed: int, n: int = 20) -> LP:
     """LP with no constraint rows (m = 0): min c^T x over a finite box, c_j != 0."""
     rng = np.random.default_rng(30_000 + seed)

@@ -62,6 +62,8 @@ CASES = {
     # two entries per column: the K^T walk takes four 64-entry tiles per work item, and 4001
     # columns leave a ragged last group (two tiles, the second with one row)
     "short_cols": lambda: lpgen.make_standard_planted(5, m=1000, n=4001, col_nnz=2),
+    # rows of 3000 and columns of 2400 entries: long rows of 10-12 chunks on both sides
+    "long_lines": lambda: lpgen.make_long_lines(0),
 }
 
 
@@ -713,7 +715,7 @@ def test_mixed_restart_decisions_fp32_vs_fp64_grade_sums(rh, case, alg):
 
 
 @pytest.mark.parametrize("warps", [8, 16])
-@pytest.mark.parametrize("case", ["c2_small", "c3_small", "short_cols"])
+@pytest.mark.parametrize("case", ["c2_small", "c3_small", "short_cols", "long_lines"])
 def test_cta_width_iterates_match_oracle(rh, case, warps):
     """Every CTA width the autotuner may choose computes the same method: with 8- and 16-warp
     CTAs the FP64 PDHG points after 200 iterations match the oracle's to 1e-10 and the restart
