@@ -74,6 +74,7 @@ struct rhpdhg_handle {
   ColVecs cv{};
   int grid_row = 1, grid_col = 1, smem_row = 0, smem_col = 0;
   int grid_row1 = 1, grid_col1 = 1;   // restart-mode mixed kernels: at most one resident wave
+  int col_rows_last = 1;              // CTA rows the last column launch wrote (see DeferredCol)
   double eta = 1.0, omega0 = 1.0, sigma_max = 0.0;
 
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -251,15 +252,24 @@ SideShape current_shape(const rhpdhg_handle *h, bool row) {
 }
 
 void launch_row(rhpdhg_handle *h) {
+  // the column stage that precedes this row stage, for the case that it deferred its reduction:
+  // an ordinary column launch (grid_col CTAs; the mixed ordinary kernel's long-row groups use
+  // the second walk scratch, the FP64 kernel's the first)
+  DeferredCol dc;
+  dc.part = h->part_col;
+  dc.gpart = h->mixed ? h->cols.wb.group_part : h->cols.wa.group_part;
+  dc.nb = h->col_rows_last;   // the column launch before this one (the autotuner varies grids)
+  dc.ngroups = h->cols.lay.n_long_tiles;
   if (h->mixed)
     launch_row_iter_mx(h->st, h->rows, h->rvm, h->dxt, h->dxt64, h->x0, h->ctl, h->part_row,
-                       h->ic, h->grid_row, h->grid_row1, h->smem_row);
+                       h->ic, h->grid_row, h->grid_row1, h->smem_row, dc);
   else
     launch_row_iter(h->st, h->rows, h->xt, h->rv, h->ctl, h->part_row, h->ic, h->grid_row,
-                    h->smem_row);
+                    h->smem_row, dc);
 }
 
 void launch_col(rhpdhg_handle *h, int phase) {
+  h->col_rows_last = h->grid_col;   // a deferring (ordinary) column launch has grid_col CTAs
   if (h->mixed)
     launch_col_iter_mx(h->st, h->cols, h->cvm, h->dyt, h->dyt64, h->y0, h->ctl, h->part_col,
                        h->ic, h->grid_col, h->grid_col1, h->smem_col, phase);
@@ -273,12 +283,18 @@ void launch_iteration(rhpdhg_handle *h) {
   launch_col(h, 0);
 }
 
+// Iterations per host chunk (one captured graph, one read of the control block): the check
+// cadence, at most kMaxChunk, so that a large check_every does not make a graph of that many
+// launches (the device makes every decision; the host only polls between chunks).
+constexpr int kMaxChunk = 256;
+int chunk_iters(const rhpdhg_handle *h) { return std::min(h->p.check_every, kMaxChunk); }
+
 int capture_graphs(rhpdhg_handle *h) {
   for (int g = 0; g < 2; ++g) {
     if (h->gexec[g]) continue;
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
-    for (int i = 0; i < h->p.check_every; ++i) launch_iteration(h);
+    for (int i = 0; i < chunk_iters(h); ++i) launch_iteration(h);
     cudaMemcpyAsync(h->h_mirror + g, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st);
     CK(cudaStreamEndCapture(h->st, &graph));
     cudaError_t e = cudaGraphInstantiate(&h->gexec[g], graph, 0);
@@ -346,6 +362,7 @@ int escalate_to_fp64(rhpdhg_handle *h) {
   c.n_next = c.n;
   c.cnt_row = c.cnt_col = 0;
   c.mv_ready = 0;
+  c.col_deferred = 0;
   c.escalated = 1;
   CK(cudaMemcpyAsync(h->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
   side_spmv(h->st, h->rows, h->xt, h->kxt, h->grid_row);
@@ -540,8 +557,9 @@ void drive(rhpdhg_handle *h) {
   cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
   std::vector<cudaEvent_t> pev;
+  const int chunk = chunk_iters(h);
   if (h->p.profile) {
-    pev.resize(3 * h->p.check_every);
+    pev.resize(3 * chunk);
     for (auto &e : pev) cudaEventCreate(&e);
   }
   h->ms_row = h->ms_col = 0.0;
@@ -565,7 +583,7 @@ void drive(rhpdhg_handle *h) {
         if (graphs) {
           cudaGraphLaunch(h->gexec[g], h->st);
         } else {
-          for (int i = 0; i < h->p.check_every; ++i) {
+          for (int i = 0; i < chunk; ++i) {
             if (h->p.profile) cudaEventRecord(pev[3 * i], h->st);
             launch_row(h);
             if (h->p.profile) cudaEventRecord(pev[3 * i + 1], h->st);
@@ -576,7 +594,7 @@ void drive(rhpdhg_handle *h) {
         }
         cudaEventRecord(ev[g], h->st);
         ++launched;
-        h->launches += (h->mixed ? 4LL : 2LL) * h->p.check_every;
+        h->launches += (h->mixed ? 4LL : 2LL) * chunk;
       }
       if (done >= launched) break;
       const int g = (int)(done & 1);
@@ -594,7 +612,7 @@ void drive(rhpdhg_handle *h) {
         long long ran = mc.t - last_t;
         if (mc.status == kNumericalError) ran += 1;
         last_t = mc.t;
-        for (long long i = 0; i < ran && i < h->p.check_every; ++i) {
+        for (long long i = 0; i < ran && i < chunk; ++i) {
           float a = 0, b = 0;
           cudaEventElapsedTime(&a, pev[3 * i], pev[3 * i + 1]);
           cudaEventElapsedTime(&b, pev[3 * i + 1], pev[3 * i + 2]);

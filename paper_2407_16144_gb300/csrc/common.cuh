@@ -108,6 +108,15 @@ struct WalkScratch {
                                       // long-row epilogues of each group (see walk_tiles)
 };
 
+// An ordinary column stage that left its grid reduction to the next row kernel (see
+// col_defers): its CTA rows of partials, its long-row groups' partials, and their counts.
+struct DeferredCol {
+  const double *part = nullptr;
+  const double *gpart = nullptr;
+  int nb = 0;
+  int ngroups = 0;
+};
+
 // Device control block.  Written only by the last CTA of a kernel (or by the host while no
 // kernel of the handle runs); read by every CTA at kernel entry.
 struct Ctl {
@@ -117,6 +126,9 @@ struct Ctl {
   long long k_next, n_next;
   int status;
   int restart_pending;   // 1: iterate t+1 is the restart point T(z^{n,k})
+  int col_deferred;      // 1: the last column stage left its reduction to the next row kernel
+                         // (set by every CTA of that stage, which no column kernel reads;
+                         // cleared by the row finaliser that applies it)
   double w;              // Halpern weight (k+1)/(k+2) of the pending blend
   double omega, tau, sigma, eta;
   double tau_inv, sigma_inv;   // 1 / tau, 1 / sigma (set with tau and sigma: the restart test
@@ -333,7 +345,7 @@ __device__ __forceinline__ double (*cta_red())[kMaxPartials] {
 // slots set in prewarp hold, in lane 0, a value already summed over the warp (FP64 slots only).
 // Returns true in every thread of the last CTA to finish (after a fence), which then owns the
 // grid-level reduction.
-template <int NS, int NM, int ND, bool EXACT>
+template <int NS, int NM, int ND, bool EXACT, bool TICKET = true>
 __device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND, EXACT> &a, unsigned smask, unsigned mmask,
                                       unsigned prewarp, double *part, unsigned int *ticket) {
   double (*red)[kMaxPartials] = cta_red();
@@ -381,13 +393,27 @@ __device__ bool cta_reduce_and_ticket(Acc<NS, NM, ND, EXACT> &a, unsigned smask,
       for (int w = 1; w < nw; ++w) v = fmax(v, red[w][NS + i]);
       dst[NS + i] = v;
     }
-    __threadfence();
-    const unsigned int tk = atomicAdd(ticket, 1u);
-    last = (tk == gridDim.x - 1);
+    if constexpr (TICKET) {
+      __threadfence();
+      const unsigned int tk = atomicAdd(ticket, 1u);
+      last = (tk == gridDim.x - 1);
+    }
   }
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
+  if constexpr (TICKET) {
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+  } else {
+    return false;
+  }
+}
+
+// The CTA-level half of cta_reduce_and_ticket: the CTA's row of partials is written and no ticket
+// is taken (the row is reduced by a later kernel, after this one has completed).
+template <int NS, int NM, int ND, bool EXACT>
+__device__ void cta_reduce_store(Acc<NS, NM, ND, EXACT> &a, unsigned smask, unsigned mmask,
+                                 double *part) {
+  cta_reduce_and_ticket<NS, NM, ND, EXACT, false>(a, smask, mmask, 0u, part, nullptr);
 }
 
 // Warp-collective: reduce the long-row sums al of every lane and store them as group grp's
@@ -428,10 +454,10 @@ __device__ __forceinline__ void store_group(Acc<NS, 0, ND, EXACT> &al, unsigned 
 constexpr int kGridBatch = 10;
 template <int NS, int NM, bool BATCH = true, int ND = 0, bool EXACT = true>
 __device__ void grid_finish(const double *part, double *out, unsigned smask, unsigned mmask,
-                            const double *gpart = nullptr, int ngroups = 0) {
+                            const double *gpart = nullptr, int ngroups = 0, int nrows = -1) {
   double (*red)[kMaxPartials] = cta_red();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int nb = gridDim.x;
+  const int nb = nrows >= 0 ? nrows : (int)gridDim.x;   // rows of part (default: this grid's)
   double v[NS + NM];
   DF vd[ND > 0 ? ND : 1];
 #pragma unroll

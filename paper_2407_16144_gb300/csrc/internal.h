@@ -152,8 +152,10 @@ void vmul(cudaStream_t st, int n, const double *a, const double *x, double *y, i
 void vclamp(cudaStream_t st, int n, double *x, const double *l, const double *u);
 
 // ---- iteration (iterate.cu) -----------------------------------------------------------------
+// dc: the column stage's partials, which the row kernel reduces when that stage deferred them
 void launch_row_iter(cudaStream_t st, const SideStore &side, const double *xt, const RowVecs &v,
-                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem);
+                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem,
+                     const DeferredCol &dc);
 void launch_col_iter(cudaStream_t st, const SideStore &side, const double *yt, const ColVecs &v,
                      Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem,
                      int phase);
@@ -176,7 +178,8 @@ cudaError_t kkt_eval_with_scratch(const rhpdhg_problem *lp, const double *x, con
 // grid: CTAs of the ordinary kernel; grid1: CTAs of the restart-mode kernel (at most one wave)
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
-                        double *part, const IterConsts &ic, int grid, int grid1, int smem);
+                        double *part, const IterConsts &ic, int grid, int grid1, int smem,
+                        const DeferredCol &dc);
 void launch_col_iter_mx(cudaStream_t st, const SideStore &side, const ColVecsMx &v,
                         const float *dyt, const double *dyt64, const double *y0, Ctl *ctl,
                         double *part, const IterConsts &ic, int grid, int grid1, int smem,

@@ -60,9 +60,40 @@ __device__ __forceinline__ int farkas_status(double qv, double uterm, double lte
 // then the fixed frequency max_epoch_len) and the primal-weight update.
 // With move set (the restart applied by this kernel was decided by a phase-0 column kernel that
 // staged its parts) it first completes the anchor-movement candidate's test.
+// An ordinary column stage (phase 0, no termination check, no certificate test, no restart
+// transition, no adaptive step) needs from its grid reduction only ||x_t - x~_t||^2 and
+// ||x~_t - x^{n,0}||^2, and from its finaliser only their storage and the advance of (t, k, n).
+// It therefore writes its CTA partials and ends without a ticket (the control block keeps
+// stage = 1, and every CTA sets col_deferred); the next row kernel adds those partials in its last
+// CTA and row_finalize applies the column update first (dcol).  (stage = 1 alone does not mark a
+// deferral: in mixed precision the restart-mode row kernel, launched before the ordinary one,
+// also leaves stage = 1 when it runs.)  Its serial tail (ticket, grid reduction, finaliser) leaves the
+// critical path of every ordinary iteration.
+__device__ __forceinline__ bool col_defers(const IterConsts &ic, int phase, bool check, bool cert,
+                                           bool move) {
+  return phase == 0 && !check && !cert && !move && !ic.adaptive;
+}
+
+// rc: the deferred column stage's sums (dcol; see col_defers), (t, k, n_ep) the iteration after
+// it.
 __device__ __forceinline__ void row_finalize(Ctl *ctl, const IterConsts &ic, const double *r,
                                              long long t, long long k, long long n_ep,
-                                             double sigma, bool move) {
+                                             double sigma, bool move, bool dcol = false,
+                                             const double *rc = nullptr) {
+  if (dcol) {
+    // the finaliser the column stage left: its sums and the advance of (t, k, n)
+    ctl->col_deferred = 0;
+    ctl->dx_sq = rc[0];
+    ctl->xa_sq = rc[1];
+    ctl->t = t;
+    ctl->k = k;
+    ctl->n = n_ep;
+    if (!isfinite(rc[0])) {
+      ctl->status = kNumericalError;
+      ctl->cnt_row = 0;
+      return;
+    }
+  }
   if (move) {
     ctl->mv_ready = 0;
     const int st = farkas_status(r[6], ctl->mv_u, ctl->mv_l,

@@ -32,10 +32,15 @@ constexpr int kFp64MaxRegs = 128;
 template <int RHO2, bool GRP>
 __global__ void __maxnreg__(kFp64MaxRegs)
 k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *__restrict__ xt,
-           RowVecs v, Ctl *ctl, double *part, IterConsts ic) {
+           RowVecs v, Ctl *ctl, double *part, IterConsts ic, DeferredCol dc) {
   extern __shared__ double smem[];
-  if (ctl->status != kRunning || ctl->stage != 0) return;
-  const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
+  if (ctl->status != kRunning) return;
+  // stage 1 here: the preceding ordinary column stage deferred its reduction (col_defers)
+  const bool dcol = ctl->stage == 1 && ctl->col_deferred && !ic.adaptive;
+  if (ctl->stage != 0 && !dcol) return;
+  const long long t = dcol ? ctl->t + 1 : ctl->t;
+  const long long k = dcol ? ctl->k_next : ctl->k;
+  const long long n_ep = dcol ? ctl->n_next : ctl->n;
   const int restart = ctl->restart_pending;
   const double w = ctl->w, sigma = ctl->sigma;
   const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
@@ -64,7 +69,10 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
     double r[13];
     grid_finish<7, 6, false>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
-    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
+    double rc[2] = {0.0, 0.0};
+    if (dcol)   // the deferred ordinary column stage's two sums
+      grid_finish<2, 0, false>(dc.part, rc, 0x3u, 0u, dc.gpart, dc.ngroups, dc.nb);
+    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move, dcol, rc);
   }
 }
 
@@ -123,6 +131,11 @@ k_col_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   walk_tiles<double, double, GRP>(lay, vals, gather, my, ws, epi, gdone);
   if (check) tel_flush(ctl, tl);
 
+  if (col_defers(ic, phase, check, cert, move)) {
+    cta_reduce_store(a, smask, mmask, part);   // reduced by the next row kernel
+    if (threadIdx.x == 0) ctl->col_deferred = 1;
+    return;
+  }
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[19];
     grid_finish<11, 8, false>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
@@ -141,10 +154,11 @@ __global__ void k_unscale(int n, int m, const double *e, const double *xs, const
 
 // GRP: the grouped walk for sides whose short tiles are walked several at a time.
 void launch_row_iter(cudaStream_t st, const SideStore &side, const double *xt, const RowVecs &v,
-                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem) {
+                     Ctl *ctl, double *part, const IterConsts &ic, int grid, int smem,
+                     const DeferredCol &dc) {
   const int threads = side.lay.cta_warps * kWarp;
   auto go = [&](auto kern) {
-    kern<<<grid, threads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl, part, ic);
+    kern<<<grid, threads, smem, st>>>(side.lay, side.v64, side.wa, xt, v, ctl, part, ic, dc);
   };
   const bool grp = side.lay.tile_mult > 1;
   if (ic.rho2) grp ? go(k_row_iter<1, true>) : go(k_row_iter<1, false>);

@@ -63,12 +63,19 @@ __global__ void __maxnreg__(mx_max_regs(MODE, WALK, DFS))
 k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, WalkScratch wa,
               WalkScratch wb, RowVecsMx v, const float *__restrict__ dxt,
               const double *__restrict__ dxt64, const double *__restrict__ x0, Ctl *ctl,
-              double *part, IterConsts ic) {
+              double *part, IterConsts ic, DeferredCol dc) {
   extern __shared__ double smem[];
-  if (ctl->status != kRunning || ctl->stage != 0) return;
+  if (ctl->status != kRunning) return;
+  // stage 1 here: the preceding ordinary column stage deferred its reduction (col_defers); this
+  // iteration is the one after it (an ordinary column stage leaves no restart pending)
+  const int stage = ctl->stage;
+  const bool dcol = MODE == 0 && stage == 1 && ctl->col_deferred;
+  if (stage != 0 && !dcol) return;
   const int restart = ctl->restart_pending;
   if (restart != MODE) return;
-  const long long t = ctl->t, k = ctl->k, n_ep = ctl->n;
+  const long long t = dcol ? ctl->t + 1 : ctl->t;
+  const long long k = dcol ? ctl->k_next : ctl->k;
+  const long long n_ep = dcol ? ctl->n_next : ctl->n;
   const double w = ctl->w, sigma = ctl->sigma;
   const float wf = (float)w, sigf = (float)sigma;
   const bool check = ((t + 1) % ic.check_every == 0) || (t + 1 >= ic.max_iters);
@@ -140,7 +147,11 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, Walk
     double r[13];
     grid_finish<7, 6, true, ND, DFS == 1>(part, r, smask, mmask, wb.group_part,
                                           lay.n_long_tiles);
-    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move);
+    double rc[2] = {0.0, 0.0};
+    if (dcol)   // the deferred ordinary column stage's two sums (its packed slots)
+      grid_finish<2, 0, true, col_df_slots<0>(), DFS == 1>(dc.part, rc, 0x3u, 0u, dc.gpart,
+                                                           dc.ngroups, dc.nb);
+    if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move, dcol, rc);
   }
 }
 
@@ -222,6 +233,11 @@ k_col_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, Walk
     if (check) tel_flush(ctl, tl);
     fa.flush(a);
   }
+  if (MODE == 0 && col_defers(ic, phase, check, rp, move)) {
+    cta_reduce_store(a, smask, mmask, part);   // reduced by the next row kernel
+    if (threadIdx.x == 0) ctl->col_deferred = 1;
+    return;
+  }
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_col)) {
     double r[19];
     grid_finish<11, 8, true, ND, DFS == 1>(part, r, smask, mmask,
@@ -276,11 +292,12 @@ void with_rho_dfs(int rho2, int dfs, F &&f) {
 // entry in all but a few iterations, takes a single wave of CTAs.
 void launch_row_iter_mx(cudaStream_t st, const SideStore &side, const RowVecsMx &v,
                         const float *dxt, const double *dxt64, const double *x0, Ctl *ctl,
-                        double *part, const IterConsts &ic, int grid, int grid1, int smem) {
+                        double *part, const IterConsts &ic, int grid, int grid1, int smem,
+                        const DeferredCol &dc) {
   const int threads = side.lay.cta_warps * kWarp;
   auto go = [&](auto kern, int g, int sm, auto vals) {
     kern<<<g, threads, sm, st>>>(side.lay, side.v64, vals, side.wa, side.wb, v, dxt, dxt64, x0,
-                                 ctl, part, ic);
+                                 ctl, part, ic, dc);
   };
   with_rho_dfs(ic.rho2, ic.df_sums, [&](auto R, auto D) {
     go(k_row_iter_mx<R(), 1, kWalkGrouped, 0, 0>, grid1, smem, side.v32);
