@@ -534,6 +534,80 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
   __syncthreads();
 }
 
+// The last CTA of a row kernel adds a deferred column stage's two sums (see DeferredCol) after
+// its own grid reduction.  dcol_prefetch issues, before that reduction, the loads of the first
+// kDcolPre column rows of each thread (t, t + blockDim, ...), so that their latency overlaps the
+// row reduction's; dcol_finish adds them, any further rows and the column's long-row groups in
+// the order grid_finish uses (a thread's rows in index order, then its groups; lanes by the
+// shuffle tree; warps in index order), and returns the sums (the first ND double-floats) in
+// every thread.
+constexpr int kDcolPre = 4;
+struct DcolPre {
+  double p[kDcolPre][2];
+};
+
+__device__ __forceinline__ void dcol_prefetch(const DeferredCol &dc, DcolPre &pre) {
+#pragma unroll
+  for (int j = 0; j < kDcolPre; ++j) {
+    const int b = (int)threadIdx.x + j * (int)blockDim.x;
+    const double *src = dc.part + (size_t)b * kMaxPartials;
+    pre.p[j][0] = b < dc.nb ? __ldcg(src) : 0.0;
+    pre.p[j][1] = b < dc.nb ? __ldcg(src + 1) : 0.0;
+  }
+}
+
+template <int ND, bool EXACT>
+__device__ void dcol_finish(const DeferredCol &dc, const DcolPre &pre, double *out) {
+  double (*red)[kMaxPartials] = cta_red();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double v[2] = {0.0, 0.0};
+  DF vd[2] = {DF{0.f, 0.f}, DF{0.f, 0.f}};
+  auto take = [&](int i, double p) {
+    if (i < ND) vd[i] = dfx_add<EXACT>(vd[i], df_unpack(p));
+    else v[i] += p;
+  };
+#pragma unroll
+  for (int j = 0; j < kDcolPre; ++j) {
+    if ((int)threadIdx.x + j * (int)blockDim.x >= dc.nb) break;
+    take(0, pre.p[j][0]);
+    take(1, pre.p[j][1]);
+  }
+  for (int b = (int)threadIdx.x + kDcolPre * (int)blockDim.x; b < dc.nb; b += blockDim.x) {
+    const double *src = dc.part + (size_t)b * kMaxPartials;
+    take(0, __ldcg(src));
+    take(1, __ldcg(src + 1));
+  }
+  for (int g = threadIdx.x; g < dc.ngroups; g += blockDim.x) {
+    const double *src = dc.gpart + (size_t)g * kMaxPartials;
+    take(0, __ldcg(src));
+    take(1, __ldcg(src + 1));
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    if (i < ND) {
+      const DF r = dfx_warp_sum<EXACT>(vd[i]);
+      if (lane == 0) red[warp][i] = df_pack(r);
+    } else {
+      const double r = warp_sum(v[i]);
+      if (lane == 0) red[warp][i] = r;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    if (i < ND) {
+      DF r = df_unpack(red[0][i]);
+      for (int w = 1; w < nw; ++w) r = dfx_add<EXACT>(r, df_unpack(red[w][i]));
+      out[i] = df_value(r);
+    } else {
+      double r = red[0][i];
+      for (int w = 1; w < nw; ++w) r += red[w][i];
+      out[i] = r;
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------------------
 // The tile walker: computes dot = (row of the side operator) . src for every row and calls
 // epi(row, dot, is_long) once per row, from one lane, 32 rows per warp at a time.  Work items are

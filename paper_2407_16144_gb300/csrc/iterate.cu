@@ -67,11 +67,13 @@ k_row_iter(SideLayout lay, SideVals<double> vals, WalkScratch ws, const double *
   walk_tiles<double, double, GRP>(lay, vals, gather, my, ws, epi, gdone);
 
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
+    DcolPre pre;
+    if (dcol) dcol_prefetch(dc, pre);   // in flight during the row reduction
     double r[13];
     grid_finish<7, 6, false>(part, r, smask, mmask, ws.group_part, lay.n_long_tiles);
     double rc[2] = {0.0, 0.0};
     if (dcol)   // the deferred ordinary column stage's two sums
-      grid_finish<2, 0, false>(dc.part, rc, 0x3u, 0u, dc.gpart, dc.ngroups, dc.nb);
+      dcol_finish<0, true>(dc, pre, rc);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move, dcol, rc);
   }
 }

@@ -144,13 +144,14 @@ k_row_iter_mx(SideLayout lay, SideVals<double> v64, SideVals<LowT<LP>> v32, Walk
     fa.flush(a);
   }
   if (cta_reduce_and_ticket(a, smask, mmask, 0u, part, &ctl->cnt_row)) {
+    DcolPre pre;
+    if (dcol) dcol_prefetch(dc, pre);   // in flight during the row reduction
     double r[13];
     grid_finish<7, 6, true, ND, DFS == 1>(part, r, smask, mmask, wb.group_part,
                                           lay.n_long_tiles);
     double rc[2] = {0.0, 0.0};
     if (dcol)   // the deferred ordinary column stage's two sums (its packed slots)
-      grid_finish<2, 0, true, col_df_slots<0>(), DFS == 1>(dc.part, rc, 0x3u, 0u, dc.gpart,
-                                                           dc.ngroups, dc.nb);
+      dcol_finish<col_df_slots<0>(), DFS == 1>(dc, pre, rc);
     if (threadIdx.x == 0) row_finalize(ctl, ic, r, t, k, n_ep, sigma, move, dcol, rc);
   }
 }
