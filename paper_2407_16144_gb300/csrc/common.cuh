@@ -542,6 +542,7 @@ __device__ void grid_finish(const double *part, double *out, unsigned smask, uns
 // shuffle tree; warps in index order), and returns the sums (the first ND double-floats) in
 // every thread.
 constexpr int kDcolPre = 4;
+constexpr int kDcolBatch = 6;
 struct DcolPre {
   double p[kDcolPre][2];
 };
@@ -572,10 +573,23 @@ __device__ void dcol_finish(const DeferredCol &dc, const DcolPre &pre, double *o
     take(0, pre.p[j][0]);
     take(1, pre.p[j][1]);
   }
-  for (int b = (int)threadIdx.x + kDcolPre * (int)blockDim.x; b < dc.nb; b += blockDim.x) {
-    const double *src = dc.part + (size_t)b * kMaxPartials;
-    take(0, __ldcg(src));
-    take(1, __ldcg(src + 1));
+  // further rows kDcolBatch at a time, all in flight together
+  const int bd = (int)blockDim.x;
+  for (int b0 = (int)threadIdx.x + kDcolPre * bd; b0 < dc.nb; b0 += kDcolBatch * bd) {
+    double q[kDcolBatch][2];
+#pragma unroll
+    for (int j = 0; j < kDcolBatch; ++j) {
+      const int b = b0 + j * bd;
+      const double *src = dc.part + (size_t)b * kMaxPartials;
+      q[j][0] = b < dc.nb ? __ldcg(src) : 0.0;
+      q[j][1] = b < dc.nb ? __ldcg(src + 1) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kDcolBatch; ++j) {
+      if (b0 + j * bd >= dc.nb) break;
+      take(0, q[j][0]);
+      take(1, q[j][1]);
+    }
   }
   for (int g = threadIdx.x; g < dc.ngroups; g += blockDim.x) {
     const double *src = dc.gpart + (size_t)g * kMaxPartials;
